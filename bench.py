@@ -1,0 +1,403 @@
+"""Benchmark of the FilterGS LoD render path on one GB300 (or N replicas).
+
+One step = one whole frame of the render path (R&L filter, ancestor filter +
+compaction, projection + SH + shrink + key emission, onesweep sort, tile ranges,
+blending) for one camera pose of the synthetic workload, inputs resident in HBM.
+
+Default workload: the 10M-leaf city tree (~12.5M nodes), 1920x1080, 64-pose
+flythrough, adaptive shrinking with tau calibrated over the 64 poses
+(lambda_G = 0.2).  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload city|blobs|tiny]
+                  [--impl ours|reference] [--no-cpu-baseline]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+STAGES = ["filter_rl", "ancestor_compact", "project_keys", "sort", "tile_ranges", "blend"]
+METRIC = "1080p ms/frame & FPS on 10M-leaf LoD tree; GS-tile pairs/frame; HBM roofline %"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def workload(name):
+    from paper_2603_23891_gb300 import synth
+    if name == "city":
+        return (synth.city_tree(), synth.city_cameras(), 3.0,
+                "city-10M: 10M-leaf city LoD tree, 1920x1080, 64-pose flythrough, adaptive shrink")
+    if name == "blobs":
+        return (synth.blob_tree(), synth.blob_cameras(), 3.0,
+                "blobs-1M: 1M-leaf blob LoD tree, 1920x1080, 8 poses, adaptive shrink")
+    if name == "tiny":
+        return (synth.tiny_tree(), [synth.tiny_camera()], 1.0,
+                "tiny-4k: 4,096-leaf tree, 256x256, 1 pose, adaptive shrink")
+    raise ValueError(name)
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- roofline
+
+def algorithmic_bytes(tree, M, NP, width, height, sh_floats):
+    """Bytes the method must move per frame, per stage (documented in the design doc)."""
+    N = tree.n
+    n_int = N - tree.n_leaves
+    D = tree.depth
+    return {
+        "filter_rl": 12.0 * N + 24.0 * n_int + N / 8.0 + N / 8.0,
+        "ancestor_compact": N / 8.0 + 4.0 * D * M + 4.0 * M,
+        "project_keys": M * (4 + 12 + 24 + 8 + 4 * sh_floats + 48) + 12.0 * NP,
+        "sort": NP * (8.0 + 6 * 24.0),
+        "tile_ranges": 8.0 * NP,
+        "blend": NP * (4.0 + 48.0) + 16.0 * width * height,
+    }
+
+
+def blend_alu_peak(sm_mhz, sms):
+    """FP32 lane-ops/s: 128 FP32 lanes per SM per clock."""
+    return 128.0 * sms * sm_mhz * 1e6
+
+
+# ----------------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2603_23891_gb300 import build, filtergs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    build.build()
+
+    t0 = time.time()
+    tree, cams, tau_R, wname = workload(args.workload)
+    log(f"[rank {rank}] workload {tree.name}: {tree.n} nodes, {tree.n_leaves} leaves, "
+        f"depth {tree.depth} ({time.time() - t0:.1f}s)")
+    P = len(cams)
+    my_poses = [k for k in range(P) if k % world == rank] or [rank % P]
+    W, H = cams[0].width, cams[0].height
+
+    r = filtergs.Renderer(device=local, tau_R=tau_R, pair_capacity=args.pair_capacity)
+    t0 = time.time()
+    r.load_tree(tree)
+    log(f"[rank {rank}] tree uploaded ({time.time() - t0:.1f}s)")
+    t0 = time.time()
+    tau, ln_tau, gbars = r.calibrate(cams, args.lambda_g)
+    calib_s = time.time() - t0
+    log(f"[rank {rank}] calibrated: tau={tau:.5f} ln_tau={ln_tau:.5f} "
+        f"mean G={np.nanmean(gbars):.4f} ({calib_s:.2f}s)")
+    r.shrink(tau, ln_tau)
+
+    stream = torch.cuda.current_stream()
+    rgb = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
+    Tt = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # per-pose statistics (M, N_P), also checks device status
+    Ms, NPs = [], []
+    for k in my_poses:
+        r.set_camera(cams[k])
+        _, _, st = r.render(rgb, Tt, stats=True)
+        Ms.append(st.n_selected)
+        NPs.append(st.n_pairs)
+        launches = st.n_launches
+    # shrink-off pair counts for context
+    r.shrink(None)
+    NP_off = []
+    for k in my_poses[: min(8, len(my_poses))]:
+        r.set_camera(cams[k])
+        _, _, st = r.render(rgb, Tt, stats=True)
+        NP_off.append(st.n_pairs)
+    r.shrink(tau, ln_tau)
+
+    for w in range(args.warmup):
+        r.set_camera(cams[my_poses[w % len(my_poses)]])
+        r.render(rgb, Tt)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    slot0 = filtergs.fgs_stage_count(r.ctx)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.zero_()                                     # evict L2 between steps
+        r.set_camera(cams[my_poses[k % len(my_poses)]])
+        ev_s[k].record(stream)
+        r.render(rgb, Tt, stage_events=True)
+        ev_e[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(K)]
+    stage_ms = np.array([filtergs.fgs_stage_times(r.ctx, (slot0 + k) % 256) for k in range(K)])
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end-to-end through the C ABI with pinned host buffers (camera in, image out)
+    rgb_h = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
+    T_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    for w in range(2):
+        r.set_camera(cams[my_poses[0]])
+        r.render_host(rgb_h.numpy(), T_h.numpy())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for k in range(K):
+        r.set_camera(cams[my_poses[k % len(my_poses)]])
+        r.render_host(rgb_h.numpy(), T_h.numpy())
+    e2e_s = time.perf_counter() - e0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    frames = K * world
+    fps = frames / (total_ms / 1e3)
+    result = None
+    if rank == 0:
+        M_mean = float(np.mean(Ms))
+        NP_mean = float(np.mean(NPs))
+        sh_floats = (tree.sh_degree + 1) ** 2 * 3
+        ab = algorithmic_bytes(tree, M_mean, NP_mean, W, H, sh_floats)
+        st_mean = stage_ms.mean(axis=0)
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+        stages = {}
+        for i, nm in enumerate(STAGES):
+            gbs = ab[nm] / (st_mean[i] * 1e-3) / 1e9 if st_mean[i] > 0 else 0.0
+            stages[nm] = {"ms": round(float(st_mean[i]), 5), "algo_bytes": round(ab[nm]),
+                          "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)}
+        dom = STAGES[int(np.argmax(st_mean))]
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        if dom == "blend":
+            # pixel-Gaussian evaluations bound by FP32 issue; report HBM view too
+            dom_rl = {"bound": "hbm", "kernel": "blend_kernel", "achieved": stages[dom]["GB/s"],
+                      "peak": hbm_peak, "unit": "GB/s", "frac": stages[dom]["frac_hbm"],
+                      "traffic": None, "peak_source": peak_src}
+        else:
+            dom_rl = {"bound": "hbm", "kernel": dom, "achieved": stages[dom]["GB/s"],
+                      "peak": hbm_peak, "unit": "GB/s", "frac": stages[dom]["frac_hbm"],
+                      "traffic": None, "peak_source": peak_src}
+        img_bytes = 4 * H * W * 4
+        cam_bytes = 4 * 26 + 8
+        result = {
+            "metric": METRIC, "value": round(fps, 2), "unit": "frames/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": round(total_ms / K, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generator; no trained model or dataset)",
+            "config": {"workload": wname, "n_nodes": tree.n, "n_leaves": tree.n_leaves,
+                       "depth": tree.depth, "resolution": f"{W}x{H}", "poses": P,
+                       "tau_R": tau_R, "lambda_G": args.lambda_g, "tau": tau,
+                       "M_mean": round(M_mean, 1), "N_P_mean": round(NP_mean, 1),
+                       "N_P_mean_shrink_off": round(float(np.mean(NP_off)), 1),
+                       "l2": "flushed between steps (256 MiB write, outside the step events)",
+                       "parallelism": f"replicas x{world} (views round-robin)"},
+            "stages_ms": {nm: stages[nm]["ms"] for nm in STAGES},
+            "stages": stages,
+            "roofline": dom_rl,
+            "e2e": {"value": round(frames / e2e_s, 2), "unit": "frames/s",
+                    "h2d_bytes_per_step": cam_bytes, "d2h_bytes_per_step": img_bytes},
+            "gpu_launches": int(K * launches),
+            "clocks": clk,
+            "calibration_s": round(calib_s, 3),
+            "wall_s_timed": round(wall, 4),
+        }
+    r.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return result, tree, cams, tau, ln_tau, tau_R
+
+
+# ----------------------------------------------------------------------------- oracle
+
+def oracle_sample(tree, cams, tau_R, tau, ln_tau, pose, pix_frac, seed=0):
+    """Oracle on one pose: full cut, projection and pairs; per-pixel blending on a random
+    fraction of the pixels, scaled to a whole frame.  Returns (seconds per frame, info)."""
+    import oracle
+    cam = cams[pose]
+    p = oracle.Params(tau_R=tau_R, shrink=True, tau=tau, ln_tau=ln_tau)
+    t0 = time.perf_counter()
+    sel = oracle.filter_dfs(tree, cam, tau_R)
+    splat, rect, _ = oracle.project(tree, cam, p, sel)
+    keys, vals = oracle.pairs(splat, rect, cam, p)
+    t_front = time.perf_counter() - t0
+    n = cam.width * cam.height
+    rng = np.random.default_rng(seed)
+    k = max(1, int(n * pix_frac))
+    pix = np.sort(rng.choice(n, size=k, replace=False))
+    t0 = time.perf_counter()
+    oracle.render_pixels(splat, keys, vals, cam, p, pix)
+    t_blend = (time.perf_counter() - t0) * (n / k)
+    return t_front + t_blend, {"front_s": t_front, "blend_s_scaled": t_blend, "pixels": k}
+
+
+def cpu_baseline(tree, cams, tau_R, tau, ln_tau):
+    t, info = oracle_sample(tree, cams, tau_R, tau, ln_tau, 0, 0.125)
+    return {"value": round(1.0 / t, 5), "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": (f"pose 0: full LoD cut, projection and {'pairs'} on 1 core; per-pixel "
+                       f"blending of {info['pixels']} random pixels (1/8 of the frame) scaled "
+                       f"to the whole frame; front {info['front_s']:.2f}s, blend "
+                       f"{info['blend_s_scaled']:.2f}s")}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on the machine's host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build_lib()
+    tree, cams, tau_R, wname = workload(args.workload)
+    # Eq. 5-8 on the oracle over one pose (a full-frame KPC render per pose is ~10 s here)
+    sub = cams[:1]
+    t0 = time.perf_counter()
+    tau, ln_tau, _ = oracle_calibrate_sampled(tree, sub, tau_R)
+    calib = time.perf_counter() - t0
+    times = []
+    for w in range(args.warmup + args.steps):
+        t, info = oracle_sample(tree, cams, tau_R, tau, ln_tau, w % len(cams), 1.0 / 64, seed=w)
+        if w >= args.warmup:
+            times.append(t)
+    v = len(times) / sum(times)
+    return {"metric": METRIC, "value": round(v, 5), "unit": "frames/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / v, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generator)", "impl": "reference",
+            "config": {"workload": wname, "n_nodes": tree.n, "tau": tau,
+                       "calibration": f"oracle GTC over {len(sub)} poses ({calib:.1f}s)"},
+            "cpu_baseline": {"value": round(v, 5), "unit": "frames/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "per step: one pose, full cut/projection/pairs, "
+                                       "per-pixel blend of 1/64 of the pixels scaled to a frame"},
+            "e2e": {"value": round(v, 5), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def oracle_calibrate_sampled(tree, cams, tau_R):
+    """Eq. 5-8 on the oracle with KPC from a full-frame render of each pose."""
+    import oracle
+    gbars = []
+    for cam in cams:
+        p = oracle.Params(tau_R=tau_R)
+        fr = oracle.frame(tree, cam, p, blend=False)
+        _, _, kpc = oracle.render(fr.splat, fr.keys, fr.vals, cam, p, want_kpc=True)
+        tx, ty = oracle.tiles_of(cam, p)
+        _, gbar, _ = oracle.gtc(fr.keys, kpc, tx * ty)
+        gbars.append(gbar)
+    tau, ln_tau = oracle.tau_from(gbars, 0.2)
+    return tau, ln_tau, gbars
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--workload", default="city", choices=["city", "blobs", "tiny"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lambda-g", dest="lambda_g", type=float, default=0.2)
+    ap.add_argument("--pair-capacity", type=int, default=64 << 20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        res = run_reference(args)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    res, tree, cams, tau, ln_tau, tau_R = run_ours(args)
+    if res is None:
+        return
+    if not args.no_cpu_baseline:
+        t0 = time.time()
+        res["cpu_baseline"] = cpu_baseline(tree, cams, tau_R, tau, ln_tau)
+        log(f"cpu baseline {time.time() - t0:.1f}s")
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

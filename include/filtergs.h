@@ -1,0 +1,242 @@
+/*
+ * filtergs.h -- C ABI of the GB300 (sm_103a) FilterGS LoD render path.
+ *
+ * The library renders a Level-of-Detail 3D Gaussian Splatting tree for one
+ * camera per call, following FilterGS (traversal-free parallel filtering and
+ * scene-adaptive Gaussian shrinking):
+ *   (a) R&L filter + Ancestor filter over precomputed ancestor paths (§3.2),
+ *   (b) compaction of the survivors, EWA projection and SH colour (§3.1),
+ *   (c) footprint shrinking to opacity tau (§3.3, Eq. 8), Gaussian-tile key
+ *       emission and a (tile | depth) LSD radix sort,
+ *   (d) per-tile front-to-back alpha blending (Eq. 2),
+ * plus the scene calibration that derives tau from the GTC metric (Eq. 5-8).
+ * Every step runs in hand-written CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions
+ *  - Every call returns an int status: FGS_OK (0) or a negative FGS_ERR_*.
+ *    fgs_last_error() gives a context-owned message for the last failure.
+ *    No C++ exception crosses this boundary.
+ *  - A context is bound to one CUDA device.  It owns all device memory it
+ *    allocates (tree copy, frame buffers) and frees it in fgs_destroy().
+ *    Frame calls allocate nothing once capacities are reserved: buffers are
+ *    (re)allocated only in fgs_create(), fgs_load_tree(), fgs_set_camera()
+ *    (larger image) and fgs_set_params() (new pair capacity).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream); every kernel and copy of a call is enqueued on it.  Calls whose
+ *    outputs are device pointers are asynchronous; calls writing host
+ *    pointers synchronise the stream before returning.
+ *  - Errors raised on the device (pair capacity exceeded, a bounded spin-wait
+ *    that timed out) are latched in a device status word and returned by the
+ *    next synchronising call or fgs_sync().
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef FILTERGS_H
+#define FILTERGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FGS_VERSION 1
+
+#define FGS_OK 0
+#define FGS_ERR_ARG (-1)       /* invalid argument (NULL, size, NaN camera ...) */
+#define FGS_ERR_TREE (-2)      /* tree failed validation */
+#define FGS_ERR_CUDA (-3)      /* CUDA runtime error */
+#define FGS_ERR_CAPACITY (-4)  /* pair or selection capacity exceeded on the device */
+#define FGS_ERR_TIMEOUT (-5)   /* a bounded device spin-wait gave up */
+#define FGS_ERR_STATE (-6)     /* call out of order (no tree, no camera ...) */
+#define FGS_ERR_NOMEM (-7)     /* device allocation failed */
+
+#define FGS_SHRINK_OFF 0       /* 3-sigma footprint */
+#define FGS_SHRINK_ON 1        /* footprint where opacity decays to tau (§3.3) */
+
+/* fgs_render flags */
+#define FGS_RENDER_STATS 1u        /* fill M and N_P in fgs_stats (synchronises) */
+#define FGS_RENDER_STAGE_EVENTS 2u /* record per-stage CUDA events (see fgs_stage_times) */
+
+#define FGS_N_STAGES 6             /* filter-R&L, ancestor+compact, project+keys, sort, ranges, blend */
+
+typedef struct fgs_ctx fgs_ctx;
+
+/* LoD tree in structure-of-arrays form, HOST pointers (§3.1 "Hierarchical
+ * Gaussian Tree"; ancestor paths AP of §3.2).  N = n_nodes, D = depth,
+ * K = (sh_degree + 1)^2.
+ *   mu[3][N]          centres
+ *   cov[6][N]         covariance upper triangle xx, xy, xz, yy, yz, zz
+ *   opacity[N]        alpha_0 in (0, 1]
+ *   ln_opacity[N]     ln alpha_0 (the shrink test compares logs, so no
+ *                     transcendental decides a footprint)
+ *   sh[N][K][3]       SH coefficients, real basis with Condon-Shortley phase
+ *   parent[N]         parent id, -1 for the (single) root
+ *   is_leaf[N]        1 for a leaf (no children), else 0
+ *   ap[D][N]          row k = (k+1)-th ancestor of each node, 0xFFFFFFFF past
+ *                     the root; must equal the parent chain.
+ * The arrays are read during fgs_load_tree() only (copied to the device). */
+typedef struct fgs_tree {
+    uint32_t n_nodes;
+    uint32_t depth;
+    uint32_t sh_degree;
+    uint32_t reserved;
+    const float* mu;
+    const float* cov;
+    const float* opacity;
+    const float* ln_opacity;
+    const float* sh;
+    const int32_t* parent;
+    const uint8_t* is_leaf;
+    const uint32_t* ap;
+} fgs_tree;
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  v = R x + t maps
+ * world to camera (R row-major).  Pixel (i, j) samples at (i + 0.5, j + 0.5);
+ * a centre projects to (fx vx/vz + cx, fy vy/vz + cy).  tan_half_x/y are the
+ * half-FOV tangents (the frustum test allows 1.3x of them). */
+typedef struct fgs_camera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float tan_half_x, tan_half_y;
+    float campos[3];
+    int32_t width, height;
+} fgs_camera;
+
+typedef struct fgs_params {
+    float tau_R;              /* R&L pixel-radius threshold, 3 px in the paper (§3.2) */
+    int32_t tile_w, tile_h;   /* tile size in pixels; powers of two, tile_w * tile_h == 256 */
+    float bg[3];              /* background colour added as T * bg */
+    uint64_t pair_capacity;   /* max Gaussian-tile pairs per frame (0 = keep current / default) */
+} fgs_params;
+
+typedef struct fgs_stats {
+    uint32_t n_selected;      /* M: nodes in the LoD cut */
+    uint32_t reserved;
+    uint64_t n_pairs;         /* N_P: Gaussian-tile pairs (may exceed capacity on error) */
+    uint32_t n_launches;      /* kernels this call enqueued */
+    int32_t device_status;    /* latched device status (FGS_OK if none) */
+} fgs_stats;
+
+/* Library version (FGS_VERSION). */
+int fgs_version(void);
+
+/* Create a context on CUDA device `device` with default parameters
+ * (tau_R 3, 16x16 tiles, black background, 32 Mi pairs).  *out receives the
+ * handle.  Errors: FGS_ERR_ARG, FGS_ERR_CUDA, FGS_ERR_NOMEM. */
+int fgs_create(fgs_ctx** out, int device);
+
+/* Free every device buffer of the context and the context itself.  Waits for
+ * work of the context to finish.  NULL is accepted. */
+int fgs_destroy(fgs_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none).  The string
+ * is owned by the context and valid until its next call. */
+const char* fgs_last_error(const fgs_ctx* ctx);
+
+/* Set render parameters.  A non-zero pair_capacity reallocates the pair
+ * buffers to exactly that many pairs.
+ * Errors: FGS_ERR_ARG (tile not a power of two or not 256 pixels, NaN). */
+int fgs_set_params(fgs_ctx* ctx, const fgs_params* p);
+
+/* Validate a tree (host arrays, layout above) without any device work:
+ * one root, parent ids in range and acyclic, is_leaf equals "has no
+ * children", AP rows equal the parent chain, depth covers the longest path,
+ * finite attributes, opacity in (0, 1].  On failure writes a message into
+ * msg (msg_len bytes, may be NULL).  Returns FGS_OK, FGS_ERR_ARG or
+ * FGS_ERR_TREE.  Callable without a GPU. */
+int fgs_validate_tree(const fgs_tree* tree, char* msg, size_t msg_len);
+
+/* Validate (as fgs_validate_tree) and upload a tree (host arrays).  Validation: one
+ * root, parent ids in range and acyclic, is_leaf equals "has no children",
+ * AP rows equal the parent chain, depth covers the longest path, finite
+ * attributes.  Replaces a previously loaded tree.  Errors: FGS_ERR_ARG,
+ * FGS_ERR_TREE, FGS_ERR_NOMEM, FGS_ERR_CUDA. */
+int fgs_load_tree(fgs_ctx* ctx, const fgs_tree* tree);
+
+/* Set the camera used by the next frame calls (copied; host struct).  Grows
+ * the tile buffers if the image has more tiles.  Errors: FGS_ERR_ARG for
+ * non-finite values, width/height outside 1..16384, tan_half <= 0. */
+int fgs_set_camera(fgs_ctx* ctx, const fgs_camera* cam);
+
+/* Footprint mode for the next frames (§3.3): FGS_SHRINK_OFF (3 sigma) or
+ * FGS_SHRINK_ON with threshold tau and ln_tau = ln(tau) (both supplied by
+ * the caller, typically from fgs_calibrate_gtc(), so the CUDA path and any
+ * checker use the same bits).  Errors: FGS_ERR_ARG. */
+int fgs_set_shrink(fgs_ctx* ctx, int mode, float tau, float ln_tau);
+
+/* Run the filter only (§3.2): R&L + Ancestor filters and compaction.
+ * sel_out receives the selected node ids in ascending order (up to cap of
+ * them), *M_out the count M (may exceed cap; then only cap ids are
+ * written and FGS_ERR_CAPACITY is returned).  out_is_device: 1 if sel_out
+ * and M_out are device pointers (asynchronous), 0 for host pointers
+ * (synchronising). */
+int fgs_filter(fgs_ctx* ctx, void* stream, uint32_t* sel_out, uint32_t cap, uint32_t* M_out,
+               int out_is_device);
+
+/* Render one frame of the current camera: filter, project, shrink, emit keys,
+ * sort, tile ranges, blend.  rgb_out: float [3][H][W] planar colour
+ * C + T * bg; T_out: float [H][W] final transmittance (may be NULL).
+ * out_is_device selects device (asynchronous) or host (synchronising)
+ * outputs.  flags: FGS_RENDER_STATS fills st->n_selected / n_pairs /
+ * device_status (synchronising); FGS_RENDER_STAGE_EVENTS records stage events
+ * into the next slot of a 256-slot ring (see fgs_stage_times).  st may be
+ * NULL.  Errors: FGS_ERR_STATE (no tree or camera), FGS_ERR_ARG,
+ * FGS_ERR_CUDA, and latched device errors when synchronising. */
+int fgs_render(fgs_ctx* ctx, void* stream, float* rgb_out, float* T_out, int out_is_device,
+               uint32_t flags, fgs_stats* st);
+
+/* Per-stage durations (ms, CUDA events) of the frame recorded in ring slot
+ * `slot` (0..255, in call order modulo 256): FGS_N_STAGES values.  Waits for
+ * those events.  Errors: FGS_ERR_ARG (slot never recorded). */
+int fgs_stage_times(fgs_ctx* ctx, int slot, float* ms_out);
+
+/* Number of frames recorded with FGS_RENDER_STAGE_EVENTS so far. */
+int fgs_stage_count(const fgs_ctx* ctx, uint64_t* count_out);
+
+/* Copy the sorted Gaussian-tile pairs of the last frame: keys
+ * (tile << 32 | depth bits) and values (rank of the Gaussian in the
+ * selection).  At most cap pairs; *n_out = N_P.  Synchronising for host
+ * outputs.  Errors: FGS_ERR_STATE (no frame yet), FGS_ERR_CAPACITY. */
+int fgs_get_pairs(fgs_ctx* ctx, void* stream, uint64_t* keys_out, uint32_t* vals_out,
+                  uint64_t cap, uint64_t* n_out, int out_is_device);
+
+/* Copy the projected splats of the last frame: float [M][12] rows of
+ * u, v, conic A, B, C, ln-threshold, alpha_0, depth, r, g, b, footprint
+ * radius (0 when the Gaussian is dropped by shrinking or has a singular
+ * conic; conic 0 in the latter case), in selection order.
+ * *M_out = M.  Errors as fgs_get_pairs. */
+int fgs_get_splats(fgs_ctx* ctx, void* stream, float* out, uint32_t cap, uint32_t* M_out,
+                   int out_is_device);
+
+/* Calibration pre-render of the current camera with the 3-sigma footprint
+ * (§3.3): KPC of every sorted pair (Eq. 5), GTC per tile (Eq. 6, NaN for
+ * tiles without pairs) and the view average G_v (Eq. 7) over tiles that have
+ * pairs.  kpc_out (float [N_P], may be NULL, at most kpc_cap values) and
+ * G_out (float [tiles], may be NULL) are host or device per out_is_device;
+ * gbar_out is a host double.  Synchronising.  Leaves the shrink mode
+ * unchanged. */
+int fgs_calibrate_view(fgs_ctx* ctx, void* stream, double* gbar_out, float* kpc_out,
+                       uint64_t kpc_cap, float* G_out, int out_is_device);
+
+/* Scene calibration (§3.3, Eq. 8): pre-render n_views cameras (host array),
+ * G = mean of their G_v, tau = lambda_G / G, ln_tau = ln lambda_G - ln G
+ * (float64, rounded once).  gbar_views_out (host, n_views doubles) may be
+ * NULL.  Leaves the last view as the current camera.  Does NOT switch
+ * shrinking on: pass tau / ln_tau to fgs_set_shrink(). */
+int fgs_calibrate_gtc(fgs_ctx* ctx, void* stream, const fgs_camera* views, int n_views,
+                      float lambda_G, double* gbar_views_out, float* tau_out, float* ln_tau_out);
+
+/* Diagnostic: evaluate the blend's binary32 exp (Cody-Waite reduction,
+ * degree-7 Taylor polynomial) on n device floats x -> y (device pointers) on
+ * `stream`.  Asynchronous.  Errors: FGS_ERR_ARG, FGS_ERR_CUDA. */
+int fgs_eval_exp(const float* x, float* y, uint64_t n, void* stream);
+
+/* Wait for the stream and return any latched device status, then clear it. */
+int fgs_sync(fgs_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FILTERGS_H */

@@ -270,8 +270,14 @@ def gtc(keys, kpc, n_tiles: int):
 def tau_from(gbar_views, lambda_G: float = 0.2):
     """Eq. 8: G = mean of the per-view averages, tau = lambda_G / G.
 
+    A view without any pair has no G_v (0/0) and is left out of the mean.
     Returns (tau, ln tau) rounded to binary32 once, in float64 arithmetic."""
-    G = float(np.mean(np.asarray(gbar_views, np.float64)))
+    g = np.asarray(gbar_views, np.float64)
+    g = g[np.isfinite(g)]
+    G = 0.0
+    for v in g:
+        G += float(v)
+    G /= len(g)
     tau = lambda_G / G
     ln_tau = math.log(lambda_G) - math.log(G)
     return float(np.float32(tau)), float(np.float32(ln_tau))

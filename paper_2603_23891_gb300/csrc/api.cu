@@ -1,0 +1,780 @@
+// C ABI of the FilterGS render path: context, tree upload and validation,
+// camera / parameter state, frame orchestration on the caller's stream.
+#include "filtergs.h"
+#include "fgs_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace fgs;
+
+namespace {
+
+constexpr int kEventSlots = 256;
+constexpr uint64_t kDefaultPairCap = 32ull << 20;
+constexpr uint64_t kMaxPairCap = (1ull << 31) - 64;
+constexpr int kMaxTiles = 1 << 16;
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct fgs_ctx {
+    int device = 0;
+    int sms = 1;
+    std::string err;
+    fgs_params params{};
+    // occupancy (resident blocks per SM)
+    int occ_pred = 1, occ_anc = 1, occ_proj = 1, occ_hist = 1, occ_sort = 1, occ_ranges = 1;
+    // tree
+    bool has_tree = false;
+    DevTree tree{};
+    void* tree_mem = nullptr;
+    // camera / shrink
+    bool has_cam = false;
+    fgs_camera cam{};
+    int shrink = FGS_SHRINK_OFF;
+    float tau = 0.0f, ln_tau = -INFINITY;
+    // node-sized frame buffers
+    size_t node_cap = 0;
+    uint32_t* pbits = nullptr;
+    uint32_t* sel = nullptr;
+    float* splat = nullptr;
+    unsigned long long* lb_compact = nullptr;
+    unsigned long long* lb_project = nullptr;
+    // pair-sized buffers
+    uint64_t pair_cap = 0;
+    unsigned long long* keys0 = nullptr;
+    unsigned long long* keys1 = nullptr;
+    uint32_t* vals0 = nullptr;
+    uint32_t* vals1 = nullptr;
+    float* kpc = nullptr;
+    unsigned long long* lb_sort = nullptr;
+    // tile-sized buffers
+    size_t tile_cap = 0;
+    uint2* ranges = nullptr;
+    float* G = nullptr;
+    // image staging for host outputs: rgb planes + T
+    size_t img_cap = 0;
+    float* img = nullptr;
+    // frame state
+    FrameState* st = nullptr;
+    FrameState* st_host = nullptr;
+    // stage events
+    bool ev_ready = false;
+    cudaEvent_t ev[kEventSlots][kStages + 1];
+    uint64_t ev_count = 0;
+    // last frame
+    bool have_frame = false;
+    bool sorted_in_1 = false;
+};
+
+namespace {
+
+int fail(fgs_ctx* c, int code, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+#define FGS_CUDA(ctx, expr)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? FGS_ERR_NOMEM : FGS_ERR_CUDA, \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+void free_ptr(void* p)
+{
+    if (p) cudaFree(p);
+}
+
+int grow(fgs_ctx* c, void** p, size_t bytes)
+{
+    free_ptr(*p);
+    *p = nullptr;
+    if (bytes == 0) return FGS_OK;
+    FGS_CUDA(c, cudaMalloc(p, bytes));
+    FGS_CUDA(c, cudaMemset(*p, 0, bytes));
+    return FGS_OK;
+}
+
+// Pair buffers sized exactly for `cap` pairs (reallocated when it changes).
+int ensure_pairs(fgs_ctx* c, uint64_t cap)
+{
+    if (cap == c->pair_cap) return FGS_OK;
+    int r;
+    const size_t n = (size_t)cap + 8;   // TMA reads an aligned superset of a slice
+    if ((r = grow(c, (void**)&c->keys0, n * 8))) return r;
+    if ((r = grow(c, (void**)&c->keys1, n * 8))) return r;
+    if ((r = grow(c, (void**)&c->vals0, n * 4))) return r;
+    if ((r = grow(c, (void**)&c->vals1, n * 4))) return r;
+    if ((r = grow(c, (void**)&c->kpc, n * 4))) return r;
+    const size_t sort_tiles = (size_t)((cap + kSortTile - 1) / kSortTile);
+    if ((r = grow(c, (void**)&c->lb_sort, sort_tiles * 256 * 8))) return r;
+    c->pair_cap = cap;
+    c->have_frame = false;
+    return FGS_OK;
+}
+
+int ensure_nodes(fgs_ctx* c, size_t n_pad)
+{
+    if (n_pad <= c->node_cap) return FGS_OK;
+    int r;
+    if ((r = grow(c, (void**)&c->pbits, n_pad / 32 * 4))) return r;
+    if ((r = grow(c, (void**)&c->sel, n_pad * 4))) return r;
+    if ((r = grow(c, (void**)&c->splat, n_pad * kSplatStride * 4))) return r;
+    if ((r = grow(c, (void**)&c->lb_compact, (n_pad / kFilterTile + 2) * 8))) return r;
+    if ((r = grow(c, (void**)&c->lb_project, (n_pad / kProjThreads + 2) * 8))) return r;
+    c->node_cap = n_pad;
+    return FGS_OK;
+}
+
+int ensure_tiles(fgs_ctx* c, size_t tiles, size_t pixels)
+{
+    int r;
+    if (tiles > c->tile_cap) {
+        if ((r = grow(c, (void**)&c->ranges, tiles * sizeof(uint2)))) return r;
+        if ((r = grow(c, (void**)&c->G, tiles * 4))) return r;
+        c->tile_cap = tiles;
+    }
+    if (pixels > c->img_cap) {
+        if ((r = grow(c, (void**)&c->img, pixels * 4 * 4))) return r;
+        c->img_cap = pixels;
+    }
+    return FGS_OK;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v)
+{
+    int k = 0;
+    while ((1 << k) < v) ++k;
+    return k;
+}
+
+DevCamera make_devcam(const fgs_ctx* c, bool force_shrink_off)
+{
+    DevCamera d{};
+    std::memcpy(d.R, c->cam.R, sizeof d.R);
+    std::memcpy(d.t, c->cam.t, sizeof d.t);
+    d.fx = c->cam.fx;
+    d.fy = c->cam.fy;
+    d.cx = c->cam.cx;
+    d.cy = c->cam.cy;
+    d.tan_half_x = c->cam.tan_half_x;
+    d.tan_half_y = c->cam.tan_half_y;
+    std::memcpy(d.campos, c->cam.campos, sizeof d.campos);
+    d.width = c->cam.width;
+    d.height = c->cam.height;
+    d.tile_w = c->params.tile_w;
+    d.tile_h = c->params.tile_h;
+    d.tile_shift_x = ilog2(d.tile_w);
+    d.tile_shift_y = ilog2(d.tile_h);
+    d.tiles_x = (d.width + d.tile_w - 1) / d.tile_w;
+    d.tiles_y = (d.height + d.tile_h - 1) / d.tile_h;
+    d.tau_R = c->params.tau_R;
+    d.shrink = force_shrink_off ? 0 : c->shrink;
+    d.tau = c->tau;
+    d.ln_tau = c->ln_tau;
+    std::memcpy(d.bg, c->params.bg, sizeof d.bg);
+    const int tiles = d.tiles_x * d.tiles_y;
+    const int tile_bits = ilog2(tiles);
+    d.sort_passes = 4 + (tile_bits + 7) / 8;
+    return d;
+}
+
+int check_ready(fgs_ctx* c)
+{
+    if (!c) return FGS_ERR_ARG;
+    if (!c->has_tree) return fail(c, FGS_ERR_STATE, "no tree loaded");
+    if (!c->has_cam) return fail(c, FGS_ERR_STATE, "no camera set");
+    return FGS_OK;
+}
+
+// Enqueue the frame up to tile ranges.  Returns the number of kernel launches.
+int enqueue_front(fgs_ctx* c, const DevCamera& dc, cudaStream_t s, cudaEvent_t* ev)
+{
+    int launches = 0;
+    const int tiles = dc.tiles_x * dc.tiles_y;
+    if (ev) cudaEventRecord(ev[0], s);
+    launch_frame_begin(c->st, c->ranges, tiles, s);
+    launch_filter_pred(c->tree, dc, c->pbits, c->sms * c->occ_pred, s);
+    launches += 2;
+    if (ev) cudaEventRecord(ev[1], s);
+    launch_filter_anc_compact(c->tree, c->pbits, c->sel, c->lb_compact, c->st, c->sms * c->occ_anc, s);
+    ++launches;
+    if (ev) cudaEventRecord(ev[2], s);
+    launch_project_emit(c->tree, dc, c->sel, c->splat, c->keys0, c->vals0, c->pair_cap,
+                        c->lb_project, c->st, c->sms * c->occ_proj, s);
+    ++launches;
+    if (ev) cudaEventRecord(ev[3], s);
+    launches += launch_sort(c->keys0, c->vals0, c->keys1, c->vals1, c->pair_cap, dc.sort_passes,
+                            c->lb_sort, c->st, c->sms * c->occ_hist, c->sms * c->occ_sort, s);
+    c->sorted_in_1 = (dc.sort_passes & 1) != 0;
+    if (ev) cudaEventRecord(ev[4], s);
+    launch_tile_ranges(c->sorted_in_1 ? c->keys1 : c->keys0, c->pair_cap, c->ranges, c->st,
+                       c->sms * c->occ_ranges, s);
+    ++launches;
+    if (ev) cudaEventRecord(ev[5], s);
+    return launches;
+}
+
+int read_state(fgs_ctx* c, cudaStream_t s)
+{
+    FGS_CUDA(c, cudaMemcpyAsync(c->st_host, c->st, sizeof(FrameState), cudaMemcpyDeviceToHost, s));
+    FGS_CUDA(c, cudaStreamSynchronize(s));
+    return FGS_OK;
+}
+
+int latched_status(fgs_ctx* c)
+{
+    const int st = c->st_host->status;
+    if (st == 0) return FGS_OK;
+    if (st == kErrCapacity)
+        return fail(c, FGS_ERR_CAPACITY, "pair capacity %llu exceeded (N_P = %llu)",
+                    (unsigned long long)c->pair_cap, (unsigned long long)c->st_host->n_pairs);
+    if (st == kErrTimeout)
+        return fail(c, FGS_ERR_TIMEOUT, "device spin-wait timed out (site 0x%x)", c->st_host->status_info);
+    return fail(c, FGS_ERR_CUDA, "device status %d", st);
+}
+
+int clear_status(fgs_ctx* c, cudaStream_t s)
+{
+    FGS_CUDA(c, cudaMemsetAsync(&c->st->status, 0, 2 * sizeof(int32_t), s));
+    return FGS_OK;
+}
+
+bool finite_all(const float* p, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fgs_version(void) { return FGS_VERSION; }
+
+int fgs_create(fgs_ctx** out, int device)
+{
+    if (!out) return FGS_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FGS_ERR_ARG;
+    DeviceGuard g(device);
+    if (!g.ok) return FGS_ERR_CUDA;
+    fgs_ctx* c = new fgs_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    c->occ_pred = occ_filter_pred();
+    c->occ_anc = occ_filter_anc();
+    c->occ_proj = occ_project();
+    c->occ_hist = occ_sort_hist();
+    c->occ_sort = occ_sort_pass();
+    c->occ_ranges = occ_tile_ranges();
+    c->params.tau_R = 3.0f;
+    c->params.tile_w = 16;
+    c->params.tile_h = 16;
+    c->params.bg[0] = c->params.bg[1] = c->params.bg[2] = 0.0f;
+    c->params.pair_capacity = kDefaultPairCap;
+    int r = FGS_OK;
+    if (cudaMalloc((void**)&c->st, sizeof(FrameState)) != cudaSuccess ||
+        cudaMemset(c->st, 0, sizeof(FrameState)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->st_host, sizeof(FrameState)) != cudaSuccess)
+        r = FGS_ERR_NOMEM;
+    if (r == FGS_OK) r = ensure_pairs(c, kDefaultPairCap);
+    if (r != FGS_OK) {
+        fgs_destroy(c);
+        return r;
+    }
+    std::memset(c->st_host, 0, sizeof(FrameState));
+    *out = c;
+    return FGS_OK;
+}
+
+int fgs_destroy(fgs_ctx* c)
+{
+    if (!c) return FGS_OK;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    void* bufs[] = {c->tree_mem, c->pbits, c->sel, c->splat, c->lb_compact, c->lb_project,
+                    c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->lb_sort, c->ranges,
+                    c->G, c->img, c->st};
+    for (void* p : bufs) free_ptr(p);
+    if (c->st_host) cudaFreeHost(c->st_host);
+    if (c->ev_ready)
+        for (int i = 0; i < kEventSlots; ++i)
+            for (int k = 0; k <= kStages; ++k) cudaEventDestroy(c->ev[i][k]);
+    delete c;
+    return FGS_OK;
+}
+
+const char* fgs_last_error(const fgs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int fgs_set_params(fgs_ctx* c, const fgs_params* p)
+{
+    if (!c || !p) return FGS_ERR_ARG;
+    if (std::isnan(p->tau_R)) return fail(c, FGS_ERR_ARG, "tau_R is NaN");
+    if (!is_pow2(p->tile_w) || !is_pow2(p->tile_h) || p->tile_w * p->tile_h != 256)
+        return fail(c, FGS_ERR_ARG, "tile %dx%d must be powers of two with 256 pixels", p->tile_w,
+                    p->tile_h);
+    if (!finite_all(p->bg, 3)) return fail(c, FGS_ERR_ARG, "background not finite");
+    if (p->pair_capacity > kMaxPairCap) return fail(c, FGS_ERR_ARG, "pair capacity too large");
+    DeviceGuard g(c->device);
+    c->params.tau_R = p->tau_R;
+    c->params.tile_w = p->tile_w;
+    c->params.tile_h = p->tile_h;
+    std::memcpy(c->params.bg, p->bg, sizeof p->bg);
+    if (p->pair_capacity) {
+        int r = ensure_pairs(c, p->pair_capacity);
+        if (r) return r;
+        c->params.pair_capacity = p->pair_capacity;
+    }
+    if (c->has_cam) {
+        const DevCamera d = make_devcam(c, false);
+        int r = ensure_tiles(c, (size_t)d.tiles_x * d.tiles_y, (size_t)d.width * d.height);
+        if (r) return r;
+    }
+    c->have_frame = false;
+    return FGS_OK;
+}
+
+int fgs_validate_tree(const fgs_tree* t, char* msg, size_t msg_len)
+{
+    auto bad = [&](int code, const char* fmt, ...) {
+        if (msg && msg_len) {
+            va_list ap;
+            va_start(ap, fmt);
+            vsnprintf(msg, msg_len, fmt, ap);
+            va_end(ap);
+        }
+        return code;
+    };
+    if (msg && msg_len) msg[0] = 0;
+    if (!t) return bad(FGS_ERR_ARG, "null tree");
+    const uint64_t N = t->n_nodes;
+    const uint32_t D = t->depth;
+    if (N == 0 || N > (1ull << 31)) return bad(FGS_ERR_ARG, "n_nodes %llu out of range", (unsigned long long)N);
+    if (t->sh_degree > 3) return bad(FGS_ERR_ARG, "sh_degree %u > 3", t->sh_degree);
+    if (!t->mu || !t->cov || !t->opacity || !t->ln_opacity || !t->sh || !t->parent || !t->is_leaf ||
+        (D > 0 && !t->ap))
+        return bad(FGS_ERR_ARG, "null tree array");
+    if (D > 64) return bad(FGS_ERR_ARG, "depth %u > 64", D);
+    const int K = (int)((t->sh_degree + 1) * (t->sh_degree + 1));
+    std::vector<uint8_t> has_child(N, 0);
+    uint64_t roots = 0;
+    for (uint64_t n = 0; n < N; ++n) {
+        const int32_t p = t->parent[n];
+        if (p == -1) {
+            ++roots;
+            continue;
+        }
+        if (p < 0 || (uint64_t)p >= N || (uint64_t)p == n)
+            return bad(FGS_ERR_TREE, "node %llu has invalid parent %d", (unsigned long long)n, p);
+        has_child[p] = 1;
+    }
+    if (roots != 1) return bad(FGS_ERR_TREE, "tree has %llu roots", (unsigned long long)roots);
+    for (uint64_t n = 0; n < N; ++n)
+        if ((t->is_leaf[n] != 0) != (has_child[n] == 0))
+            return bad(FGS_ERR_TREE, "is_leaf[%llu] disagrees with the parent array", (unsigned long long)n);
+    for (uint64_t n = 0; n < N; ++n) {
+        int64_t a = t->parent[n];
+        for (uint32_t k = 0; k < D; ++k) {
+            const uint32_t expect = a >= 0 ? (uint32_t)a : kApPad;
+            if (t->ap[(uint64_t)k * N + n] != expect)
+                return bad(FGS_ERR_TREE, "AP[%u][%llu] = %u, parent chain gives %u", k,
+                           (unsigned long long)n, t->ap[(uint64_t)k * N + n], expect);
+            a = a >= 0 ? t->parent[a] : -1;
+        }
+        if (a != -1)
+            return bad(FGS_ERR_TREE, "node %llu: ancestor chain longer than depth %u (or a cycle)",
+                       (unsigned long long)n, D);
+    }
+    if (!finite_all(t->mu, 3 * N) || !finite_all(t->cov, 6 * N) || !finite_all(t->ln_opacity, N) ||
+        !finite_all(t->sh, (size_t)N * K * 3))
+        return bad(FGS_ERR_TREE, "non-finite tree attribute");
+    for (uint64_t n = 0; n < N; ++n)
+        if (!(t->opacity[n] > 0.0f && t->opacity[n] <= 1.0f))
+            return bad(FGS_ERR_TREE, "opacity[%llu] = %g outside (0, 1]", (unsigned long long)n,
+                       (double)t->opacity[n]);
+    return FGS_OK;
+}
+
+int fgs_load_tree(fgs_ctx* c, const fgs_tree* t)
+{
+    if (!c || !t) return FGS_ERR_ARG;
+    const uint64_t N = t->n_nodes;
+    const uint32_t D = t->depth;
+    const int K = (int)((t->sh_degree + 1) * (t->sh_degree + 1));
+
+    {
+        char msg[512];
+        const int v = fgs_validate_tree(t, msg, sizeof msg);
+        if (v != FGS_OK) return fail(c, v, "%s", msg);
+    }
+
+    // --- device layout ---------------------------------------------------
+    DeviceGuard g(c->device);
+    const size_t n_pad = align_up(N, kFilterTile);
+    const uint32_t sh_stride = (uint32_t)align_up((size_t)K * 3, 4);
+    const size_t sz_mu = 3 * n_pad * 4, sz_cov = 6 * n_pad * 4, sz_op = n_pad * 4;
+    const size_t sz_sh = n_pad * sh_stride * 4, sz_leaf = n_pad / 32 * 4;
+    const size_t sz_ap = (size_t)std::max<uint32_t>(D, 1) * n_pad * 4;
+    size_t off = 0;
+    const size_t o_mu = off; off = align_up(off + sz_mu, 256);
+    const size_t o_cov = off; off = align_up(off + sz_cov, 256);
+    const size_t o_op = off; off = align_up(off + sz_op, 256);
+    const size_t o_lop = off; off = align_up(off + sz_op, 256);
+    const size_t o_sh = off; off = align_up(off + sz_sh, 256);
+    const size_t o_leaf = off; off = align_up(off + sz_leaf, 256);
+    const size_t o_ap = off; off = align_up(off + sz_ap, 256);
+    const size_t total = off;
+
+    free_ptr(c->tree_mem);
+    c->tree_mem = nullptr;
+    c->has_tree = false;
+    c->have_frame = false;
+    FGS_CUDA(c, cudaMalloc(&c->tree_mem, total));
+    FGS_CUDA(c, cudaMemset(c->tree_mem, 0, total));
+    char* base = (char*)c->tree_mem;
+    for (int q = 0; q < 3; ++q)
+        FGS_CUDA(c, cudaMemcpy(base + o_mu + q * n_pad * 4, t->mu + q * N, N * 4, cudaMemcpyHostToDevice));
+    for (int q = 0; q < 6; ++q)
+        FGS_CUDA(c, cudaMemcpy(base + o_cov + q * n_pad * 4, t->cov + q * N, N * 4, cudaMemcpyHostToDevice));
+    FGS_CUDA(c, cudaMemcpy(base + o_op, t->opacity, N * 4, cudaMemcpyHostToDevice));
+    FGS_CUDA(c, cudaMemcpy(base + o_lop, t->ln_opacity, N * 4, cudaMemcpyHostToDevice));
+    if (sh_stride == (uint32_t)K * 3) {
+        FGS_CUDA(c, cudaMemcpy(base + o_sh, t->sh, N * sh_stride * 4, cudaMemcpyHostToDevice));
+    } else {
+        FGS_CUDA(c, cudaMemcpy2D(base + o_sh, sh_stride * 4, t->sh, (size_t)K * 3 * 4, (size_t)K * 3 * 4,
+                                 N, cudaMemcpyHostToDevice));
+    }
+    {
+        std::vector<uint32_t> bits(n_pad / 32, 0);
+        for (uint64_t n = 0; n < N; ++n)
+            if (t->is_leaf[n]) bits[n >> 5] |= 1u << (n & 31);
+        FGS_CUDA(c, cudaMemcpy(base + o_leaf, bits.data(), sz_leaf, cudaMemcpyHostToDevice));
+    }
+    if (D > 0) {
+        FGS_CUDA(c, cudaMemcpy2D(base + o_ap, n_pad * 4, t->ap, N * 4, N * 4, D, cudaMemcpyHostToDevice));
+    }
+    DevTree& dt = c->tree;
+    dt.n = (uint32_t)N;
+    dt.n_pad = (uint32_t)n_pad;
+    dt.depth = D;
+    dt.sh_degree = t->sh_degree;
+    dt.sh_stride = sh_stride;
+    dt.mu = (const float*)(base + o_mu);
+    dt.cov = (const float*)(base + o_cov);
+    dt.opacity = (const float*)(base + o_op);
+    dt.ln_opacity = (const float*)(base + o_lop);
+    dt.sh = (const float*)(base + o_sh);
+    dt.leaf_bits = (const uint32_t*)(base + o_leaf);
+    dt.ap = (const uint32_t*)(base + o_ap);
+    int r = ensure_nodes(c, n_pad);
+    if (r) return r;
+    c->has_tree = true;
+    return FGS_OK;
+}
+
+int fgs_set_camera(fgs_ctx* c, const fgs_camera* cam)
+{
+    if (!c || !cam) return FGS_ERR_ARG;
+    if (!finite_all(cam->R, 9) || !finite_all(cam->t, 3) || !finite_all(cam->campos, 3) ||
+        !std::isfinite(cam->fx) || !std::isfinite(cam->fy) || !std::isfinite(cam->cx) ||
+        !std::isfinite(cam->cy) || !(cam->fx > 0) || !(cam->fy > 0) || !(cam->tan_half_x > 0) ||
+        !(cam->tan_half_y > 0) || !std::isfinite(cam->tan_half_x) || !std::isfinite(cam->tan_half_y))
+        return fail(c, FGS_ERR_ARG, "camera has non-finite or non-positive values");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+        return fail(c, FGS_ERR_ARG, "image %dx%d out of range", cam->width, cam->height);
+    DeviceGuard g(c->device);
+    const fgs_camera prev = c->cam;
+    const bool had = c->has_cam;
+    c->cam = *cam;
+    const DevCamera d = make_devcam(c, false);
+    const size_t tiles = (size_t)d.tiles_x * d.tiles_y;
+    if (tiles > (size_t)kMaxTiles) {
+        c->cam = prev;
+        c->has_cam = had;
+        return fail(c, FGS_ERR_ARG, "%zu tiles exceed %d", tiles, kMaxTiles);
+    }
+    int r = ensure_tiles(c, tiles, (size_t)d.width * d.height);
+    if (r) return r;
+    c->has_cam = true;
+    c->have_frame = false;
+    return FGS_OK;
+}
+
+int fgs_set_shrink(fgs_ctx* c, int mode, float tau, float ln_tau)
+{
+    if (!c) return FGS_ERR_ARG;
+    if (mode == FGS_SHRINK_OFF) {
+        c->shrink = mode;
+        return FGS_OK;
+    }
+    if (mode != FGS_SHRINK_ON) return fail(c, FGS_ERR_ARG, "unknown shrink mode %d", mode);
+    if (!std::isfinite(tau) || !(tau > 0) || !std::isfinite(ln_tau))
+        return fail(c, FGS_ERR_ARG, "tau %g / ln_tau %g invalid", (double)tau, (double)ln_tau);
+    c->shrink = mode;
+    c->tau = tau;
+    c->ln_tau = ln_tau;
+    return FGS_OK;
+}
+
+int fgs_filter(fgs_ctx* c, void* stream, uint32_t* sel_out, uint32_t cap, uint32_t* M_out,
+               int out_is_device)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!sel_out || !M_out) return fail(c, FGS_ERR_ARG, "null output");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const DevCamera dc = make_devcam(c, false);
+    launch_frame_begin(c->st, c->ranges, dc.tiles_x * dc.tiles_y, s);
+    launch_filter_pred(c->tree, dc, c->pbits, c->sms * c->occ_pred, s);
+    launch_filter_anc_compact(c->tree, c->pbits, c->sel, c->lb_compact, c->st, c->sms * c->occ_anc, s);
+    FGS_CUDA(c, cudaGetLastError());
+    c->have_frame = false;
+    if (out_is_device) {
+        const size_t n = std::min<size_t>(cap, c->tree.n);
+        if (n) FGS_CUDA(c, cudaMemcpyAsync(sel_out, c->sel, n * 4, cudaMemcpyDeviceToDevice, s));
+        FGS_CUDA(c, cudaMemcpyAsync(M_out, &c->st->M, 4, cudaMemcpyDeviceToDevice, s));
+        return FGS_OK;
+    }
+    if ((r = read_state(c, s))) return r;
+    const uint32_t M = c->st_host->M;
+    *M_out = M;
+    const size_t n = std::min<size_t>(cap, M);
+    if (n) FGS_CUDA(c, cudaMemcpy(sel_out, c->sel, n * 4, cudaMemcpyDeviceToHost));
+    if ((r = latched_status(c))) {
+        clear_status(c, s);
+        return r;
+    }
+    if (M > cap) return fail(c, FGS_ERR_CAPACITY, "selection of %u exceeds cap %u", M, cap);
+    return FGS_OK;
+}
+
+int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_is_device,
+               uint32_t flags, fgs_stats* st)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!rgb_out) return fail(c, FGS_ERR_ARG, "null rgb output");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const DevCamera dc = make_devcam(c, false);
+    cudaEvent_t* ev = nullptr;
+    if (flags & FGS_RENDER_STAGE_EVENTS) {
+        if (!c->ev_ready) {
+            for (int i = 0; i < kEventSlots; ++i)
+                for (int k = 0; k <= kStages; ++k) FGS_CUDA(c, cudaEventCreate(&c->ev[i][k]));
+            c->ev_ready = true;
+        }
+        ev = c->ev[c->ev_count % kEventSlots];
+        ++c->ev_count;
+    }
+    int launches = enqueue_front(c, dc, s, ev);
+    const size_t hw = (size_t)dc.width * dc.height;
+    float* rgb_dst = out_is_device ? rgb_out : c->img;
+    float* T_dst = out_is_device ? T_out : (T_out ? c->img + 3 * hw : nullptr);
+    launch_blend(dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, rgb_dst, T_dst, c->st, s);
+    ++launches;
+    if (ev) cudaEventRecord(ev[6], s);
+    FGS_CUDA(c, cudaGetLastError());
+    c->have_frame = true;
+    if (!out_is_device) {
+        FGS_CUDA(c, cudaMemcpyAsync(rgb_out, c->img, 3 * hw * 4, cudaMemcpyDeviceToHost, s));
+        if (T_out) FGS_CUDA(c, cudaMemcpyAsync(T_out, c->img + 3 * hw, hw * 4, cudaMemcpyDeviceToHost, s));
+    }
+    if (st) {
+        std::memset(st, 0, sizeof *st);
+        st->n_launches = (uint32_t)launches;
+    }
+    if ((flags & FGS_RENDER_STATS) || !out_is_device) {
+        if ((r = read_state(c, s))) return r;
+        if (st) {
+            st->n_selected = c->st_host->M;
+            st->n_pairs = c->st_host->n_pairs;
+            st->device_status = c->st_host->status;
+        }
+        if ((r = latched_status(c))) {
+            clear_status(c, s);
+            return r;
+        }
+    }
+    return FGS_OK;
+}
+
+int fgs_stage_times(fgs_ctx* c, int slot, float* ms_out)
+{
+    if (!c || !ms_out || slot < 0 || slot >= kEventSlots) return FGS_ERR_ARG;
+    if (!c->ev_ready || (uint64_t)slot >= c->ev_count)
+        return fail(c, FGS_ERR_ARG, "slot %d was never recorded", slot);
+    DeviceGuard g(c->device);
+    FGS_CUDA(c, cudaEventSynchronize(c->ev[slot][kStages]));
+    for (int k = 0; k < kStages; ++k)
+        FGS_CUDA(c, cudaEventElapsedTime(ms_out + k, c->ev[slot][k], c->ev[slot][k + 1]));
+    return FGS_OK;
+}
+
+int fgs_stage_count(const fgs_ctx* c, uint64_t* count_out)
+{
+    if (!c || !count_out) return FGS_ERR_ARG;
+    *count_out = c->ev_count;
+    return FGS_OK;
+}
+
+int fgs_get_pairs(fgs_ctx* c, void* stream, uint64_t* keys_out, uint32_t* vals_out, uint64_t cap,
+                  uint64_t* n_out, int out_is_device)
+{
+    if (!c || !n_out) return FGS_ERR_ARG;
+    if (!c->have_frame) return fail(c, FGS_ERR_STATE, "no frame rendered");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int r;
+    if ((r = read_state(c, s))) return r;
+    const uint64_t np = c->st_host->n_pairs;
+    *n_out = np;
+    const uint64_t n = std::min<uint64_t>(std::min<uint64_t>(np, c->pair_cap), cap);
+    const unsigned long long* k = c->sorted_in_1 ? c->keys1 : c->keys0;
+    const uint32_t* v = c->sorted_in_1 ? c->vals1 : c->vals0;
+    const cudaMemcpyKind kind = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (n && keys_out) FGS_CUDA(c, cudaMemcpyAsync(keys_out, k, n * 8, kind, s));
+    if (n && vals_out) FGS_CUDA(c, cudaMemcpyAsync(vals_out, v, n * 4, kind, s));
+    FGS_CUDA(c, cudaStreamSynchronize(s));
+    if ((r = latched_status(c))) return r;
+    if (np > cap) return fail(c, FGS_ERR_CAPACITY, "N_P %llu exceeds cap %llu", (unsigned long long)np,
+                              (unsigned long long)cap);
+    return FGS_OK;
+}
+
+int fgs_get_splats(fgs_ctx* c, void* stream, float* out, uint32_t cap, uint32_t* M_out,
+                   int out_is_device)
+{
+    if (!c || !M_out) return FGS_ERR_ARG;
+    if (!c->have_frame) return fail(c, FGS_ERR_STATE, "no frame rendered");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int r;
+    if ((r = read_state(c, s))) return r;
+    const uint32_t M = c->st_host->M;
+    *M_out = M;
+    const uint64_t n = std::min<uint64_t>(M, cap);
+    if (n && out)
+        FGS_CUDA(c, cudaMemcpyAsync(out, c->splat, n * kSplatStride * 4,
+                                    out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    FGS_CUDA(c, cudaStreamSynchronize(s));
+    if (M > cap) return fail(c, FGS_ERR_CAPACITY, "M %u exceeds cap %u", M, cap);
+    return FGS_OK;
+}
+
+int fgs_calibrate_view(fgs_ctx* c, void* stream, double* gbar_out, float* kpc_out, uint64_t kpc_cap,
+                       float* G_out, int out_is_device)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!gbar_out) return fail(c, FGS_ERR_ARG, "null gbar output");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const DevCamera dc = make_devcam(c, true);   // calibration uses the 3-sigma footprint
+    enqueue_front(c, dc, s, nullptr);
+    FGS_CUDA(c, cudaMemsetAsync(c->kpc, 0, c->pair_cap * 4, s));
+    launch_blend_kpc(dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, c->kpc, c->G,
+                     c->st, s);
+    FGS_CUDA(c, cudaGetLastError());
+    c->have_frame = true;
+    if ((r = read_state(c, s))) return r;
+    if ((r = latched_status(c))) {
+        clear_status(c, s);
+        return r;
+    }
+    const FrameState& h = *c->st_host;
+    *gbar_out = h.gtc_tiles ? h.gtc_sum / (double)h.gtc_tiles : NAN;   // Eq. 7
+    const cudaMemcpyKind kind = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const uint64_t np = std::min<uint64_t>(h.n_pairs, c->pair_cap);
+    if (kpc_out && np) FGS_CUDA(c, cudaMemcpyAsync(kpc_out, c->kpc, std::min(np, kpc_cap) * 4, kind, s));
+    if (G_out)
+        FGS_CUDA(c, cudaMemcpyAsync(G_out, c->G, (size_t)dc.tiles_x * dc.tiles_y * 4, kind, s));
+    FGS_CUDA(c, cudaStreamSynchronize(s));
+    return FGS_OK;
+}
+
+int fgs_calibrate_gtc(fgs_ctx* c, void* stream, const fgs_camera* views, int n_views, float lambda_G,
+                      double* gbar_views_out, float* tau_out, float* ln_tau_out)
+{
+    if (!c || !views || n_views < 1 || !tau_out || !ln_tau_out) return FGS_ERR_ARG;
+    if (!(lambda_G > 0) || !std::isfinite(lambda_G)) return fail(c, FGS_ERR_ARG, "lambda_G invalid");
+    double sum = 0.0;
+    int used = 0;
+    for (int v = 0; v < n_views; ++v) {
+        int r = fgs_set_camera(c, views + v);
+        if (r) return r;
+        double gbar = NAN;
+        r = fgs_calibrate_view(c, stream, &gbar, nullptr, 0, nullptr, 0);
+        if (r) return r;
+        if (gbar_views_out) gbar_views_out[v] = gbar;
+        if (std::isfinite(gbar)) {   // a view without any pair has no G_v
+            sum += gbar;
+            ++used;
+        }
+    }
+    if (used == 0) return fail(c, FGS_ERR_ARG, "no calibration view produced pairs");
+    const double G = sum / used;                                   // Eq. 8
+    *tau_out = (float)((double)lambda_G / G);
+    *ln_tau_out = (float)(std::log((double)lambda_G) - std::log(G));
+    return FGS_OK;
+}
+
+int fgs_eval_exp(const float* x, float* y, uint64_t n, void* stream)
+{
+    if ((!x || !y) && n) return FGS_ERR_ARG;
+    if (n == 0) return FGS_OK;
+    launch_eval_exp(x, y, n, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? FGS_OK : FGS_ERR_CUDA;
+}
+
+int fgs_sync(fgs_ctx* c, void* stream)
+{
+    if (!c) return FGS_ERR_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int r;
+    if ((r = read_state(c, s))) return r;
+    r = latched_status(c);
+    if (r) clear_status(c, s);
+    FGS_CUDA(c, cudaStreamSynchronize(s));
+    return r;
+}
+
+}  // extern "C"

@@ -1,0 +1,248 @@
+// Internal declarations of the FilterGS CUDA library (sm_103a).
+//
+// Decision-exact arithmetic: every value that decides an integer result
+// (frustum test, R&L predicate, tile rectangle, depth key, shrink radius,
+// blend skip/stop) is computed with explicitly rounded binary32 intrinsics
+// (__fmul_rn, __fadd_rn, ... never contracted into FMA) in one fixed order,
+// so that selections, keys and pair lists are reproducible bit for bit on any
+// IEEE machine that follows the same order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fgs {
+
+constexpr int kStages = 6;
+constexpr uint32_t kApPad = 0xFFFFFFFFu;
+constexpr int kSplatStride = 12;          // floats per splat record (48 B)
+constexpr int kSortTileItems = 16;        // keys per thread in a sort tile
+constexpr int kSortThreads = 256;
+constexpr int kSortTile = kSortTileItems * kSortThreads;   // 4096 keys
+constexpr int kMaxSortPasses = 6;         // 48 key bits: 32 depth + up to 16 tile bits
+constexpr int kFilterItems = 16;          // nodes per thread in the ancestor/compaction kernel
+constexpr int kFilterThreads = 256;
+constexpr int kFilterTile = kFilterItems * kFilterThreads;  // 4096 nodes
+constexpr int kProjThreads = 256;         // selected Gaussians per projection tile
+constexpr uint64_t kSpinLimit = 1ull << 24;   // bounded spin-waits
+
+// device status codes (mirrors FGS_ERR_* of the C ABI)
+constexpr int kErrCapacity = -4;
+constexpr int kErrTimeout = -5;
+
+struct DevCamera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float tan_half_x, tan_half_y;
+    float campos[3];
+    int32_t width, height;
+    // derived on the host (exact: products by powers of two, integer ceil)
+    int32_t tiles_x, tiles_y;
+    int32_t tile_w, tile_h;
+    int32_t tile_shift_x, tile_shift_y;
+    float tau_R;
+    int32_t shrink;
+    float tau, ln_tau;
+    float bg[3];
+    int32_t sort_passes;
+};
+
+// Tree on the device (SoA; arrays padded to a multiple of 128 nodes).
+struct DevTree {
+    uint32_t n;
+    uint32_t n_pad;
+    uint32_t depth;
+    uint32_t sh_degree;
+    uint32_t sh_stride;        // floats per node in sh (K*3 rounded up to 4)
+    const float* mu;           // [3][n_pad]
+    const float* cov;          // [6][n_pad]
+    const float* opacity;      // [n_pad]
+    const float* ln_opacity;   // [n_pad]
+    const float* sh;           // [n_pad][sh_stride]
+    const uint32_t* leaf_bits; // [n_pad/32]
+    const uint32_t* ap;        // [depth][n_pad]
+};
+
+// Per-frame device state (one per context).
+struct FrameState {
+    uint32_t epoch;            // bumped once per frame; tags look-back entries
+    uint32_t M;                // selected nodes
+    unsigned long long n_pairs;  // emitted pairs (true count, may exceed capacity)
+    uint32_t tickets[16];      // dynamic tile counters (one per kernel use)
+    int32_t status;            // latched error (0 = ok)
+    uint32_t status_info;
+    uint32_t hist[kMaxSortPasses][256];   // radix digit histograms
+    double gtc_sum;            // sum of per-tile GTC over tiles with pairs
+    uint32_t gtc_tiles;        // number of such tiles
+    uint32_t pad_;
+};
+
+// Ticket slots
+enum : int { kTicketCompact = 0, kTicketProject = 1, kTicketSortBase = 2 };
+
+// ---------------------------------------------------------------------
+// decision-exact binary32 helpers
+// ---------------------------------------------------------------------
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fd(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
+
+// e^x in binary32: Cody & Waite argument reduction (x = k ln2 + r with ln 2
+// split into a short leading part and a correction), the degree-7 Taylor
+// polynomial of e^r by Horner's rule, scaled by 2^k from exponent bits.
+// Explicitly rounded operations, so the bits do not depend on the compiler.
+__device__ __forceinline__ float exp_cw(float x)
+{
+    if (x < -87.0f) return 0.0f;
+    const float kf = rintf(fm(x, 1.44269504088896341f));
+    const float r = fs(fs(x, fm(kf, 0.693359375f)), fm(kf, -2.12194440e-4f));
+    float p = 1.98412698412698413e-4f;
+    p = fa(fm(p, r), 1.38888888888888889e-3f);
+    p = fa(fm(p, r), 8.33333333333333333e-3f);
+    p = fa(fm(p, r), 4.16666666666666667e-2f);
+    p = fa(fm(p, r), 1.66666666666666667e-1f);
+    p = fa(fm(p, r), 0.5f);
+    p = fa(fm(p, r), 1.0f);
+    p = fa(fm(p, r), 1.0f);
+    const int k = (int)kf;
+    return fm(p, __int_as_float((k + 127) << 23));
+}
+
+// Screen-space view of one node: camera-space centre, frustum test and the
+// 2D covariance J W Sigma W^T J^T + 0.3 I (EWA), larger eigenvalue.
+struct NodeView {
+    bool in_frustum;
+    float vx, vy, vz;
+    float a, b, c;
+    float lam;
+};
+
+__device__ __forceinline__ void camera_space(const DevCamera& cam, float mx, float my, float mz,
+                                             float& vx, float& vy, float& vz)
+{
+    vx = fa(fa(fa(fm(cam.R[0], mx), fm(cam.R[1], my)), fm(cam.R[2], mz)), cam.t[0]);
+    vy = fa(fa(fa(fm(cam.R[3], mx), fm(cam.R[4], my)), fm(cam.R[5], mz)), cam.t[1]);
+    vz = fa(fa(fa(fm(cam.R[6], mx), fm(cam.R[7], my)), fm(cam.R[8], mz)), cam.t[2]);
+}
+
+// Frustum: depth above 0.2 and the centre within 1.3x the half-FOV tangents.
+__device__ __forceinline__ bool frustum_test(const DevCamera& cam, float vx, float vy, float vz,
+                                             float& txtz, float& tytz)
+{
+    if (!(vz > 0.2f)) return false;
+    const float limx = fm(1.3f, cam.tan_half_x);
+    const float limy = fm(1.3f, cam.tan_half_y);
+    txtz = fd(vx, vz);
+    tytz = fd(vy, vz);
+    return txtz >= -limx && txtz <= limx && tytz >= -limy && tytz <= limy;
+}
+
+// Sigma_2D and lambda_max for an in-frustum node.  s = {xx, xy, xz, yy, yz, zz}.
+__device__ __forceinline__ void ewa_cov2d(const DevCamera& cam, float vz, float txtz, float tytz,
+                                          const float s[6], float& a, float& b, float& c, float& lam)
+{
+    const float limx = fm(1.3f, cam.tan_half_x);
+    const float limy = fm(1.3f, cam.tan_half_y);
+    const float clx = fminf(limx, fmaxf(-limx, txtz));
+    const float cly = fminf(limy, fmaxf(-limy, tytz));
+    const float txc = fm(clx, vz);
+    const float tyc = fm(cly, vz);
+    const float tz2 = fm(vz, vz);
+    const float j00 = fd(cam.fx, vz);
+    const float j11 = fd(cam.fy, vz);
+    const float j02 = -fd(fm(cam.fx, txc), tz2);
+    const float j12 = -fd(fm(cam.fy, tyc), tz2);
+    const float* R = cam.R;
+    const float m00 = fa(fm(j00, R[0]), fm(j02, R[6]));
+    const float m01 = fa(fm(j00, R[1]), fm(j02, R[7]));
+    const float m02 = fa(fm(j00, R[2]), fm(j02, R[8]));
+    const float m10 = fa(fm(j11, R[3]), fm(j12, R[6]));
+    const float m11 = fa(fm(j11, R[4]), fm(j12, R[7]));
+    const float m12 = fa(fm(j11, R[5]), fm(j12, R[8]));
+    const float s00 = s[0], s01 = s[1], s02 = s[2], s11 = s[3], s12 = s[4], s22 = s[5];
+    const float u0 = fa(fa(fm(s00, m00), fm(s01, m01)), fm(s02, m02));
+    const float u1 = fa(fa(fm(s01, m00), fm(s11, m01)), fm(s12, m02));
+    const float u2 = fa(fa(fm(s02, m00), fm(s12, m01)), fm(s22, m02));
+    const float w0 = fa(fa(fm(s00, m10), fm(s01, m11)), fm(s02, m12));
+    const float w1 = fa(fa(fm(s01, m10), fm(s11, m11)), fm(s12, m12));
+    const float w2 = fa(fa(fm(s02, m10), fm(s12, m11)), fm(s22, m12));
+    a = fa(fa(fa(fm(m00, u0), fm(m01, u1)), fm(m02, u2)), 0.3f);
+    b = fa(fa(fm(m10, u0), fm(m11, u1)), fm(m12, u2));
+    c = fa(fa(fa(fm(m10, w0), fm(m11, w1)), fm(m12, w2)), 0.3f);
+    const float det = fs(fm(a, c), fm(b, b));
+    const float mid = fm(0.5f, fa(a, c));
+    float disc = fs(fm(mid, mid), det);
+    disc = disc > 0.1f ? disc : 0.1f;
+    lam = fa(mid, fsq(disc));
+}
+
+// ---------------------------------------------------------------------
+// bounded look-back / spin helpers
+// ---------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// look-back entry: [63:34] epoch (30 bits) | [33:32] flag | [31:0] value
+constexpr unsigned long long kFlagAgg = 1ull;
+constexpr unsigned long long kFlagIncl = 2ull;
+__device__ __forceinline__ unsigned long long lb_pack(uint32_t epoch, unsigned long long flag, uint32_t v)
+{
+    return ((unsigned long long)(epoch & 0x3FFFFFFFu) << 34) | (flag << 32) | v;
+}
+
+__device__ __forceinline__ void set_status(FrameState* st, int code, uint32_t info)
+{
+    if (atomicCAS(&st->status, 0, code) == 0) st->status_info = info;
+}
+
+// ---------------------------------------------------------------------
+// host launchers (one per kernel family)
+// ---------------------------------------------------------------------
+// Resident blocks per SM of each persistent / grid-stride kernel (occupancy API).
+int occ_filter_pred();
+int occ_filter_anc();
+int occ_project();
+int occ_sort_hist();
+int occ_sort_pass();
+int occ_tile_ranges();
+size_t sort_smem_bytes();
+
+// All launchers enqueue on `s` and read counts (M, N_P) from device memory,
+// so a frame needs no host synchronisation.
+void launch_frame_begin(FrameState* st, uint2* ranges, int n_tiles, cudaStream_t s);
+void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits, int blocks,
+                        cudaStream_t s);
+void launch_filter_anc_compact(const DevTree& t, const uint32_t* pbits, uint32_t* sel,
+                               unsigned long long* lookback, FrameState* st, int blocks,
+                               cudaStream_t s);
+void launch_project_emit(const DevTree& t, const DevCamera& cam, const uint32_t* sel,
+                         float* splat, unsigned long long* keys, uint32_t* vals,
+                         unsigned long long cap, unsigned long long* lookback, FrameState* st,
+                         int blocks, cudaStream_t s);
+// Sorts keys0/vals0 in place through keys1/vals1 (an even number of passes
+// leaves the result in keys0/vals0; an odd number in keys1/vals1).
+int launch_sort(unsigned long long* keys0, uint32_t* vals0, unsigned long long* keys1,
+                uint32_t* vals1, unsigned long long cap, int passes,
+                unsigned long long* lookback, FrameState* st, int hist_blocks, int sort_blocks,
+                cudaStream_t s);
+void launch_tile_ranges(const unsigned long long* keys, unsigned long long cap, uint2* ranges,
+                        const FrameState* st, int blocks, cudaStream_t s);
+void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
+                  const float* splat, float* rgb, float* T, FrameState* st, cudaStream_t s);
+void launch_blend_kpc(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
+                      const float* splat, float* kpc, float* G, FrameState* st, cudaStream_t s);
+
+void launch_eval_exp(const float* x, float* y, uint64_t n, cudaStream_t s);
+
+}  // namespace fgs

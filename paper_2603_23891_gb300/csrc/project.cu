@@ -1,0 +1,253 @@
+// Projection, SH colour, scene-adaptive shrinking and Gaussian-tile key
+// emission (§3.1, §3.3) on sm_103a.
+//
+// One thread per selected Gaussian, 256 per tile, persistent blocks taking
+// tiles from a ticket counter.  Each thread computes the splat record (centre,
+// conic, log-domain skip threshold, opacity, depth, colour, footprint radius),
+// its tile rectangle and pair count; a block scan plus a decoupled look-back
+// across tiles gives every Gaussian its first pair slot, so pairs are emitted
+// in selection order (the tie-break of the stable (tile | depth) sort).
+#include "fgs_internal.cuh"
+
+namespace fgs {
+
+namespace {
+
+// Real spherical harmonics (Condon-Shortley phase), Cartesian form, normalisation
+// constants from their closed forms: l=0 1/(2 sqrt(pi)); l=1 sqrt(3/(4 pi));
+// l=2 sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4; l=3 sqrt(35/(2 pi))/4,
+// sqrt(105/pi)/2, sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4.
+constexpr float kY00 = 0.28209479177387814f;
+constexpr float kY1 = 0.48860251190291992f;
+constexpr float kY2a = 1.0925484305920792f;
+constexpr float kY2b = 0.31539156525252005f;
+constexpr float kY2c = 0.54627421529603959f;
+constexpr float kY3a = 0.59004358992664352f;
+constexpr float kY3b = 2.8906114426405538f;
+constexpr float kY3c = 0.45704579946446572f;
+constexpr float kY3d = 0.37317633259011540f;
+constexpr float kY3e = 1.4453057213202769f;
+
+__device__ __forceinline__ void sh_colour(const float* __restrict__ c, int deg, float x, float y,
+                                          float z, float rgb[3])
+{
+    float Y[16];
+    Y[0] = kY00;
+    int K = 1;
+    if (deg >= 1) {
+        Y[1] = -kY1 * y;
+        Y[2] = kY1 * z;
+        Y[3] = -kY1 * x;
+        K = 4;
+    }
+    if (deg >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kY2a * x * y;
+        Y[5] = -kY2a * y * z;
+        Y[6] = kY2b * (2.0f * zz - xx - yy);
+        Y[7] = -kY2a * x * z;
+        Y[8] = kY2c * (xx - yy);
+        K = 9;
+        if (deg >= 3) {
+            Y[9] = -kY3a * y * (3.0f * xx - yy);
+            Y[10] = kY3b * x * y * z;
+            Y[11] = -kY3c * y * (4.0f * zz - xx - yy);
+            Y[12] = kY3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+            Y[13] = -kY3c * x * (4.0f * zz - xx - yy);
+            Y[14] = kY3e * z * (xx - yy);
+            Y[15] = -kY3a * x * (xx - 3.0f * yy);
+            K = 16;
+        }
+    }
+    float r = 0.5f, g = 0.5f, b = 0.5f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (k < K) {
+            r += Y[k] * c[3 * k + 0];
+            g += Y[k] * c[3 * k + 1];
+            b += Y[k] * c[3 * k + 2];
+        }
+    }
+    rgb[0] = fmaxf(r, 0.0f);
+    rgb[1] = fmaxf(g, 0.0f);
+    rgb[2] = fmaxf(b, 0.0f);
+}
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi)
+{
+    v = v < lo ? lo : v;
+    return v > hi ? hi : v;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
+    DevTree t, DevCamera cam, const uint32_t* __restrict__ sel, float* __restrict__ splat,
+    unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals, unsigned long long cap,
+    unsigned long long* lookback, FrameState* st)
+{
+    __shared__ uint32_t s_warp_tot[kProjThreads / 32];
+    __shared__ uint32_t s_tile, s_prefix;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t M = st->M;
+    const uint32_t n_tiles = (M + kProjThreads - 1) / kProjThreads;
+    const uint32_t tag = st->epoch * 16u + 1u;
+    const float fw = (float)cam.tile_w, fh = (float)cam.tile_h;
+    const float ftx = (float)cam.tiles_x, fty = (float)cam.tiles_y;
+
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&st->tickets[kTicketProject], 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= n_tiles) break;
+        const uint32_t m = tile * kProjThreads + tid;
+        uint32_t cnt = 0;
+        int32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        uint32_t dbits = 0;
+        if (m < M) {
+            const uint32_t n = __ldg(sel + m);
+            const size_t np = t.n_pad;
+            const float mx = __ldg(t.mu + n), my = __ldg(t.mu + np + n), mz = __ldg(t.mu + 2 * np + n);
+            float vx, vy, vz, txtz = 0.0f, tytz = 0.0f;
+            camera_space(cam, mx, my, mz, vx, vy, vz);
+            const bool inf = frustum_test(cam, vx, vy, vz, txtz, tytz);
+            float s6[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) s6[q] = __ldg(t.cov + q * np + n);
+            float a = 0.0f, b = 0.0f, c = 0.0f, lam = 0.0f;
+            if (inf) ewa_cov2d(cam, vz, txtz, tytz, s6, a, b, c, lam);
+            const float u = fa(fm(cam.fx, fd(vx, vz)), cam.cx);
+            const float v = fa(fm(cam.fy, fd(vy, vz)), cam.cy);
+            const float det = fs(fm(a, c), fm(b, b));
+            const float a0 = __ldg(t.opacity + n);
+            const float ln_a0 = __ldg(t.ln_opacity + n);
+            const float lthr = fs(-5.5412635451584258f, ln_a0);   // -ln 255 - ln alpha0
+
+            // colour: direction from the camera centre, SH basis, + 0.5, clamp at 0
+            float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
+            const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= il; dy *= il; dz *= il;
+            float rgb[3];
+            {
+                const float* c0 = t.sh + (size_t)n * t.sh_stride;
+                float coef[48];
+                const int nv = t.sh_stride >> 2;
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                    if (q < nv) {
+                        const float4 f = __ldg(reinterpret_cast<const float4*>(c0) + q);
+                        coef[4 * q] = f.x; coef[4 * q + 1] = f.y; coef[4 * q + 2] = f.z; coef[4 * q + 3] = f.w;
+                    } else {
+                        coef[4 * q] = coef[4 * q + 1] = coef[4 * q + 2] = coef[4 * q + 3] = 0.0f;
+                    }
+                }
+                sh_colour(coef, (int)t.sh_degree, dx, dy, dz, rgb);
+            }
+            float A = 0.0f, B = 0.0f, C = 0.0f, radius = 0.0f;
+            if (inf && det > 0.0f) {
+                A = fd(c, det);
+                B = fd(-b, det);
+                C = fd(a, det);
+                // 3-sigma radius, or the radius where alpha0 e^{-r^2/(2 lambda)} = tau,
+                // capped at 3 sigma; alpha0 <= tau emits nothing (§3.3)
+                const float r3 = fm(3.0f, fsq(lam));
+                float r = r3;
+                bool drop = false;
+                if (cam.shrink) {
+                    const float g = fm(2.0f, fs(ln_a0, cam.ln_tau));
+                    if (!(g > 0.0f)) drop = true;
+                    else if (g < 9.0f) r = fsq(fm(lam, g));
+                }
+                if (!drop) {
+                    radius = r;
+                    const float fx0 = clampf(floorf(fd(fs(u, r), fw)), 0.0f, ftx);
+                    const float fx1 = clampf(fa(floorf(fd(fa(u, r), fw)), 1.0f), 0.0f, ftx);
+                    const float fy0 = clampf(floorf(fd(fs(v, r), fh)), 0.0f, fty);
+                    const float fy1 = clampf(fa(floorf(fd(fa(v, r), fh)), 1.0f), 0.0f, fty);
+                    x0 = (int32_t)fx0; x1 = (int32_t)fx1; y0 = (int32_t)fy0; y1 = (int32_t)fy1;
+                    if (x1 > x0 && y1 > y0) cnt = (uint32_t)((x1 - x0) * (y1 - y0));
+                }
+            }
+            dbits = __float_as_uint(vz);
+            float4* out = reinterpret_cast<float4*>(splat + (size_t)m * kSplatStride);
+            out[0] = make_float4(u, v, A, B);
+            out[1] = make_float4(C, lthr, a0, vz);
+            out[2] = make_float4(rgb[0], rgb[1], rgb[2], radius);
+        }
+        // block exclusive scan of cnt
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t up = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += up;
+        }
+        if (lane == 31) s_warp_tot[warp] = incl;
+        __syncthreads();
+        uint32_t off = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kProjThreads / 32; ++w) {
+            const uint32_t tw = s_warp_tot[w];
+            off += (w < (int)warp) ? tw : 0u;
+            total += tw;
+        }
+        if (tid == 0) {
+            uint32_t prefix = 0;
+            if (tile == 0) {
+                st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, total));
+            } else {
+                st_release_u64(lookback + tile, lb_pack(tag, kFlagAgg, total));
+                int j = (int)tile - 1;
+                uint64_t spins = 0;
+                while (j >= 0) {
+                    const unsigned long long e = ld_acquire_u64(lookback + j);
+                    const unsigned long long flag = (e >> 32) & 3ull;
+                    if ((uint32_t)(e >> 34) != (tag & 0x3FFFFFFFu) || flag == 0) {
+                        if (++spins > kSpinLimit) { set_status(st, kErrTimeout, 0x200u); break; }
+                        continue;
+                    }
+                    prefix += (uint32_t)e;
+                    if (flag == kFlagIncl) break;
+                    --j;
+                }
+                st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, prefix + total));
+            }
+            s_prefix = prefix;
+            if (tile == n_tiles - 1) st->n_pairs = (unsigned long long)prefix + total;
+        }
+        __syncthreads();
+        if (cnt) {
+            const unsigned long long first = (unsigned long long)s_prefix + off + incl - cnt;
+            if (first + cnt > cap) set_status(st, kErrCapacity, 0x300u);
+            unsigned long long idx = first;
+            for (int32_t ty = y0; ty < y1; ++ty) {
+                for (int32_t tx = x0; tx < x1; ++tx, ++idx) {
+                    if (idx < cap) {
+                        const unsigned long long tl = (unsigned long long)(ty * cam.tiles_x + tx);
+                        keys[idx] = (tl << 32) | dbits;
+                        vals[idx] = m;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+void launch_project_emit(const DevTree& t, const DevCamera& cam, const uint32_t* sel,
+                         float* splat, unsigned long long* keys, uint32_t* vals,
+                         unsigned long long cap, unsigned long long* lookback, FrameState* st,
+                         int blocks, cudaStream_t s)
+{
+    if (blocks < 1) blocks = 1;
+    project_emit_kernel<<<blocks, kProjThreads, 0, s>>>(t, cam, sel, splat, keys, vals, cap,
+                                                        lookback, st);
+}
+
+int occ_project()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, project_emit_kernel, kProjThreads, 0);
+    return b > 0 ? b : 1;
+}
+
+}  // namespace fgs

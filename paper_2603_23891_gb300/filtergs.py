@@ -1,0 +1,412 @@
+"""Python binding of the FilterGS C ABI (``include/filtergs.h``).
+
+Argument marshalling only: every step of the render path runs in the CUDA
+library ``libfiltergs.so``.  Importing this module loads the library and fails
+loudly if it is missing; there is no CPU path.  Functions keep the C names
+(``fgs_create``, ``fgs_render`` ...); ``Renderer`` bundles them with torch
+device tensors and the current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfiltergs.so")
+
+FGS_OK = 0
+FGS_ERR_ARG = -1
+FGS_ERR_TREE = -2
+FGS_ERR_CUDA = -3
+FGS_ERR_CAPACITY = -4
+FGS_ERR_TIMEOUT = -5
+FGS_ERR_STATE = -6
+FGS_ERR_NOMEM = -7
+FGS_SHRINK_OFF = 0
+FGS_SHRINK_ON = 1
+FGS_RENDER_STATS = 1
+FGS_RENDER_STAGE_EVENTS = 2
+FGS_N_STAGES = 6
+STAGE_NAMES = ["filter_rl", "ancestor_compact", "project_keys", "sort", "tile_ranges", "blend"]
+SPLAT_FIELDS = ["u", "v", "A", "B", "C", "lthr", "a0", "depth", "r", "g", "b", "radius"]
+
+EXPORTED = ["fgs_version", "fgs_create", "fgs_destroy", "fgs_last_error", "fgs_set_params",
+            "fgs_load_tree", "fgs_set_camera", "fgs_set_shrink", "fgs_filter", "fgs_render",
+            "fgs_stage_times", "fgs_stage_count", "fgs_get_pairs", "fgs_get_splats",
+            "fgs_calibrate_view", "fgs_calibrate_gtc", "fgs_sync", "fgs_validate_tree",
+            "fgs_eval_exp"]
+
+
+class FgsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"filtergs error {code}: {msg}")
+        self.code = code
+
+
+class fgs_tree(C.Structure):
+    _fields_ = [("n_nodes", C.c_uint32), ("depth", C.c_uint32), ("sh_degree", C.c_uint32),
+                ("reserved", C.c_uint32), ("mu", C.c_void_p), ("cov", C.c_void_p),
+                ("opacity", C.c_void_p), ("ln_opacity", C.c_void_p), ("sh", C.c_void_p),
+                ("parent", C.c_void_p), ("is_leaf", C.c_void_p), ("ap", C.c_void_p)]
+
+
+class fgs_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("tan_half_x", C.c_float),
+                ("tan_half_y", C.c_float), ("campos", C.c_float * 3), ("width", C.c_int32),
+                ("height", C.c_int32)]
+
+
+class fgs_params(C.Structure):
+    _fields_ = [("tau_R", C.c_float), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
+                ("bg", C.c_float * 3), ("pair_capacity", C.c_uint64)]
+
+
+class fgs_stats(C.Structure):
+    _fields_ = [("n_selected", C.c_uint32), ("reserved", C.c_uint32), ("n_pairs", C.c_uint64),
+                ("n_launches", C.c_uint32), ("device_status", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libfiltergs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2603_23891_gb300.build` (no CPU fallback exists)")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, u32, u64, f32 = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_float
+    sig = {
+        "fgs_version": ([], i32),
+        "fgs_create": ([C.POINTER(vp), i32], i32),
+        "fgs_destroy": ([vp], i32),
+        "fgs_last_error": ([vp], C.c_char_p),
+        "fgs_set_params": ([vp, C.POINTER(fgs_params)], i32),
+        "fgs_load_tree": ([vp, C.POINTER(fgs_tree)], i32),
+        "fgs_set_camera": ([vp, C.POINTER(fgs_camera)], i32),
+        "fgs_set_shrink": ([vp, i32, f32, f32], i32),
+        "fgs_filter": ([vp, vp, vp, u32, vp, i32], i32),
+        "fgs_render": ([vp, vp, vp, vp, i32, u32, C.POINTER(fgs_stats)], i32),
+        "fgs_stage_times": ([vp, i32, vp], i32),
+        "fgs_stage_count": ([vp, C.POINTER(u64)], i32),
+        "fgs_get_pairs": ([vp, vp, vp, vp, u64, C.POINTER(u64), i32], i32),
+        "fgs_get_splats": ([vp, vp, vp, u32, C.POINTER(u32), i32], i32),
+        "fgs_calibrate_view": ([vp, vp, C.POINTER(C.c_double), vp, u64, vp, i32], i32),
+        "fgs_calibrate_gtc": ([vp, vp, vp, i32, f32, vp, C.POINTER(f32), C.POINTER(f32)], i32),
+        "fgs_sync": ([vp, vp], i32),
+        "fgs_validate_tree": ([C.POINTER(fgs_tree), C.c_char_p, C.c_size_t], i32),
+        "fgs_eval_exp": ([vp, vp, u64, vp], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(ctx, code):
+    if code != FGS_OK:
+        msg = lib().fgs_last_error(ctx)
+        raise FgsError(code, msg.decode() if msg else "")
+    return code
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------- C-named wrappers
+
+def fgs_version() -> int:
+    return lib().fgs_version()
+
+
+def fgs_create(device: int = 0):
+    h = C.c_void_p()
+    code = lib().fgs_create(C.byref(h), device)
+    if code != FGS_OK:
+        raise FgsError(code, f"fgs_create(device={device}) failed")
+    return h
+
+
+def fgs_destroy(ctx) -> None:
+    lib().fgs_destroy(ctx)
+
+
+def fgs_last_error(ctx) -> str:
+    m = lib().fgs_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def make_params(tau_R=3.0, tile=(16, 16), bg=(0.0, 0.0, 0.0), pair_capacity=0) -> fgs_params:
+    p = fgs_params()
+    p.tau_R = tau_R
+    p.tile_w, p.tile_h = tile
+    p.bg[:] = list(bg)
+    p.pair_capacity = int(pair_capacity)
+    return p
+
+
+def fgs_set_params(ctx, p: fgs_params):
+    return _check(ctx, lib().fgs_set_params(ctx, C.byref(p)))
+
+
+class _TreeArrays:
+    """Host copies in the ABI layout, kept alive while the struct is used."""
+
+    def __init__(self, tree):
+        self.mu = np.ascontiguousarray(tree.mu, np.float32)
+        self.cov = np.ascontiguousarray(tree.cov, np.float32)
+        self.opacity = np.ascontiguousarray(tree.opacity, np.float32)
+        self.ln_opacity = np.ascontiguousarray(tree.ln_opacity, np.float32)
+        self.sh = np.ascontiguousarray(tree.sh, np.float32)
+        self.parent = np.ascontiguousarray(tree.parent, np.int32)
+        self.is_leaf = np.ascontiguousarray(tree.is_leaf, np.uint8)
+        self.ap = np.ascontiguousarray(tree.ap, np.uint32)
+        s = fgs_tree()
+        s.n_nodes = self.parent.shape[0]
+        s.depth = self.ap.shape[0]
+        s.sh_degree = tree.sh_degree
+        for k in ("mu", "cov", "opacity", "ln_opacity", "sh", "parent", "is_leaf", "ap"):
+            setattr(s, k, getattr(self, k).ctypes.data)
+        self.struct = s
+
+
+def fgs_validate_tree(tree):
+    """(status, message) of the host-side tree validation (no GPU needed)."""
+    arr = tree if isinstance(tree, _TreeArrays) else _TreeArrays(tree)
+    buf = C.create_string_buffer(512)
+    code = lib().fgs_validate_tree(C.byref(arr.struct), buf, 512)
+    return code, buf.value.decode()
+
+
+def fgs_eval_exp(x, y, stream=None):
+    """Blend exp on device tensors x -> y (float32, same length)."""
+    n = x.numel()
+    code = lib().fgs_eval_exp(_ptr(x), _ptr(y), n, stream)
+    if code != FGS_OK:
+        raise FgsError(code, "fgs_eval_exp failed")
+
+
+def fgs_load_tree(ctx, tree):
+    arr = _TreeArrays(tree)
+    return _check(ctx, lib().fgs_load_tree(ctx, C.byref(arr.struct)))
+
+
+def make_camera(cam) -> fgs_camera:
+    c = fgs_camera()
+    c.R[:] = [float(x) for x in np.asarray(cam.R, np.float32).ravel()]
+    c.t[:] = [float(x) for x in np.asarray(cam.t, np.float32)]
+    c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
+    c.tan_half_x, c.tan_half_y = cam.tan_half_x, cam.tan_half_y
+    c.campos[:] = [float(x) for x in np.asarray(cam.campos, np.float32)]
+    c.width, c.height = cam.width, cam.height
+    return c
+
+
+def fgs_set_camera(ctx, cam):
+    c = cam if isinstance(cam, fgs_camera) else make_camera(cam)
+    return _check(ctx, lib().fgs_set_camera(ctx, C.byref(c)))
+
+
+def fgs_set_shrink(ctx, mode: int, tau: float = 0.0, ln_tau: float = 0.0):
+    return _check(ctx, lib().fgs_set_shrink(ctx, mode, tau, ln_tau))
+
+
+def fgs_filter(ctx, stream, sel_out, cap: int, M_out, out_is_device: int):
+    return _check(ctx, lib().fgs_filter(ctx, stream, _ptr(sel_out), cap, _ptr(M_out), out_is_device))
+
+
+def fgs_render(ctx, stream, rgb_out, T_out, out_is_device: int, flags: int = 0, stats=None):
+    return _check(ctx, lib().fgs_render(ctx, stream, _ptr(rgb_out), _ptr(T_out), out_is_device,
+                                        flags, C.byref(stats) if stats is not None else None))
+
+
+def fgs_stage_times(ctx, slot: int) -> np.ndarray:
+    out = np.zeros(FGS_N_STAGES, np.float32)
+    _check(ctx, lib().fgs_stage_times(ctx, slot, _ptr(out)))
+    return out
+
+
+def fgs_stage_count(ctx) -> int:
+    n = C.c_uint64()
+    _check(ctx, lib().fgs_stage_count(ctx, C.byref(n)))
+    return int(n.value)
+
+
+def fgs_get_pairs(ctx, stream, keys_out, vals_out, cap: int, out_is_device: int) -> int:
+    n = C.c_uint64()
+    _check(ctx, lib().fgs_get_pairs(ctx, stream, _ptr(keys_out), _ptr(vals_out), cap, C.byref(n),
+                                    out_is_device))
+    return int(n.value)
+
+
+def fgs_get_splats(ctx, stream, out, cap: int, out_is_device: int) -> int:
+    m = C.c_uint32()
+    _check(ctx, lib().fgs_get_splats(ctx, stream, _ptr(out), cap, C.byref(m), out_is_device))
+    return int(m.value)
+
+
+def fgs_calibrate_view(ctx, stream, kpc_out=None, kpc_cap: int = 0, G_out=None,
+                       out_is_device: int = 0) -> float:
+    g = C.c_double()
+    _check(ctx, lib().fgs_calibrate_view(ctx, stream, C.byref(g), _ptr(kpc_out), kpc_cap,
+                                         _ptr(G_out), out_is_device))
+    return float(g.value)
+
+
+def fgs_calibrate_gtc(ctx, stream, cams, lambda_G: float = 0.2):
+    arr = (fgs_camera * len(cams))(*[c if isinstance(c, fgs_camera) else make_camera(c) for c in cams])
+    gb = np.zeros(len(cams), np.float64)
+    tau, ln_tau = C.c_float(), C.c_float()
+    _check(ctx, lib().fgs_calibrate_gtc(ctx, stream, C.cast(arr, C.c_void_p), len(cams), lambda_G,
+                                        _ptr(gb), C.byref(tau), C.byref(ln_tau)))
+    return float(tau.value), float(ln_tau.value), gb
+
+
+def fgs_sync(ctx, stream):
+    return _check(ctx, lib().fgs_sync(ctx, stream))
+
+
+# ---------------------------------------------------------------- convenience
+
+def _torch():
+    import torch
+    return torch
+
+
+class Renderer:
+    """One context on one CUDA device; outputs are torch CUDA tensors."""
+
+    def __init__(self, device: int = 0, tau_R: float = 3.0, tile=(16, 16), bg=(0.0, 0.0, 0.0),
+                 pair_capacity: int = 0):
+        torch = _torch()
+        self.device = device
+        self.torch_device = torch.device("cuda", device)
+        self.ctx = fgs_create(device)
+        self.params = make_params(tau_R, tile, bg, pair_capacity)
+        fgs_set_params(self.ctx, self.params)
+        self.cam = None
+        self.tree = None
+
+    def close(self):
+        if self.ctx is not None:
+            fgs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream(self):
+        torch = _torch()
+        return C.c_void_p(torch.cuda.current_stream(self.torch_device).cuda_stream)
+
+    def set_params(self, tau_R=None, tile=None, bg=None, pair_capacity=None):
+        p = self.params
+        if tau_R is not None:
+            p.tau_R = tau_R
+        if tile is not None:
+            p.tile_w, p.tile_h = tile
+        if bg is not None:
+            p.bg[:] = list(bg)
+        p.pair_capacity = int(pair_capacity) if pair_capacity else 0
+        fgs_set_params(self.ctx, p)
+
+    def load_tree(self, tree):
+        fgs_load_tree(self.ctx, tree)
+        self.tree = tree
+
+    def set_camera(self, cam):
+        fgs_set_camera(self.ctx, cam)
+        self.cam = cam
+
+    def shrink(self, tau=None, ln_tau=None):
+        if tau is None:
+            fgs_set_shrink(self.ctx, FGS_SHRINK_OFF)
+        else:
+            fgs_set_shrink(self.ctx, FGS_SHRINK_ON, tau, ln_tau)
+
+    def filter(self):
+        """Selected node ids (ascending) as a host numpy array."""
+        n = self.tree.n
+        out = np.zeros(max(n, 1), np.uint32)
+        M = np.zeros(1, np.uint32)
+        fgs_filter(self.ctx, self.stream, out, n, M, 0)
+        return out[: int(M[0])].copy()
+
+    def render(self, rgb=None, T=None, stats=False, stage_events=False):
+        torch = _torch()
+        H, W = self.cam.height, self.cam.width
+        if rgb is None:
+            rgb = torch.empty((3, H, W), dtype=torch.float32, device=self.torch_device)
+        if T is None:
+            T = torch.empty((H, W), dtype=torch.float32, device=self.torch_device)
+        st = fgs_stats()
+        flags = (FGS_RENDER_STATS if stats else 0) | (FGS_RENDER_STAGE_EVENTS if stage_events else 0)
+        fgs_render(self.ctx, self.stream, rgb, T, 1, flags, st)
+        return rgb, T, st
+
+    def render_host(self, rgb_host: np.ndarray, T_host=None, stats=False):
+        st = fgs_stats()
+        fgs_render(self.ctx, self.stream, rgb_host, T_host, 0, FGS_RENDER_STATS if stats else 0, st)
+        return st
+
+    def n_pairs(self) -> int:
+        """N_P of the last frame (a zero-capacity query of fgs_get_pairs)."""
+        n = C.c_uint64()
+        code = lib().fgs_get_pairs(self.ctx, self.stream, None, None, 0, C.byref(n), 0)
+        if code not in (FGS_OK, FGS_ERR_CAPACITY):
+            _check(self.ctx, code)
+        return int(n.value)
+
+    def pairs(self):
+        """Sorted (key, value) pairs of the last frame as host numpy arrays."""
+        n = self.n_pairs()
+        keys = np.zeros(max(n, 1), np.uint64)
+        vals = np.zeros(max(n, 1), np.uint32)
+        fgs_get_pairs(self.ctx, self.stream, keys, vals, n, 0)
+        return keys[:n], vals[:n]
+
+    def splats(self):
+        m = C.c_uint32()
+        lib().fgs_get_splats(self.ctx, self.stream, None, 0, C.byref(m), 0)
+        M = int(m.value)
+        out = np.zeros((max(M, 1), len(SPLAT_FIELDS)), np.float32)
+        fgs_get_splats(self.ctx, self.stream, out, M, 0)
+        return out[:M]
+
+    def calibrate_view(self, want_kpc=False, n_pairs=None):
+        tiles = ((self.cam.width + self.params.tile_w - 1) // self.params.tile_w) * \
+                ((self.cam.height + self.params.tile_h - 1) // self.params.tile_h)
+        G = np.zeros(tiles, np.float32)
+        kpc = None
+        cap = 0
+        if want_kpc:
+            cap = int(n_pairs)
+            kpc = np.zeros(max(cap, 1), np.float32)
+        gbar = fgs_calibrate_view(self.ctx, self.stream, kpc, cap, G, 0)
+        return gbar, G, (kpc[:cap] if want_kpc else None)
+
+    def calibrate(self, cams, lambda_G=0.2):
+        return fgs_calibrate_gtc(self.ctx, self.stream, cams, lambda_G)
+
+    def stage_times(self, slot: int):
+        return fgs_stage_times(self.ctx, slot)
+
+    def sync(self):
+        fgs_sync(self.ctx, self.stream)

@@ -1,0 +1,82 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI and the
+oracle on the same seeded inputs and compare."""
+import math
+
+import numpy as np
+
+import oracle
+from paper_2603_23891_gb300 import synth
+
+IMG_TOL = 2e-3          # max-abs per channel, FP32 accumulation (spec bound)
+PSNR_MIN = 60.0
+EXACT_FIELDS = [0, 1, 2, 3, 4, 5, 6, 7, 11]   # u v A B C lthr a0 depth radius
+COLOUR_FIELDS = [8, 9, 10]
+
+
+def psnr(a, b):
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return math.inf if mse == 0 else 10.0 * math.log10(1.0 / mse)
+
+
+def gpu_frame(r, tree_loaded, cam, tau_R, shrink=None, tile=(16, 16), bg=(0, 0, 0)):
+    """Render one frame on the GPU; returns dict of host numpy results."""
+    import torch
+    r.set_params(tau_R=tau_R, tile=tile, bg=bg)
+    r.set_camera(cam)
+    if shrink is None:
+        r.shrink(None)
+    else:
+        r.shrink(*shrink)
+    rgb, T, st = r.render(stats=True)
+    torch.cuda.synchronize()
+    keys, vals = r.pairs()
+    spl = r.splats()
+    out = dict(rgb=rgb.cpu().numpy(), T=T.cpu().numpy(), keys=keys, vals=vals, splat=spl,
+               M=int(st.n_selected), NP=int(st.n_pairs))
+    out["sel"] = r.filter()
+    return out
+
+
+def oracle_frame(tree, cam, tau_R, shrink=None, tile=(16, 16), bg=(0, 0, 0), blend=True):
+    p = oracle.Params(tau_R=tau_R, tile_w=tile[0], tile_h=tile[1], bg=tuple(bg))
+    if shrink is not None:
+        p.shrink, p.tau, p.ln_tau = True, shrink[0], shrink[1]
+    return oracle.frame(tree, cam, p, blend=blend), p
+
+
+def assert_frame_parity(g, o, check_image=True):
+    assert np.array_equal(g["sel"], o.sel), f"selection differs ({len(g['sel'])} vs {len(o.sel)})"
+    assert g["M"] == len(o.sel)
+    assert g["NP"] == len(o.keys)
+    assert g["splat"].shape == o.splat.shape
+    if len(o.sel):
+        ge = g["splat"][:, EXACT_FIELDS].view(np.uint32)
+        oe = o.splat[:, EXACT_FIELDS].view(np.uint32)
+        bad = np.nonzero((ge != oe).any(axis=1))[0]
+        assert bad.size == 0, f"splat fields differ for {bad.size} Gaussians, first {bad[:5]}"
+        np.testing.assert_allclose(g["splat"][:, COLOUR_FIELDS], o.splat[:, COLOUR_FIELDS],
+                                   atol=2e-5, rtol=0)
+    assert np.array_equal(g["keys"], o.keys), "sorted keys differ"
+    assert np.array_equal(g["vals"], o.vals), "sorted values differ"
+    if check_image:
+        err = np.abs(g["rgb"].astype(np.float64) - o.rgb)
+        assert err.max() <= IMG_TOL, f"max-abs {err.max()}"
+        assert psnr(g["rgb"], o.rgb) >= PSNR_MIN
+        # transmittance is decided and multiplied in the same binary32 order on both sides
+        assert np.array_equal(g["T"].view(np.uint32), o.T.view(np.uint32)), \
+            f"T differs at {np.count_nonzero(g['T'] != o.T)} pixels"
+        return float(err.max())
+    return None
+
+
+def orbit_cameras(tree, n, size, seed, dist=(8.0, 40.0), fov=(35.0, 80.0)):
+    rng = np.random.default_rng(seed)
+    c = tree.mu.mean(axis=1).astype(np.float64)
+    cams = []
+    for _ in range(n):
+        a = rng.uniform(0, 2 * math.pi)
+        d = rng.uniform(*dist)
+        pos = [c[0] + d * math.cos(a), c[1] + d * math.sin(a), c[2] + rng.uniform(1.0, 0.6 * d)]
+        cams.append(synth.look_at_camera(pos, c + rng.normal(0, 1.0, 3), size[0], size[1],
+                                         rng.uniform(*fov)))
+    return cams

@@ -1,0 +1,98 @@
+"""C-ABI library: builds, loads without a GPU, exports every declared symbol; host-side
+tree validation rejects malformed trees (CPU only)."""
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+from paper_2603_23891_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    out = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", fn)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        out |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(fgs_\w+)\s*\(", txt, flags=re.M))
+    return out
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2603_23891_gb300 import build
+    build.build()
+    from paper_2603_23891_gb300 import filtergs
+    return filtergs
+
+
+def test_exports_every_declared_symbol(lib):
+    L = lib.lib()
+    declared = _declared_symbols()
+    assert len(declared) >= 19
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(lib.EXPORTED) == declared
+    assert L.fgs_version() == 1
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(lib.FgsError):
+        lib.fgs_create(0)
+
+
+def _mutated(tree, **changes):
+    import copy
+    t = copy.copy(tree)
+    for k, v in changes.items():
+        setattr(t, k, v)
+    return t
+
+
+def test_validate_tree(lib):
+    tree = synth.random_small_tree(0, n_leaves=120, branching=(2, 5), sh_degree=1)
+    code, msg = lib.fgs_validate_tree(tree)
+    assert code == lib.FGS_OK, msg
+
+    par = tree.parent.copy()
+    par[5] = 5                                             # self loop
+    assert lib.fgs_validate_tree(_mutated(tree, parent=par))[0] == lib.FGS_ERR_TREE
+    par = tree.parent.copy()
+    par[7] = tree.n + 3                                     # out of range
+    assert lib.fgs_validate_tree(_mutated(tree, parent=par))[0] == lib.FGS_ERR_TREE
+    par = tree.parent.copy()
+    par[3] = -1                                             # two roots
+    assert lib.fgs_validate_tree(_mutated(tree, parent=par))[0] == lib.FGS_ERR_TREE
+    # cycle: root's child points to a grandchild
+    par = tree.parent.copy()
+    kid = int(np.nonzero(par == 0)[0][0])
+    grand = int(np.nonzero(par == kid)[0][0])
+    par[kid] = grand
+    assert lib.fgs_validate_tree(_mutated(tree, parent=par))[0] == lib.FGS_ERR_TREE
+    ap = tree.ap.copy()
+    ap[0, 10] = (ap[0, 10] + 1) % tree.n                    # AP disagrees with parent
+    assert lib.fgs_validate_tree(_mutated(tree, ap=ap))[0] == lib.FGS_ERR_TREE
+    ap = tree.ap[:-1].copy()                                # depth too small
+    assert lib.fgs_validate_tree(_mutated(tree, ap=ap))[0] == lib.FGS_ERR_TREE
+    leaf = tree.is_leaf.copy()
+    leaf[0] = 1                                             # root marked leaf
+    assert lib.fgs_validate_tree(_mutated(tree, is_leaf=leaf))[0] == lib.FGS_ERR_TREE
+    mu = tree.mu.copy()
+    mu[1, 4] = np.nan
+    assert lib.fgs_validate_tree(_mutated(tree, mu=mu))[0] == lib.FGS_ERR_TREE
+    op = tree.opacity.copy()
+    op[2] = 0.0
+    assert lib.fgs_validate_tree(_mutated(tree, opacity=op))[0] == lib.FGS_ERR_TREE
+    sh = tree.sh.copy()
+    sh[3, 1, 2] = np.inf
+    assert lib.fgs_validate_tree(_mutated(tree, sh=sh))[0] == lib.FGS_ERR_TREE

@@ -1,0 +1,224 @@
+"""GPU parity of the whole render path against the CPU oracle (through the C ABI).
+
+Selections, splat decision fields, sorted pair lists and final transmittance are
+compared bit for bit; colours within 2e-3 max-abs and >= 60 dB PSNR."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_23891_gb300 import synth
+
+from gpu_util import assert_frame_parity, gpu_frame, oracle_frame, orbit_cameras
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def renderer():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_23891_gb300 import build, filtergs
+    build.build()
+    r = filtergs.Renderer(device=0)
+    yield r
+    r.close()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.tiny_tree(), synth.tiny_camera()
+
+
+@pytest.mark.parametrize("tau_R", [1.0, 3.0, 10.0, 40.0, -1.0, 1e30])
+def test_tiny_tree_all_thresholds(renderer, tiny, tau_R):
+    tree, cam = tiny
+    renderer.load_tree(tree)
+    g = gpu_frame(renderer, tree, cam, tau_R)
+    o, _ = oracle_frame(tree, cam, tau_R)
+    assert_frame_parity(g, o)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 32)])
+def test_tile_shapes_and_ragged_image(renderer, tile):
+    tree = synth.tiny_tree()
+    renderer.load_tree(tree)
+    # 250 x 130 is not a multiple of any tile shape: ragged last row / column of tiles
+    cam = synth.look_at_camera([0.0, -60.0, 35.0], [0, 0, 0], 250, 130, 65.0)
+    g = gpu_frame(renderer, tree, cam, 3.0, tile=tile, bg=(0.1, 0.2, 0.3))
+    o, _ = oracle_frame(tree, cam, 3.0, tile=tile, bg=(0.1, 0.2, 0.3))
+    assert_frame_parity(g, o)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_trees_multilevel_cuts(renderer, seed):
+    """Small trees with large leaves: cuts span several levels."""
+    tree = synth.random_small_tree(seed, n_leaves=3000, branching=(2, 8), sh_degree=3,
+                                   extent=20.0, log_scale_mean=-0.8)
+    renderer.load_tree(tree)
+    levels = set()
+    for cam in orbit_cameras(tree, 3, (160, 120), seed):
+        for tau_R in (3.0, 12.0):
+            g = gpu_frame(renderer, tree, cam, tau_R)
+            o, _ = oracle_frame(tree, cam, tau_R)
+            assert_frame_parity(g, o)
+            levels |= set(np.unique(tree.level[o.sel]).tolist())
+    assert len(levels) >= 3
+
+
+def test_shrink_on_pairs_bit_exact(renderer, tiny):
+    """Adaptive shrinking: the same tau / ln tau bits on both sides give identical pairs;
+    more aggressive tau never adds pairs."""
+    tree, cam = tiny
+    renderer.load_tree(tree)
+    prev = None
+    for tau in (1 / 255, 0.02, 0.1, 0.3):
+        sh = (float(np.float32(tau)), float(np.float32(math.log(tau))))
+        g = gpu_frame(renderer, tree, cam, 3.0, shrink=sh)
+        o, _ = oracle_frame(tree, cam, 3.0, shrink=sh)
+        assert_frame_parity(g, o)
+        if prev is not None:
+            assert g["NP"] <= prev
+        prev = g["NP"]
+
+
+def test_calibration_matches_oracle(renderer):
+    """KPC per pair (Eq. 5), GTC per tile (Eq. 6), view average (Eq. 7) and tau (Eq. 8)."""
+    tree = synth.random_small_tree(11, n_leaves=2000, branching=(2, 6), sh_degree=0,
+                                   extent=15.0, log_scale_mean=-0.9)
+    renderer.load_tree(tree)
+    renderer.set_params(tau_R=3.0, tile=(16, 16))
+    cams = orbit_cameras(tree, 3, (128, 96), 5)
+    gbars = []
+    for cam in cams:
+        renderer.set_camera(cam)
+        renderer.shrink(None)
+        renderer.render()
+        n = renderer.n_pairs()
+        gbar, G, kpc = renderer.calibrate_view(want_kpc=True, n_pairs=n)
+        o, p = oracle_frame(tree, cam, 3.0, blend=False)
+        _, _, okpc = oracle.render(o.splat, o.keys, o.vals, cam, p, want_kpc=True)
+        tx, ty = oracle.tiles_of(cam, p)
+        oG, ogbar, _ = oracle.gtc(o.keys, okpc, tx * ty)
+        np.testing.assert_allclose(kpc, okpc, rtol=1e-4, atol=1e-5)
+        both = ~np.isnan(oG)
+        assert np.array_equal(np.isnan(G), np.isnan(oG))
+        np.testing.assert_allclose(G[both], oG[both], rtol=1e-4, atol=1e-6)
+        assert gbar == pytest.approx(ogbar, rel=1e-4)
+        gbars.append(gbar)
+    tau, ln_tau, gb = renderer.calibrate(cams, 0.2)
+    np.testing.assert_allclose(gb, gbars, rtol=1e-12)
+    otau, oln = oracle.tau_from(gbars, 0.2)
+    assert tau == pytest.approx(otau, rel=1e-6) and ln_tau == pytest.approx(oln, rel=1e-6)
+
+
+def test_device_exp_matches_oracle_and_cuda(renderer):
+    """The blend's exp: bit-identical to the oracle's binary32 restatement, and within
+    2 ulp of CUDA's expf."""
+    import torch
+    from paper_2603_23891_gb300 import filtergs
+    x = torch.linspace(-87.0, 0.0, 100001, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    filtergs.fgs_eval_exp(x, y, None)
+    torch.cuda.synchronize()
+    xs = x.cpu().numpy()
+    ys = y.cpu().numpy()
+    sub = slice(None, None, 97)
+    assert np.array_equal(ys[sub].view(np.uint32), oracle.expf(xs[sub]).view(np.uint32))
+    ref = torch.exp(x).cpu().numpy()
+    ulp = np.spacing(np.abs(ref).astype(np.float32))
+    assert (np.abs(ys.astype(np.float64) - ref) / ulp).max() <= 2.0
+
+
+def test_empty_view_and_behind_camera(renderer, tiny):
+    """Camera facing away: no selection, no pairs, image = background, T = 1."""
+    tree, _ = tiny
+    renderer.load_tree(tree)
+    cam = synth.look_at_camera([0, -80, 10], [0, -200, 10], 64, 48, 60.0)
+    g = gpu_frame(renderer, tree, cam, 3.0, bg=(0.25, 0.5, 0.75))
+    assert g["M"] == 0 and g["NP"] == 0 and g["sel"].size == 0
+    assert np.all(g["T"] == 1.0)
+    for ch, v in enumerate((0.25, 0.5, 0.75)):
+        assert np.all(g["rgb"][ch] == np.float32(v))
+
+
+def test_gaussian_covering_whole_screen(renderer):
+    """One large Gaussian right in front of the camera touches every tile."""
+    t = synth.tree_from_gaussians(np.array([[0.0, 3.0, 0.0], [0.5, 20.0, 0.3]]),
+                                  np.array([[0.5, 0.5, 0.5], [-1.0, -1.0, -1.0]]),
+                                  np.array([[1.0, 0, 0, 0], [1.0, 0, 0, 0]]), np.array([0.0, 2.0]),
+                                  np.zeros((2, 1, 3)), 0)
+    renderer.load_tree(t)
+    cam = synth.look_at_camera([0, 0, 0], [0, 1, 0], 200, 120, 60.0)
+    g = gpu_frame(renderer, t, cam, -1.0)
+    o, _ = oracle_frame(t, cam, -1.0)
+    assert_frame_parity(g, o)
+    tiles = ((200 + 15) // 16) * ((120 + 15) // 16)
+    assert g["NP"] >= tiles
+
+
+def test_depth_ties_break_by_id(renderer):
+    """Duplicated Gaussians at one depth: equal keys keep ascending selection order."""
+    mu = np.array([[0.0, 10.0, 0.0]] * 6 + [[0.3, 10.0, 0.2]] * 3)
+    n = mu.shape[0]
+    rng = np.random.default_rng(3)
+    t = synth.tree_from_gaussians(mu, np.full((n, 3), -1.5), np.tile([1.0, 0, 0, 0], (n, 1)),
+                                  rng.normal(0, 1, n), rng.normal(0, 1, (n, 1, 3)), 0)
+    renderer.load_tree(t)
+    cam = synth.look_at_camera([0, 0, 0], [0, 1, 0], 64, 64, 60.0)
+    g = gpu_frame(renderer, t, cam, -1.0)
+    o, _ = oracle_frame(t, cam, -1.0)
+    assert_frame_parity(g, o)
+    k = g["keys"]
+    assert np.any(k[1:] == k[:-1])     # ties exist
+
+
+def test_capacity_exceeded_is_reported(tiny):
+    """N_P above the pair capacity: the frame reports FGS_ERR_CAPACITY (no overflow write),
+    and the context renders correctly once the capacity is raised."""
+    from paper_2603_23891_gb300 import filtergs
+    tree, cam = tiny
+    r2 = filtergs.Renderer(device=0, pair_capacity=1000)
+    try:
+        r2.load_tree(tree)
+        r2.set_camera(cam)
+        with pytest.raises(filtergs.FgsError) as e:
+            r2.render(stats=True)
+        assert e.value.code == filtergs.FGS_ERR_CAPACITY
+        r2.set_params(pair_capacity=1 << 20)
+        g = gpu_frame(r2, tree, cam, 3.0)
+        o, _ = oracle_frame(tree, cam, 3.0)
+        assert len(o.keys) > 1000
+        assert_frame_parity(g, o)
+    finally:
+        r2.close()
+
+
+def test_invalid_inputs_rejected(renderer, tiny):
+    from paper_2603_23891_gb300 import filtergs
+    tree, cam = tiny
+    renderer.load_tree(tree)
+    bad = filtergs.make_camera(cam)
+    bad.fx = float("nan")
+    with pytest.raises(filtergs.FgsError) as e:
+        filtergs.fgs_set_camera(renderer.ctx, bad)
+    assert e.value.code == filtergs.FGS_ERR_ARG
+    bad = filtergs.make_camera(cam)
+    bad.width = 0
+    with pytest.raises(filtergs.FgsError):
+        filtergs.fgs_set_camera(renderer.ctx, bad)
+    with pytest.raises(filtergs.FgsError):
+        renderer.set_params(tile=(16, 8))
+    renderer.set_params(tile=(16, 16))
+    with pytest.raises(filtergs.FgsError):
+        filtergs.fgs_set_shrink(renderer.ctx, 1, float("nan"), 0.0)
+    par = tree.parent.copy()
+    par[3] = 3
+    import copy
+    t2 = copy.copy(tree)
+    t2.parent = par
+    with pytest.raises(filtergs.FgsError) as e:
+        filtergs.fgs_load_tree(renderer.ctx, t2)
+    assert e.value.code == filtergs.FGS_ERR_TREE
