@@ -720,13 +720,23 @@ int fgs_calibrate_view(fgs_ctx* c, void* stream, double* gbar_out, float* kpc_ou
         return r;
     }
     const FrameState& h = *c->st_host;
-    *gbar_out = h.gtc_tiles ? h.gtc_sum / (double)h.gtc_tiles : NAN;   // Eq. 7
+    const size_t tiles = (size_t)dc.tiles_x * dc.tiles_y;
+    std::vector<float> Gh(tiles);
+    FGS_CUDA(c, cudaMemcpyAsync(Gh.data(), c->G, tiles * 4, cudaMemcpyDeviceToHost, s));
     const cudaMemcpyKind kind = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const uint64_t np = std::min<uint64_t>(h.n_pairs, c->pair_cap);
     if (kpc_out && np) FGS_CUDA(c, cudaMemcpyAsync(kpc_out, c->kpc, std::min(np, kpc_cap) * 4, kind, s));
-    if (G_out)
-        FGS_CUDA(c, cudaMemcpyAsync(G_out, c->G, (size_t)dc.tiles_x * dc.tiles_y * 4, kind, s));
+    if (G_out) FGS_CUDA(c, cudaMemcpyAsync(G_out, c->G, tiles * 4, kind, s));
     FGS_CUDA(c, cudaStreamSynchronize(s));
+    // Eq. 7: mean of G over the tiles that have pairs (tile order, float64)
+    double sum = 0.0;
+    size_t used = 0;
+    for (size_t i = 0; i < tiles; ++i)
+        if (!std::isnan(Gh[i])) {
+            sum += (double)Gh[i];
+            ++used;
+        }
+    *gbar_out = used ? sum / (double)used : NAN;
     return FGS_OK;
 }
 

@@ -73,7 +73,7 @@ struct BlendSmem {
     float4 g0[kChunk];   // u, v, A, B
     float4 g1[kChunk];   // C, lthr, alpha0, depth
     float4 g2[kChunk];   // r, g, b, radius
-    float kpc[kChunk];
+    float kpc_w[8][kChunk];   // per-warp partial KPC of each chunk entry
     uint64_t bar;
     int timed_out;
 };
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
                                                     float* __restrict__ G_out, FrameState* st)
 {
     __shared__ __align__(128) BlendSmem S;
-    __shared__ double s_tile_sum;
+    __shared__ double s_red[8];
     const uint32_t tile = blockIdx.x;
     const uint32_t tid = threadIdx.x;
     const uint32_t tx = tile % (uint32_t)cam.tiles_x, ty = tile / (uint32_t)cam.tiles_x;
@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
     if (tid == 0) {
         mbar_init(&S.bar, 1);
         S.timed_out = 0;
-        s_tile_sum = 0.0;
     }
+    double kpc_acc = 0.0;     // this thread's share of the tile's KPC sum (fixed order)
     __syncthreads();
 
     float T = 1.0f;
@@ -179,7 +179,6 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
             S.g0[tid] = __ldg(g);
             S.g1[tid] = __ldg(g + 1);
             S.g2[tid] = __ldg(g + 2);
-            if (kKpc) S.kpc[tid] = 0.0f;
         }
         __syncthreads();
         if (!kKpc) {
@@ -188,20 +187,23 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
                 blend_one(S.g0[j], S.g1[j], S.g2[j], px, py, T, C, done, w);
             }
         } else {
-            const uint32_t lane = tid & 31;
+            const uint32_t lane = tid & 31, warp = tid >> 5;
             for (uint32_t j = 0; j < cnt; ++j) {
                 float w = 0.0f;
                 if (!done) blend_one(S.g0[j], S.g1[j], S.g2[j], px, py, T, C, done, w);
-                // Eq. 5: sum of alpha * T over the tile's pixels for this pair
+                // Eq. 5: sum of alpha * T over the tile's pixels for this pair; a
+                // butterfly per warp, then the 8 warp partials in order: deterministic
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-                if (lane == 0 && w != 0.0f) atomicAdd(&S.kpc[j], w);
+                if (lane == 0) S.kpc_w[warp][j] = w;
             }
             __syncthreads();
             if (tid < cnt) {
-                const float k = S.kpc[tid];
+                float k = 0.0f;
+#pragma unroll
+                for (int w8 = 0; w8 < 8; ++w8) k += S.kpc_w[w8][tid];
                 kpc_out[s0 + tid] = k;
-                atomicAdd(&s_tile_sum, (double)k);
+                kpc_acc += (double)k;
             }
         }
         const int n_done = __syncthreads_count(done);
@@ -216,17 +218,16 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
         if (Tout) Tout[pix] = T;
     }
     if (kKpc) {
+        // Eq. 6: G = mean KPC over the tile's pairs; fixed-order block reduction
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) kpc_acc += __shfl_xor_sync(0xffffffffu, kpc_acc, o);
+        if ((tid & 31) == 0) s_red[tid >> 5] = kpc_acc;
         __syncthreads();
         if (tid == 0) {
             const uint32_t n = e - s;
-            if (n > 0) {
-                const double G = s_tile_sum / (double)n;   // Eq. 6
-                G_out[tile] = (float)G;
-                atomicAdd(&st->gtc_sum, G);
-                atomicAdd(&st->gtc_tiles, 1u);
-            } else {
-                G_out[tile] = __int_as_float(0x7fc00000);
-            }
+            double sum = 0.0;
+            for (int w8 = 0; w8 < 8; ++w8) sum += s_red[w8];
+            G_out[tile] = n > 0 ? (float)(sum / (double)n) : __int_as_float(0x7fc00000);
         }
     }
 }

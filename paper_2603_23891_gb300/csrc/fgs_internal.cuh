@@ -73,9 +73,7 @@ struct FrameState {
     int32_t status;            // latched error (0 = ok)
     uint32_t status_info;
     uint32_t hist[kMaxSortPasses][256];   // radix digit histograms
-    double gtc_sum;            // sum of per-tile GTC over tiles with pairs
-    uint32_t gtc_tiles;        // number of such tiles
-    uint32_t pad_;
+
 };
 
 // Ticket slots

@@ -59,8 +59,8 @@ def test_random_trees_multilevel_cuts(renderer, seed):
                                    extent=20.0, log_scale_mean=-0.8)
     renderer.load_tree(tree)
     levels = set()
-    for cam in orbit_cameras(tree, 3, (160, 120), seed):
-        for tau_R in (3.0, 12.0):
+    for cam in orbit_cameras(tree, 3, (160, 120), seed, dist=(10.0, 80.0)):
+        for tau_R in (3.0, 12.0, 40.0):
             g = gpu_frame(renderer, tree, cam, tau_R)
             o, _ = oracle_frame(tree, cam, tau_R)
             assert_frame_parity(g, o)
@@ -109,7 +109,8 @@ def test_calibration_matches_oracle(renderer):
         assert gbar == pytest.approx(ogbar, rel=1e-4)
         gbars.append(gbar)
     tau, ln_tau, gb = renderer.calibrate(cams, 0.2)
-    np.testing.assert_allclose(gb, gbars, rtol=1e-12)
+    # the reductions run in a fixed order: a second calibration gives the same bits
+    assert np.array_equal(gb, np.array(gbars))
     otau, oln = oracle.tau_from(gbars, 0.2)
     assert tau == pytest.approx(otau, rel=1e-6) and ln_tau == pytest.approx(oln, rel=1e-6)
 
