@@ -106,7 +106,7 @@ typedef struct fgs_camera {
 
 typedef struct fgs_params {
     float tau_R;              /* R&L pixel-radius threshold, 3 px in the paper (§3.2) */
-    int32_t tile_w, tile_h;   /* tile size in pixels; powers of two, tile_w * tile_h == 256 */
+    int32_t tile_w, tile_h;   /* tile size in pixels: 64x4, 32x8, 16x16 (default) or 8x32 */
     float bg[3];              /* background colour added as T * bg */
     uint64_t pair_capacity;   /* max Gaussian-tile pairs per frame (0 = keep current / default) */
 } fgs_params;

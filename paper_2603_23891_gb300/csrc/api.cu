@@ -346,8 +346,9 @@ int fgs_set_params(fgs_ctx* c, const fgs_params* p)
 {
     if (!c || !p) return FGS_ERR_ARG;
     if (std::isnan(p->tau_R)) return fail(c, FGS_ERR_ARG, "tau_R is NaN");
-    if (!is_pow2(p->tile_w) || !is_pow2(p->tile_h) || p->tile_w * p->tile_h != 256)
-        return fail(c, FGS_ERR_ARG, "tile %dx%d must be powers of two with 256 pixels", p->tile_w,
+    if (!is_pow2(p->tile_w) || !is_pow2(p->tile_h) || p->tile_w * p->tile_h != 256 ||
+        p->tile_w < 8 || p->tile_h < 4)
+        return fail(c, FGS_ERR_ARG, "tile %dx%d must be 64x4, 32x8, 16x16 or 8x32", p->tile_w,
                     p->tile_h);
     if (!finite_all(p->bg, 3)) return fail(c, FGS_ERR_ARG, "background not finite");
     if (p->pair_capacity > kMaxPairCap) return fail(c, FGS_ERR_ARG, "pair capacity too large");

@@ -1,18 +1,21 @@
 // Per-tile front-to-back alpha blending (Eq. 2) and the KPC / GTC pre-render
 // pass of the scene-adaptive shrinking (Eq. 5-7), sm_103a.
 //
-// One CTA per image tile, one thread per pixel (tile_w * tile_h = 256).  The
-// tile's slice of the sorted value list is brought into shared memory in
-// chunks of 256 by a TMA bulk copy (cp.async.bulk, completion on an mbarrier;
-// the copy starts at the 16-byte boundary at or below the slice and the
-// thread index is offset accordingly), then each thread gathers one splat
-// record into shared memory and all pixels walk the chunk front to back.
+// One CTA per image tile, one thread per pixel (tile_w * tile_h = 256); each
+// warp covers an 8 x 4 pixel block.  The tile's slice of the sorted value list
+// is brought into shared memory in chunks of 256 by a TMA bulk copy
+// (cp.async.bulk, completion on an mbarrier; the copy starts at the 16-byte
+// boundary at or below the slice and the index is offset accordingly).  Each
+// thread then gathers one splat record into shared memory and computes which
+// warps' pixels the Gaussian can reach; every warp compacts the chunk to its own
+// ordered list and walks it front to back.
 //
 // Blend decisions are exact: power, the log-domain skip test, alpha, the
 // opacity clamp and the transmittance update use explicitly rounded binary32
 // operations and a deterministic exp, so which Gaussians a pixel applies, and
-// where it stops, do not depend on the compiler.  Colour accumulation may use
-// FMA (it decides nothing).
+// where it stops, do not depend on the compiler.  The per-warp culling only
+// drops Gaussians that every pixel of the warp would skip.  Colour
+// accumulation may use FMA (it decides nothing).
 #include "fgs_internal.cuh"
 
 namespace fgs {
@@ -68,61 +71,39 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+template <bool kKpc>
 struct BlendSmem {
     uint32_t vals[kValsSlots];
-    float4 g0[kChunk];   // u, v, A, B
-    float4 g1[kChunk];   // C, lthr, alpha0, depth
-    float4 g2[kChunk];   // r, g, b, radius
-    float kpc_w[8][kChunk];   // per-warp partial KPC of each chunk entry
+    float4 g0[kChunk];          // u, v, A, B
+    float4 g1[kChunk];          // C, lthr, alpha0, depth
+    float4 g2[kChunk];          // r, g, b, radius
+    uint32_t wmask[kChunk];     // bit w: warp w's pixels can reach the skip threshold
+    uint16_t wlist[8][kChunk];  // per-warp list of chunk entries, in order
+    float kpc_w[kKpc ? 8 : 1][kKpc ? kChunk : 1];   // per-warp partial KPC (Eq. 5)
     uint64_t bar;
     int timed_out;
 };
 
-// One blend step for a pixel; returns false once the pixel has stopped.
-__device__ __forceinline__ void blend_one(const float4& g0, const float4& g1, const float4& g2,
-                                          float px, float py, float& T, float3& C, bool& done,
-                                          float& w_out)
-{
-    w_out = 0.0f;
-    const float dx = fs(g0.x, px);
-    const float dy = fs(g0.y, py);
-    const float p1 = fm(fm(g0.z, dx), dx);
-    const float p2 = fm(fm(g1.x, dy), dy);
-    const float p3 = fm(fm(g0.w, dx), dy);
-    const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
-    if (power > 0.0f || power < g1.y) return;
-    float alpha = fm(g1.z, exp_cw(power));
-    alpha = alpha < 0.99f ? alpha : 0.99f;
-    const float Tn = fm(T, fs(1.0f, alpha));
-    if (Tn < 0.0001f) {
-        done = true;
-        return;
-    }
-    const float w = alpha * T;
-    C.x = fmaf(g2.x, w, C.x);
-    C.y = fmaf(g2.y, w, C.y);
-    C.z = fmaf(g2.z, w, C.z);
-    w_out = w;
-    T = Tn;
-}
-
-// Bring chunk [s0, e0) of vals into shared memory.  Returns the offset of s0
-// inside the staged copy.  Called by all threads; thread 0 issues the copy.
-__device__ __forceinline__ uint32_t stage_vals(BlendSmem& S, const uint32_t* vals, uint32_t s0,
-                                               uint32_t e0, uint32_t& phase, FrameState* st)
+// Bring chunk [s0, e0) of the sorted values into shared memory with one TMA bulk
+// copy of the 16-byte aligned superset [s0 & ~3, (e0 + 3) & ~3).  Returns the
+// offset of s0 inside the staged copy.  Called by all threads; thread 0 issues
+// the copy and waits on the mbarrier (bounded).
+__device__ __forceinline__ uint32_t stage_vals(uint32_t* dst, uint64_t* bar, int* timed_out,
+                                               const uint32_t* vals, uint32_t s0, uint32_t e0,
+                                               uint32_t& phase, FrameState* st)
 {
     const uint32_t a0 = s0 & ~3u;
     const uint32_t a1 = (e0 + 3u) & ~3u;
     const uint32_t bytes = (a1 - a0) * 4u;
     if (threadIdx.x == 0) {
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&S.bar, bytes);
-        tma_bulk_g2s(S.vals, vals + a0, bytes, &S.bar);
+        mbar_arrive_expect_tx(bar, bytes);
+        tma_bulk_g2s(dst, vals + a0, bytes, bar);
         uint64_t spins = 0;
-        while (!mbar_try_wait(&S.bar, phase)) {
+        while (!mbar_try_wait(bar, phase)) {
             if (++spins > kSpinLimit) {
-                S.timed_out = 1;
-                if (st) set_status(st, kErrTimeout, 0x500u);
+                *timed_out = 1;
+                set_status(st, kErrTimeout, 0x500u);
                 break;
             }
         }
@@ -130,6 +111,47 @@ __device__ __forceinline__ uint32_t stage_vals(BlendSmem& S, const uint32_t* val
     phase ^= 1u;
     __syncthreads();
     return s0 - a0;
+}
+
+// Warps of a CTA cover 8 x 4 pixel blocks of the tile (tile_w / 8 across).
+__device__ __forceinline__ void warp_origin(const DevCamera& cam, uint32_t tile, uint32_t w,
+                                            int32_t& x0, int32_t& y0)
+{
+    const uint32_t tx = tile % (uint32_t)cam.tiles_x, ty = tile / (uint32_t)cam.tiles_x;
+    const uint32_t wpr = (uint32_t)(cam.tile_w >> 3);
+    const uint32_t wx = w % wpr, wy = w / wpr;
+    x0 = (int32_t)(tx * cam.tile_w + wx * 8);
+    y0 = (int32_t)(ty * cam.tile_h + wy * 4);
+}
+
+// Which warps of the tile may hold a pixel whose binary32 power reaches the
+// Gaussian's skip threshold lthr.  Exactly, power >= lthr is the ellipse
+// d^T Q d <= s with Q = [[A, B], [B, C]] and s = -2 lthr, whose bounding box has
+// half-widths sqrt(s C / det Q) and sqrt(s A / det Q).  The rounding error of the
+// binary32 power is below 1e-6 * cond(Q) * |lthr|; the box is enlarged by 5% in s
+// plus one pixel, which covers it for cond(Q) < 1e4 (cond(Q) <= tr^2 / det).
+// Beyond that, or for a singular Q, every warp keeps the Gaussian.  A warp left
+// out of the mask would have skipped the Gaussian at every one of its pixels.
+__device__ __forceinline__ uint32_t warp_mask(const DevCamera& cam, uint32_t tile, float u, float v,
+                                              float A, float B, float C, float lthr)
+{
+    if (!(lthr <= 0.0f)) return 0u;             // alpha0 < 1/255: no pixel can pass
+    const float det = A * C - B * B;
+    const float tr = A + C;
+    if (!(det > 0.0f) || tr * tr > 1e4f * det) return 0xFFu;
+    const float sq = fmaf(-2.1f, lthr, 1e-4f);  // 1.05 * (-2 lthr) + 1e-4
+    const float ex = sqrtf(sq * C / det) + 1.0f;
+    const float ey = sqrtf(sq * A / det) + 1.0f;
+    uint32_t mask = 0;
+#pragma unroll
+    for (uint32_t w = 0; w < 8; ++w) {
+        int32_t x0, y0;
+        warp_origin(cam, tile, w, x0, y0);
+        const float px0 = (float)x0 + 0.5f, px1 = (float)x0 + 7.5f;
+        const float py0 = (float)y0 + 0.5f, py1 = (float)y0 + 3.5f;
+        if (px0 <= u + ex && px1 >= u - ex && py0 <= v + ey && py1 >= v - ey) mask |= 1u << w;
+    }
+    return mask;
 }
 
 }  // namespace
@@ -142,13 +164,14 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
                                                     float* __restrict__ kpc_out,
                                                     float* __restrict__ G_out, FrameState* st)
 {
-    __shared__ __align__(128) BlendSmem S;
+    __shared__ __align__(128) BlendSmem<kKpc> S;
     __shared__ double s_red[8];
     const uint32_t tile = blockIdx.x;
-    const uint32_t tid = threadIdx.x;
-    const uint32_t tx = tile % (uint32_t)cam.tiles_x, ty = tile / (uint32_t)cam.tiles_x;
-    const int32_t x = (int32_t)(tx * cam.tile_w + (tid & (cam.tile_w - 1)));
-    const int32_t y = (int32_t)(ty * cam.tile_h + (tid >> cam.tile_shift_x));
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int32_t wx0, wy0;
+    warp_origin(cam, tile, warp, wx0, wy0);
+    const int32_t x = wx0 + (int32_t)(lane & 7);
+    const int32_t y = wy0 + (int32_t)(lane >> 3);
     const bool inside = x < cam.width && y < cam.height;
     const float px = fa((float)x, 0.5f), py = fa((float)y, 0.5f);
     const uint2 rg = ranges[tile];
@@ -159,49 +182,84 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
         mbar_init(&S.bar, 1);
         S.timed_out = 0;
     }
-    double kpc_acc = 0.0;     // this thread's share of the tile's KPC sum (fixed order)
     __syncthreads();
 
     float T = 1.0f;
-    float3 C = make_float3(0.0f, 0.0f, 0.0f);
+    float3 Cacc = make_float3(0.0f, 0.0f, 0.0f);
     bool done = !inside;
     uint32_t phase = 0;
+    double kpc_acc = 0.0;      // this thread's share of the tile's KPC sum (fixed order)
 
     for (uint32_t s0 = s; s0 < e; s0 += kChunk) {
         const uint32_t e0 = min(e, s0 + kChunk);
         const uint32_t cnt = e0 - s0;
-        const uint32_t off = stage_vals(S, vals, s0, e0, phase, st);
+        const uint32_t off = stage_vals(S.vals, &S.bar, &S.timed_out, vals, s0, e0, phase, st);
         if (S.timed_out) break;
         if (tid < cnt) {
             uint32_t m = S.vals[off + tid];
             if (m >= M) m = 0;      // only after a failed sort (status already latched)
             const float4* g = reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride);
-            S.g0[tid] = __ldg(g);
-            S.g1[tid] = __ldg(g + 1);
+            const float4 a = __ldg(g), b = __ldg(g + 1);
+            S.g0[tid] = a;
+            S.g1[tid] = b;
             S.g2[tid] = __ldg(g + 2);
+            S.wmask[tid] = warp_mask(cam, tile, a.x, a.y, a.z, a.w, b.x, b.y);
         }
         __syncthreads();
-        if (!kKpc) {
-            for (uint32_t j = 0; j < cnt && !done; ++j) {
-                float w;
-                blend_one(S.g0[j], S.g1[j], S.g2[j], px, py, T, C, done, w);
+        // this warp's ordered list of the chunk entries that can reach its pixels
+        uint32_t wcnt = 0;
+        for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            const bool mine = j < cnt && ((S.wmask[j] >> warp) & 1u);
+            const uint32_t b = __ballot_sync(0xffffffffu, mine);
+            if (mine) S.wlist[warp][wcnt + __popc(b & ((1u << lane) - 1u))] = (uint16_t)j;
+            wcnt += __popc(b);
+        }
+        __syncwarp();
+        for (uint32_t i = 0; i < wcnt; ++i) {
+            if (!kKpc && __all_sync(0xffffffffu, done)) break;
+            const uint32_t j = S.wlist[warp][i];
+            float w = 0.0f;
+            if (!done) {
+                const float4 g0 = S.g0[j];
+                const float4 g1 = S.g1[j];
+                const float dx = fs(g0.x, px);
+                const float dy = fs(g0.y, py);
+                const float p1 = fm(fm(g0.z, dx), dx);
+                const float p2 = fm(fm(g1.x, dy), dy);
+                const float p3 = fm(fm(g0.w, dx), dy);
+                const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
+                if (!(power > 0.0f || power < g1.y)) {
+                    float alpha = fm(g1.z, exp_cw(power));
+                    alpha = alpha < 0.99f ? alpha : 0.99f;
+                    const float Tn = fm(T, fs(1.0f, alpha));
+                    if (Tn < 0.0001f) {
+                        done = true;            // stop before adding this Gaussian
+                    } else {
+                        const float4 g2 = S.g2[j];
+                        w = alpha * T;
+                        Cacc.x = fmaf(g2.x, w, Cacc.x);
+                        Cacc.y = fmaf(g2.y, w, Cacc.y);
+                        Cacc.z = fmaf(g2.z, w, Cacc.z);
+                        T = Tn;
+                    }
+                }
             }
-        } else {
-            const uint32_t lane = tid & 31, warp = tid >> 5;
-            for (uint32_t j = 0; j < cnt; ++j) {
-                float w = 0.0f;
-                if (!done) blend_one(S.g0[j], S.g1[j], S.g2[j], px, py, T, C, done, w);
-                // Eq. 5: sum of alpha * T over the tile's pixels for this pair; a
-                // butterfly per warp, then the 8 warp partials in order: deterministic
+            if (kKpc) {
+                // Eq. 5: sum of alpha * T over the warp's pixels for this pair
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
                 if (lane == 0) S.kpc_w[warp][j] = w;
             }
+        }
+        if (kKpc) {
             __syncthreads();
             if (tid < cnt) {
+                const uint32_t msk = S.wmask[tid];
                 float k = 0.0f;
 #pragma unroll
-                for (int w8 = 0; w8 < 8; ++w8) k += S.kpc_w[w8][tid];
+                for (int w8 = 0; w8 < 8; ++w8)
+                    if ((msk >> w8) & 1u) k += S.kpc_w[w8][tid];
                 kpc_out[s0 + tid] = k;
                 kpc_acc += (double)k;
             }
@@ -212,16 +270,16 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
     if (inside && rgb) {
         const size_t hw = (size_t)cam.width * cam.height;
         const size_t pix = (size_t)y * cam.width + x;
-        rgb[pix] = fmaf(T, cam.bg[0], C.x);
-        rgb[hw + pix] = fmaf(T, cam.bg[1], C.y);
-        rgb[2 * hw + pix] = fmaf(T, cam.bg[2], C.z);
+        rgb[pix] = fmaf(T, cam.bg[0], Cacc.x);
+        rgb[hw + pix] = fmaf(T, cam.bg[1], Cacc.y);
+        rgb[2 * hw + pix] = fmaf(T, cam.bg[2], Cacc.z);
         if (Tout) Tout[pix] = T;
     }
     if (kKpc) {
         // Eq. 6: G = mean KPC over the tile's pairs; fixed-order block reduction
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) kpc_acc += __shfl_xor_sync(0xffffffffu, kpc_acc, o);
-        if ((tid & 31) == 0) s_red[tid >> 5] = kpc_acc;
+        if (lane == 0) s_red[warp] = kpc_acc;
         __syncthreads();
         if (tid == 0) {
             const uint32_t n = e - s;

@@ -20,6 +20,7 @@ constexpr int kSortTileItems = 16;        // keys per thread in a sort tile
 constexpr int kSortThreads = 256;
 constexpr int kSortTile = kSortTileItems * kSortThreads;   // 4096 keys
 constexpr int kMaxSortPasses = 6;         // 48 key bits: 32 depth + up to 16 tile bits
+constexpr int kLookbackRows = 8;          // predecessor tiles read per look-back round trip
 constexpr int kFilterItems = 16;          // nodes per thread in the ancestor/compaction kernel
 constexpr int kFilterThreads = 256;
 constexpr int kFilterTile = kFilterItems * kFilterThreads;  // 4096 nodes
@@ -202,6 +203,57 @@ __device__ __forceinline__ unsigned long long lb_pack(uint32_t epoch, unsigned l
 __device__ __forceinline__ void set_status(FrameState* st, int code, uint32_t info)
 {
     if (atomicCAS(&st->status, 0, code) == 0) st->status_info = info;
+}
+
+__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Decoupled look-back by one full warp: the exclusive prefix of `tile` over the
+// per-tile values published in lb[] (one 64-bit entry per tile).  Lane l reads
+// predecessor (base - l), so each round trip inspects 32 tiles; entries are
+// consumed nearest-first up to the first inclusive one.  Tiles below 0 count
+// as an inclusive zero.  Bounded: after kSpinLimit empty rounds the status is
+// latched and the partial prefix returned.  All lanes return the same value.
+__device__ __forceinline__ uint32_t warp_lookback(const unsigned long long* lb, uint32_t tile,
+                                                  uint32_t tag, FrameState* st, uint32_t site)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t tg = tag & 0x3FFFFFFFu;
+    uint32_t prefix = 0;
+    int base = (int)tile - 1;
+    uint64_t spins = 0;
+    while (base >= 0) {
+        const int j = base - (int)lane;
+        bool ready = true, incl = true;
+        uint32_t val = 0;
+        if (j >= 0) {
+            const unsigned long long e = ld_acquire_u64(lb + j);
+            const unsigned long long flag = (e >> 32) & 3ull;
+            ready = ((uint32_t)(e >> 34) == tg) && flag != 0;
+            incl = flag == kFlagIncl;
+            val = (uint32_t)e;
+        }
+        const uint32_t nr = __ballot_sync(0xffffffffu, !ready);
+        const uint32_t first_nr = nr ? (uint32_t)(__ffs(nr) - 1) : 32u;
+        const uint32_t usable = first_nr == 32u ? 0xffffffffu : ((1u << first_nr) - 1u);
+        const uint32_t inc = __ballot_sync(0xffffffffu, ready && incl) & usable;
+        const uint32_t take = inc ? (uint32_t)__ffs(inc) : first_nr;   // lanes consumed
+        prefix += warp_sum_u32(lane < take ? val : 0u);
+        if (inc) break;
+        if (take == 0) {
+            if (++spins > kSpinLimit) {
+                set_status(st, kErrTimeout, site);
+                break;
+            }
+            __nanosleep(20);
+        }
+        base -= (int)take;
+    }
+    return prefix;
 }
 
 // ---------------------------------------------------------------------

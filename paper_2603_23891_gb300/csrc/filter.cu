@@ -104,29 +104,30 @@ void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits,
 // ---------------------------------------------------------------------------
 // Ancestor filter + compaction (persistent, dynamic tiles, decoupled look-back)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t lb_lookback(unsigned long long* lb, uint32_t tile, uint32_t tag,
-                                                FrameState* st)
+
+// Ancestor filter of one node with P: does any node of AP(n) (parent first) pass
+// R&L?  The path is read in batches of 8 independent loads, then the 8 P bits
+// are gathered together, so a walk costs ceil(depth / 8) x 2 round trips.
+__device__ __forceinline__ bool ancestor_blocked(const DevTree& t, const uint32_t* __restrict__ pbits,
+                                                 uint32_t n)
 {
-    // exclusive prefix of all tiles before `tile`; walks back until an inclusive entry
-    uint32_t prefix = 0;
-    int j = (int)tile - 1;
-    uint64_t spins = 0;
-    while (j >= 0) {
-        const unsigned long long v = ld_acquire_u64(lb + j);
-        const uint32_t vt = (uint32_t)(v >> 34);
-        const unsigned long long flag = (v >> 32) & 3ull;
-        if (vt != (tag & 0x3FFFFFFFu) || flag == 0) {
-            if (++spins > kSpinLimit) {
-                set_status(st, kErrTimeout, 0x100u);
-                return prefix;
-            }
-            continue;
+    for (uint32_t k0 = 0; k0 < t.depth; k0 += 8) {
+        uint32_t a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            a[q] = (k0 + q < t.depth) ? __ldg(t.ap + (size_t)(k0 + q) * t.n_pad + n) : kApPad;
+        uint32_t w[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w[q] = a[q] != kApPad ? __ldg(pbits + (a[q] >> 5)) : 0u;
+        bool end = false;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (a[q] == kApPad) { end = true; break; }
+            if ((w[q] >> (a[q] & 31)) & 1u) return true;
         }
-        prefix += (uint32_t)v;
-        if (flag == kFlagIncl) break;
-        --j;
+        if (end) return false;
     }
-    return prefix;
+    return false;
 }
 
 __global__ void __launch_bounds__(kFilterThreads) filter_anc_compact_kernel(
@@ -148,22 +149,18 @@ __global__ void __launch_bounds__(kFilterThreads) filter_anc_compact_kernel(
         const uint32_t tile = s_tile;
         if (tile >= n_tiles) break;
         const uint32_t base = tile * kFilterTile;
-        uint32_t ballots[kFilterItems];
-#pragma unroll 4
+        uint32_t pw[kFilterItems];
+#pragma unroll
         for (int it = 0; it < kFilterItems; ++it) {
             const uint32_t n = base + it * kFilterThreads + tid;
-            bool keep = false;
-            if (n < t.n) {
-                const uint32_t wbits = __ldg(pbits + (n >> 5));
-                if ((wbits >> (n & 31)) & 1u) {
-                    keep = true;
-                    for (uint32_t k = 0; k < t.depth; ++k) {
-                        const uint32_t a = __ldg(t.ap + (size_t)k * t.n_pad + n);
-                        if (a == kApPad) break;
-                        if ((__ldg(pbits + (a >> 5)) >> (a & 31)) & 1u) { keep = false; break; }
-                    }
-                }
-            }
+            pw[it] = n < t.n ? __ldg(pbits + (n >> 5)) : 0u;
+        }
+        uint32_t ballots[kFilterItems];
+#pragma unroll
+        for (int it = 0; it < kFilterItems; ++it) {
+            const uint32_t n = base + it * kFilterThreads + tid;
+            bool keep = n < t.n && ((pw[it] >> (n & 31)) & 1u);
+            if (keep) keep = !ancestor_blocked(t, pbits, n);
             ballots[it] = __ballot_sync(0xffffffffu, keep);
             if (lane == 0) s_cnt[it * 8 + warp] = __popc(ballots[it]);
         }
@@ -186,22 +183,24 @@ __global__ void __launch_bounds__(kFilterThreads) filter_anc_compact_kernel(
             for (uint32_t w = 0; w < warp; ++w) off += s_warp_tot[w];
             s_cnt[tid] = off + incl - v;
         }
-        if (tid == 0) {
+        if (warp == 0) {
             const uint32_t total = s_warp_tot[0] + s_warp_tot[1] + s_warp_tot[2] + s_warp_tot[3];
             uint32_t prefix = 0;
             if (tile == 0) {
-                st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, total));
+                if (lane == 0) st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, total));
             } else {
-                st_release_u64(lookback + tile, lb_pack(tag, kFlagAgg, total));
-                prefix = lb_lookback(lookback, tile, tag, st);
-                st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, prefix + total));
+                if (lane == 0) st_release_u64(lookback + tile, lb_pack(tag, kFlagAgg, total));
+                prefix = warp_lookback(lookback, tile, tag, st, 0x100u);
+                if (lane == 0) st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, prefix + total));
             }
-            s_prefix = prefix;
-            if (tile == n_tiles - 1) st->M = prefix + total;
+            if (lane == 0) {
+                s_prefix = prefix;
+                if (tile == n_tiles - 1) st->M = prefix + total;
+            }
         }
         __syncthreads();
         const uint32_t prefix = s_prefix;
-#pragma unroll 4
+#pragma unroll
         for (int it = 0; it < kFilterItems; ++it) {
             const uint32_t b = ballots[it];
             if ((b >> lane) & 1u) {

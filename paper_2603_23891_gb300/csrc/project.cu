@@ -28,17 +28,20 @@ constexpr float kY3c = 0.45704579946446572f;
 constexpr float kY3d = 0.37317633259011540f;
 constexpr float kY3e = 1.4453057213202769f;
 
+// Colour = sum_k Y_k(d) c[k][ch] + 0.5, clamped at 0.  The coefficients are
+// streamed as 16-byte loads (node-major, K*3 floats padded to a multiple of 4)
+// and accumulated on the fly; element e of the stream is (k, ch) = (e / 3, e % 3).
 __device__ __forceinline__ void sh_colour(const float* __restrict__ c, int deg, float x, float y,
                                           float z, float rgb[3])
 {
     float Y[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Y[k] = 0.0f;
     Y[0] = kY00;
-    int K = 1;
     if (deg >= 1) {
         Y[1] = -kY1 * y;
         Y[2] = kY1 * z;
         Y[3] = -kY1 * x;
-        K = 4;
     }
     if (deg >= 2) {
         const float xx = x * x, yy = y * y, zz = z * z;
@@ -47,7 +50,6 @@ __device__ __forceinline__ void sh_colour(const float* __restrict__ c, int deg, 
         Y[6] = kY2b * (2.0f * zz - xx - yy);
         Y[7] = -kY2a * x * z;
         Y[8] = kY2c * (xx - yy);
-        K = 9;
         if (deg >= 3) {
             Y[9] = -kY3a * y * (3.0f * xx - yy);
             Y[10] = kY3b * x * y * z;
@@ -56,21 +58,27 @@ __device__ __forceinline__ void sh_colour(const float* __restrict__ c, int deg, 
             Y[13] = -kY3c * x * (4.0f * zz - xx - yy);
             Y[14] = kY3e * z * (xx - yy);
             Y[15] = -kY3a * x * (xx - 3.0f * yy);
-            K = 16;
         }
     }
-    float r = 0.5f, g = 0.5f, b = 0.5f;
+    const int K = (deg + 1) * (deg + 1);
+    const int nq = (K * 3 + 3) >> 2;
+    float acc[3] = {0.5f, 0.5f, 0.5f};
+    const float4* c4 = reinterpret_cast<const float4*>(c);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        if (k < K) {
-            r += Y[k] * c[3 * k + 0];
-            g += Y[k] * c[3 * k + 1];
-            b += Y[k] * c[3 * k + 2];
+    for (int q = 0; q < 12; ++q) {
+        if (q < nq) {
+            const float4 f = __ldg(c4 + q);
+            const float e[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int el = 4 * q + r;          // compile-time after unrolling
+                if (el < 48) acc[el % 3] = fmaf(Y[el / 3], e[r], acc[el % 3]);
+            }
         }
     }
-    rgb[0] = fmaxf(r, 0.0f);
-    rgb[1] = fmaxf(g, 0.0f);
-    rgb[2] = fmaxf(b, 0.0f);
+    rgb[0] = fmaxf(acc[0], 0.0f);
+    rgb[1] = fmaxf(acc[1], 0.0f);
+    rgb[2] = fmaxf(acc[2], 0.0f);
 }
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi)
@@ -128,21 +136,7 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
             const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
             dx *= il; dy *= il; dz *= il;
             float rgb[3];
-            {
-                const float* c0 = t.sh + (size_t)n * t.sh_stride;
-                float coef[48];
-                const int nv = t.sh_stride >> 2;
-#pragma unroll
-                for (int q = 0; q < 12; ++q) {
-                    if (q < nv) {
-                        const float4 f = __ldg(reinterpret_cast<const float4*>(c0) + q);
-                        coef[4 * q] = f.x; coef[4 * q + 1] = f.y; coef[4 * q + 2] = f.z; coef[4 * q + 3] = f.w;
-                    } else {
-                        coef[4 * q] = coef[4 * q + 1] = coef[4 * q + 2] = coef[4 * q + 3] = 0.0f;
-                    }
-                }
-                sh_colour(coef, (int)t.sh_degree, dx, dy, dz, rgb);
-            }
+            sh_colour(t.sh + (size_t)n * t.sh_stride, (int)t.sh_degree, dx, dy, dz, rgb);
             float A = 0.0f, B = 0.0f, C = 0.0f, radius = 0.0f;
             if (inf && det > 0.0f) {
                 A = fd(c, det);
@@ -190,41 +184,55 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
             off += (w < (int)warp) ? tw : 0u;
             total += tw;
         }
-        if (tid == 0) {
+        if (warp == 0) {
             uint32_t prefix = 0;
             if (tile == 0) {
-                st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, total));
+                if (lane == 0) st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, total));
             } else {
-                st_release_u64(lookback + tile, lb_pack(tag, kFlagAgg, total));
-                int j = (int)tile - 1;
-                uint64_t spins = 0;
-                while (j >= 0) {
-                    const unsigned long long e = ld_acquire_u64(lookback + j);
-                    const unsigned long long flag = (e >> 32) & 3ull;
-                    if ((uint32_t)(e >> 34) != (tag & 0x3FFFFFFFu) || flag == 0) {
-                        if (++spins > kSpinLimit) { set_status(st, kErrTimeout, 0x200u); break; }
-                        continue;
-                    }
-                    prefix += (uint32_t)e;
-                    if (flag == kFlagIncl) break;
-                    --j;
-                }
-                st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, prefix + total));
+                if (lane == 0) st_release_u64(lookback + tile, lb_pack(tag, kFlagAgg, total));
+                prefix = warp_lookback(lookback, tile, tag, st, 0x200u);
+                if (lane == 0) st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, prefix + total));
             }
-            s_prefix = prefix;
-            if (tile == n_tiles - 1) st->n_pairs = (unsigned long long)prefix + total;
+            if (lane == 0) {
+                s_prefix = prefix;
+                if (tile == n_tiles - 1) st->n_pairs = (unsigned long long)prefix + total;
+            }
         }
         __syncthreads();
-        if (cnt) {
-            const unsigned long long first = (unsigned long long)s_prefix + off + incl - cnt;
-            if (first + cnt > cap) set_status(st, kErrCapacity, 0x300u);
-            unsigned long long idx = first;
-            for (int32_t ty = y0; ty < y1; ++ty) {
-                for (int32_t tx = x0; tx < x1; ++tx, ++idx) {
+        // Warp-cooperative emission: the warp's pairs are numbered 0..wtot-1 in
+        // (Gaussian, row-major tile) order and written by consecutive lanes, so
+        // stores are contiguous.  Pair q belongs to the lane whose inclusive
+        // count first exceeds q (binary search over the warp's scan).
+        {
+            const unsigned long long wfirst = (unsigned long long)s_prefix + off + 0ull;
+            const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t excl = incl - cnt;
+            const int32_t rw = x1 - x0;
+            if (lane == 0 && wfirst + wtot > cap && wtot) set_status(st, kErrCapacity, 0x300u);
+            for (uint32_t q0 = 0; q0 < wtot; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                // owner: smallest lane L with incl(L) > q
+                uint32_t lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t probe = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                    if (probe <= q) lo += step;
+                }
+                const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, lo);
+                const int32_t o_x0 = __shfl_sync(0xffffffffu, x0, lo);
+                const int32_t o_rw = __shfl_sync(0xffffffffu, rw, lo);
+                const int32_t o_y0 = __shfl_sync(0xffffffffu, y0, lo);
+                const uint32_t o_d = __shfl_sync(0xffffffffu, dbits, lo);
+                const uint32_t o_m = __shfl_sync(0xffffffffu, m, lo);
+                if (q < wtot) {
+                    const unsigned long long idx = wfirst + q;
                     if (idx < cap) {
+                        const int32_t k = (int32_t)(q - o_excl);
+                        const int32_t ty = o_y0 + k / o_rw;
+                        const int32_t tx = o_x0 + k % o_rw;
                         const unsigned long long tl = (unsigned long long)(ty * cam.tiles_x + tx);
-                        keys[idx] = (tl << 32) | dbits;
-                        vals[idx] = m;
+                        keys[idx] = (tl << 32) | o_d;
+                        vals[idx] = o_m;
                     }
                 }
             }

@@ -144,19 +144,33 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(
         if (tile == 0) {
             st_release_u64(lb, lb_pack(tag, kFlagIncl, cnt));
         } else {
+            // each round trip reads this digit's entry of up to 8 preceding tiles at once
             st_release_u64(lb, lb_pack(tag, kFlagAgg, cnt));
+            const uint32_t tg = tag & 0x3FFFFFFFu;
             int j = (int)tile - 1;
             uint64_t spins = 0;
             while (j >= 0) {
-                const unsigned long long e = ld_acquire_u64(lookback + (size_t)j * 256 + tid);
-                const unsigned long long flag = (e >> 32) & 3ull;
-                if ((uint32_t)(e >> 34) != (tag & 0x3FFFFFFFu) || flag == 0) {
-                    if (++spins > kSpinLimit) { set_status(st, kErrTimeout, 0x400u + (uint32_t)pass); break; }
-                    continue;
+                unsigned long long e[kLookbackRows];
+#pragma unroll
+                for (int q = 0; q < kLookbackRows; ++q)
+                    e[q] = (j - q >= 0) ? ld_acquire_u64(lookback + (size_t)(j - q) * 256 + tid) : 0ull;
+                int used = 0;
+                bool done = false;
+#pragma unroll
+                for (int q = 0; q < kLookbackRows; ++q) {
+                    if (j - q < 0) { done = true; break; }
+                    const unsigned long long flag = (e[q] >> 32) & 3ull;
+                    if ((uint32_t)(e[q] >> 34) != tg || flag == 0) break;
+                    prefix += (uint32_t)e[q];
+                    ++used;
+                    if (flag == kFlagIncl) { done = true; break; }
                 }
-                prefix += (uint32_t)e;
-                if (flag == kFlagIncl) break;
-                --j;
+                if (done) break;
+                if (used == 0) {
+                    if (++spins > kSpinLimit) { set_status(st, kErrTimeout, 0x400u + (uint32_t)pass); break; }
+                    __nanosleep(20);
+                }
+                j -= used;
             }
             st_release_u64(lb, lb_pack(tag, kFlagIncl, prefix + cnt));
         }

@@ -223,3 +223,24 @@ def test_invalid_inputs_rejected(renderer, tiny):
     with pytest.raises(filtergs.FgsError) as e:
         filtergs.fgs_load_tree(renderer.ctx, t2)
     assert e.value.code == filtergs.FGS_ERR_TREE
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_needles_and_blobs_culling_exact(renderer, seed):
+    """Very elongated and very large Gaussians at random orientations: the per-warp culling
+    of the blend (and its fallback for ill-conditioned conics) leaves every pixel's
+    decisions unchanged, so T stays bit-identical."""
+    rng = np.random.default_rng(100 + seed)
+    n = 400
+    mu = np.stack([rng.uniform(-6, 6, n), rng.uniform(6, 30, n), rng.uniform(-4, 4, n)], 1)
+    logs = np.stack([rng.uniform(-5, -3, n), rng.uniform(-5, -3, n), rng.uniform(-0.5, 1.5, n)], 1)
+    big = rng.random(n) < 0.15
+    logs[big] = rng.uniform(-0.5, 0.8, (big.sum(), 3))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    t = synth.tree_from_gaussians(mu, logs, q, rng.normal(1.0, 1.5, n), rng.normal(0, 1, (n, 1, 3)), 0)
+    renderer.load_tree(t)
+    cam = synth.look_at_camera([0, 0, 0], [0, 1, 0], 192, 160, 70.0)
+    g = gpu_frame(renderer, t, cam, -1.0)
+    o, _ = oracle_frame(t, cam, -1.0)
+    assert_frame_parity(g, o)
