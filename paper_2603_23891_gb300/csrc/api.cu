@@ -45,7 +45,8 @@ struct fgs_ctx {
     std::string err;
     fgs_params params{};
     // occupancy (resident blocks per SM)
-    int occ_pred = 1, occ_anc = 1, occ_proj = 1, occ_hist = 1, occ_sort = 1, occ_ranges = 1;
+    int occ_pred = 1, occ_anc = 1, occ_compact = 1, occ_proj = 1, occ_hist = 1, occ_sort = 1,
+        occ_ranges = 1;
     // tree
     bool has_tree = false;
     DevTree tree{};
@@ -58,6 +59,7 @@ struct fgs_ctx {
     // node-sized frame buffers
     size_t node_cap = 0;
     uint32_t* pbits = nullptr;
+    uint32_t* selbits = nullptr;
     uint32_t* sel = nullptr;
     float* splat = nullptr;
     unsigned long long* lb_compact = nullptr;
@@ -150,9 +152,10 @@ int ensure_nodes(fgs_ctx* c, size_t n_pad)
     if (n_pad <= c->node_cap) return FGS_OK;
     int r;
     if ((r = grow(c, (void**)&c->pbits, n_pad / 32 * 4))) return r;
+    if ((r = grow(c, (void**)&c->selbits, n_pad / 32 * 4))) return r;
     if ((r = grow(c, (void**)&c->sel, n_pad * 4))) return r;
     if ((r = grow(c, (void**)&c->splat, n_pad * kSplatStride * 4))) return r;
-    if ((r = grow(c, (void**)&c->lb_compact, (n_pad / kFilterTile + 2) * 8))) return r;
+    if ((r = grow(c, (void**)&c->lb_compact, (n_pad / 32 / kCompactWords + 2) * 8))) return r;
     if ((r = grow(c, (void**)&c->lb_project, (n_pad / kProjThreads + 2) * 8))) return r;
     c->node_cap = n_pad;
     return FGS_OK;
@@ -230,8 +233,10 @@ int enqueue_front(fgs_ctx* c, const DevCamera& dc, cudaStream_t s, cudaEvent_t* 
     launch_filter_pred(c->tree, dc, c->pbits, c->sms * c->occ_pred, s);
     launches += 2;
     if (ev) cudaEventRecord(ev[1], s);
-    launch_filter_anc_compact(c->tree, c->pbits, c->sel, c->lb_compact, c->st, c->sms * c->occ_anc, s);
-    ++launches;
+    launch_filter_anc(c->tree, c->pbits, c->selbits, c->sms * c->occ_anc, s);
+    launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->lb_compact, c->st,
+                   c->sms * c->occ_compact, s);
+    launches += 2;
     if (ev) cudaEventRecord(ev[2], s);
     launch_project_emit(c->tree, dc, c->sel, c->splat, c->keys0, c->vals0, c->pair_cap,
                         c->lb_project, c->st, c->sms * c->occ_proj, s);
@@ -299,6 +304,7 @@ int fgs_create(fgs_ctx** out, int device)
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
     c->occ_pred = occ_filter_pred();
     c->occ_anc = occ_filter_anc();
+    c->occ_compact = occ_compact();
     c->occ_proj = occ_project();
     c->occ_hist = occ_sort_hist();
     c->occ_sort = occ_sort_pass();
@@ -328,7 +334,7 @@ int fgs_destroy(fgs_ctx* c)
     if (!c) return FGS_OK;
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
-    void* bufs[] = {c->tree_mem, c->pbits, c->sel, c->splat, c->lb_compact, c->lb_project,
+    void* bufs[] = {c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->lb_project,
                     c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->lb_sort, c->ranges,
                     c->G, c->img, c->st};
     for (void* p : bufs) free_ptr(p);
@@ -564,7 +570,9 @@ int fgs_filter(fgs_ctx* c, void* stream, uint32_t* sel_out, uint32_t cap, uint32
     const DevCamera dc = make_devcam(c, false);
     launch_frame_begin(c->st, c->ranges, dc.tiles_x * dc.tiles_y, s);
     launch_filter_pred(c->tree, dc, c->pbits, c->sms * c->occ_pred, s);
-    launch_filter_anc_compact(c->tree, c->pbits, c->sel, c->lb_compact, c->st, c->sms * c->occ_anc, s);
+    launch_filter_anc(c->tree, c->pbits, c->selbits, c->sms * c->occ_anc, s);
+    launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->lb_compact, c->st,
+                   c->sms * c->occ_compact, s);
     FGS_CUDA(c, cudaGetLastError());
     c->have_frame = false;
     if (out_is_device) {

@@ -16,14 +16,13 @@ namespace fgs {
 constexpr int kStages = 6;
 constexpr uint32_t kApPad = 0xFFFFFFFFu;
 constexpr int kSplatStride = 12;          // floats per splat record (48 B)
-constexpr int kSortTileItems = 16;        // keys per thread in a sort tile
+constexpr int kSortTileItems = 8;         // keys per thread in a sort tile
 constexpr int kSortThreads = 256;
-constexpr int kSortTile = kSortTileItems * kSortThreads;   // 4096 keys
+constexpr int kSortTile = kSortTileItems * kSortThreads;   // 2048 keys
 constexpr int kMaxSortPasses = 6;         // 48 key bits: 32 depth + up to 16 tile bits
-constexpr int kLookbackRows = 8;          // predecessor tiles read per look-back round trip
-constexpr int kFilterItems = 16;          // nodes per thread in the ancestor/compaction kernel
-constexpr int kFilterThreads = 256;
-constexpr int kFilterTile = kFilterItems * kFilterThreads;  // 4096 nodes
+constexpr int kLookbackRows = 16;         // predecessor tiles read per look-back round trip
+constexpr int kFilterTile = 4096;         // node arrays are padded to a multiple of this
+constexpr int kCompactWords = 1024;       // 32-bit selection words per compaction tile (32K nodes)
 constexpr int kProjThreads = 256;         // selected Gaussians per projection tile
 constexpr uint64_t kSpinLimit = 1ull << 24;   // bounded spin-waits
 
@@ -262,6 +261,7 @@ __device__ __forceinline__ uint32_t warp_lookback(const unsigned long long* lb, 
 // Resident blocks per SM of each persistent / grid-stride kernel (occupancy API).
 int occ_filter_pred();
 int occ_filter_anc();
+int occ_compact();
 int occ_project();
 int occ_sort_hist();
 int occ_sort_pass();
@@ -273,9 +273,10 @@ size_t sort_smem_bytes();
 void launch_frame_begin(FrameState* st, uint2* ranges, int n_tiles, cudaStream_t s);
 void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits, int blocks,
                         cudaStream_t s);
-void launch_filter_anc_compact(const DevTree& t, const uint32_t* pbits, uint32_t* sel,
-                               unsigned long long* lookback, FrameState* st, int blocks,
-                               cudaStream_t s);
+void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, int blocks,
+                       cudaStream_t s);
+void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel,
+                    unsigned long long* lookback, FrameState* st, int blocks, cudaStream_t s);
 void launch_project_emit(const DevTree& t, const DevCamera& cam, const uint32_t* sel,
                          float* splat, unsigned long long* keys, uint32_t* vals,
                          unsigned long long cap, unsigned long long* lookback, FrameState* st,

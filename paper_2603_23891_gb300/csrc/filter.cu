@@ -5,10 +5,11 @@
 //                     SoA centres with 16-byte loads; the covariance is read only
 //                     for in-frustum internal nodes (a leaf passes on the frustum
 //                     test alone).  Output: one bit per node.
-//  filter_anc_compact Ancestor filter + stream compaction: a node with P walks its
-//                     ancestor path AP (parent first, stopping at the first ancestor
-//                     with P); survivors are compacted in ascending id order by warp
-//                     ballots, a block scan and a decoupled look-back across tiles.
+//  filter_anc         Ancestor filter: a node with P walks its ancestor path AP
+//                     (parent first, stopping at the first ancestor with P); one bit
+//                     per node for the survivors.
+//  compact            Stream compaction of the survivor bits into ascending node ids
+//                     (popcounts, block scan, decoupled look-back across tiles).
 #include "fgs_internal.cuh"
 
 namespace fgs {
@@ -130,61 +131,118 @@ __device__ __forceinline__ bool ancestor_blocked(const DevTree& t, const uint32_
     return false;
 }
 
-__global__ void __launch_bounds__(kFilterThreads) filter_anc_compact_kernel(
-    DevTree t, const uint32_t* __restrict__ pbits, uint32_t* __restrict__ sel,
-    unsigned long long* lookback, FrameState* st)
+// Ancestor filter (§3.2): sel(n) = P(n) and no node of AP(n) has P.  One node per
+// lane, a warp per 32-node word of the bit arrays; two words per warp iteration
+// so that two nodes' ancestor-path loads are in flight per lane.  No barriers.
+__global__ void __launch_bounds__(256) filter_anc_kernel(DevTree t, const uint32_t* __restrict__ pbits,
+                                                         uint32_t* __restrict__ selbits)
 {
-    __shared__ uint32_t s_cnt[kFilterItems * 8];
-    __shared__ uint32_t s_warp_tot[4];
-    __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_prefix;
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t n_tiles = (t.n + kFilterTile - 1) / kFilterTile;
-    const uint32_t tag = st->epoch * 16u + 0u;
-    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t n_words = t.n_pad >> 5;
+    const uint32_t warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w0 = warp_g * 2; w0 < n_words; w0 += n_warps * 2) {
+        const uint32_t w1 = w0 + 1;                       // n_words is even (n_pad % 4096 == 0)
+        const uint32_t pw0 = __ldg(pbits + w0), pw1 = __ldg(pbits + w1);
+        const uint32_t n0 = (w0 << 5) + lane, n1 = (w1 << 5) + lane;
+        bool k0 = (pw0 >> lane) & 1u, k1 = (pw1 >> lane) & 1u;
+        if (k0 && k1) {
+            // both lanes walk: interleave the two paths' loads
+            for (uint32_t kb = 0; kb < t.depth && (k0 || k1); kb += 8) {
+                uint32_t a0[8], a1[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const bool in = kb + q < t.depth;
+                    a0[q] = (in && k0) ? __ldg(t.ap + (size_t)(kb + q) * t.n_pad + n0) : kApPad;
+                    a1[q] = (in && k1) ? __ldg(t.ap + (size_t)(kb + q) * t.n_pad + n1) : kApPad;
+                }
+                uint32_t b0[8], b1[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    b0[q] = a0[q] != kApPad ? __ldg(pbits + (a0[q] >> 5)) : 0u;
+                    b1[q] = a1[q] != kApPad ? __ldg(pbits + (a1[q] >> 5)) : 0u;
+                }
+                bool end0 = !k0, end1 = !k1;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (!end0) {
+                        if (a0[q] == kApPad) end0 = true;
+                        else if ((b0[q] >> (a0[q] & 31)) & 1u) { k0 = false; end0 = true; }
+                    }
+                    if (!end1) {
+                        if (a1[q] == kApPad) end1 = true;
+                        else if ((b1[q] >> (a1[q] & 31)) & 1u) { k1 = false; end1 = true; }
+                    }
+                }
+                if (end0 && end1) break;
+            }
+        } else {
+            if (k0) k0 = !ancestor_blocked(t, pbits, n0);
+            if (k1) k1 = !ancestor_blocked(t, pbits, n1);
+        }
+        k0 = k0 && n0 < t.n;
+        k1 = k1 && n1 < t.n;
+        const uint32_t s0 = __ballot_sync(0xffffffffu, k0);
+        const uint32_t s1 = __ballot_sync(0xffffffffu, k1);
+        if (lane == 0) selbits[w0] = s0;
+        if (lane == 1) selbits[w1] = s1;
+    }
+}
 
+void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, int blocks,
+                       cudaStream_t s)
+{
+    const uint32_t n_words = t.n_pad >> 5;
+    int need = (int)((n_words / 2 * 32 + 255) / 256);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    filter_anc_kernel<<<blocks, 256, 0, s>>>(t, pbits, selbits);
+}
+
+// Stream compaction of the selection bits into ascending node ids.  Tiles of
+// kCompactWords 32-bit words (4 per thread); popcounts, a block scan, and a
+// warp-parallel decoupled look-back across tiles give each word its first slot.
+__global__ void __launch_bounds__(256) compact_kernel(const uint32_t* __restrict__ selbits,
+                                                      uint32_t n_words, uint32_t* __restrict__ sel,
+                                                      unsigned long long* lookback, FrameState* st)
+{
+    __shared__ uint32_t s_warp_tot[8];
+    __shared__ uint32_t s_tile, s_prefix;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t n_tiles = (n_words + kCompactWords - 1) / kCompactWords;
+    const uint32_t tag = st->epoch * 16u + 0u;
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(&st->tickets[kTicketCompact], 1u);
         __syncthreads();
         const uint32_t tile = s_tile;
         if (tile >= n_tiles) break;
-        const uint32_t base = tile * kFilterTile;
-        uint32_t pw[kFilterItems];
-#pragma unroll
-        for (int it = 0; it < kFilterItems; ++it) {
-            const uint32_t n = base + it * kFilterThreads + tid;
-            pw[it] = n < t.n ? __ldg(pbits + (n >> 5)) : 0u;
+        const uint32_t wbase = tile * kCompactWords + tid * 4;
+        uint4 wv = make_uint4(0, 0, 0, 0);
+        if (wbase + 3 < n_words) {
+            wv = __ldg(reinterpret_cast<const uint4*>(selbits + wbase));
+        } else {
+            if (wbase < n_words) wv.x = __ldg(selbits + wbase);
+            if (wbase + 1 < n_words) wv.y = __ldg(selbits + wbase + 1);
+            if (wbase + 2 < n_words) wv.z = __ldg(selbits + wbase + 2);
         }
-        uint32_t ballots[kFilterItems];
+        const uint32_t c0 = __popc(wv.x), c1 = __popc(wv.y), c2 = __popc(wv.z), c3 = __popc(wv.w);
+        const uint32_t cnt = c0 + c1 + c2 + c3;
+        uint32_t incl = cnt;
 #pragma unroll
-        for (int it = 0; it < kFilterItems; ++it) {
-            const uint32_t n = base + it * kFilterThreads + tid;
-            bool keep = n < t.n && ((pw[it] >> (n & 31)) & 1u);
-            if (keep) keep = !ancestor_blocked(t, pbits, n);
-            ballots[it] = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0) s_cnt[it * 8 + warp] = __popc(ballots[it]);
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += u;
         }
+        if (lane == 31) s_warp_tot[warp] = incl;
         __syncthreads();
-        // exclusive scan of the 128 (item, warp) counts in id order
-        uint32_t v = 0, incl = 0;
-        if (tid < kFilterItems * 8) {
-            v = s_cnt[tid];
-            incl = v;
+        uint32_t off = 0, total = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= (uint32_t)o) incl += u;
-            }
-            if (lane == 31) s_warp_tot[warp] = incl;
-        }
-        __syncthreads();
-        if (tid < kFilterItems * 8) {
-            uint32_t off = 0;
-            for (uint32_t w = 0; w < warp; ++w) off += s_warp_tot[w];
-            s_cnt[tid] = off + incl - v;
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t tw = s_warp_tot[w];
+            off += (w < (int)warp) ? tw : 0u;
+            total += tw;
         }
         if (warp == 0) {
-            const uint32_t total = s_warp_tot[0] + s_warp_tot[1] + s_warp_tot[2] + s_warp_tot[3];
             uint32_t prefix = 0;
             if (tile == 0) {
                 if (lane == 0) st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, total));
@@ -199,27 +257,30 @@ __global__ void __launch_bounds__(kFilterThreads) filter_anc_compact_kernel(
             }
         }
         __syncthreads();
-        const uint32_t prefix = s_prefix;
-#pragma unroll
-        for (int it = 0; it < kFilterItems; ++it) {
-            const uint32_t b = ballots[it];
-            if ((b >> lane) & 1u) {
-                const uint32_t pos = prefix + s_cnt[it * 8 + warp] + __popc(b & lt_mask);
-                sel[pos] = base + it * kFilterThreads + tid;
-            }
+        // warp-cooperative expansion: the warp's 128 words in order, one bit per lane
+        const uint32_t p0 = s_prefix + off + incl - cnt;       // first slot of this lane's words
+        const uint32_t lt = (1u << lane) - 1u;
+        const uint32_t wbase_warp = tile * kCompactWords + warp * 128;
+        for (uint32_t q = 0; q < 128; ++q) {
+            const uint32_t owner = q >> 2, sub = q & 3;
+            const uint32_t mine = sub == 0 ? wv.x : sub == 1 ? wv.y : sub == 2 ? wv.z : wv.w;
+            const uint32_t before = sub == 0 ? 0u : sub == 1 ? c0 : sub == 2 ? c0 + c1 : c0 + c1 + c2;
+            const uint32_t wq = __shfl_sync(0xffffffffu, mine, owner);
+            if (wq == 0u) continue;
+            const uint32_t bq = __shfl_sync(0xffffffffu, p0 + before, owner);
+            if ((wq >> lane) & 1u) sel[bq + __popc(wq & lt)] = ((wbase_warp + q) << 5) + lane;
         }
         __syncthreads();
     }
 }
 
-void launch_filter_anc_compact(const DevTree& t, const uint32_t* pbits, uint32_t* sel,
-                               unsigned long long* lookback, FrameState* st, int blocks,
-                               cudaStream_t s)
+void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel,
+                    unsigned long long* lookback, FrameState* st, int blocks, cudaStream_t s)
 {
-    const int n_tiles = (int)((t.n + kFilterTile - 1) / kFilterTile);
+    const int n_tiles = (int)((n_words + kCompactWords - 1) / kCompactWords);
     if (blocks > n_tiles) blocks = n_tiles;
     if (blocks < 1) blocks = 1;
-    filter_anc_compact_kernel<<<blocks, kFilterThreads, 0, s>>>(t, pbits, sel, lookback, st);
+    compact_kernel<<<blocks, 256, 0, s>>>(selbits, n_words, sel, lookback, st);
 }
 
 int occ_filter_pred()
@@ -232,7 +293,14 @@ int occ_filter_pred()
 int occ_filter_anc()
 {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, filter_anc_compact_kernel, kFilterThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, filter_anc_kernel, 256, 0);
+    return b > 0 ? b : 1;
+}
+
+int occ_compact()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, compact_kernel, 256, 0);
     return b > 0 ? b : 1;
 }
 
