@@ -16,13 +16,14 @@ namespace fgs {
 constexpr int kStages = 6;
 constexpr uint32_t kApPad = 0xFFFFFFFFu;
 constexpr int kSplatStride = 12;          // floats per splat record (48 B)
-constexpr int kSortTileItems = 8;         // keys per thread in a sort tile
+constexpr int kSortTileItems = 16;        // keys per thread in a sort tile
 constexpr int kSortThreads = 256;
-constexpr int kSortTile = kSortTileItems * kSortThreads;   // 2048 keys
+constexpr int kSortTile = kSortTileItems * kSortThreads;   // 4096 keys
 constexpr int kMaxSortPasses = 6;         // 48 key bits: 32 depth + up to 16 tile bits
-constexpr int kLookbackRows = 16;         // predecessor tiles read per look-back round trip
+constexpr int kLookbackRows = 8;          // predecessor tiles read per look-back round trip
 constexpr int kFilterTile = 4096;         // node arrays are padded to a multiple of this
 constexpr int kCompactWords = 1024;       // 32-bit selection words per compaction tile (32K nodes)
+constexpr int kAncCacheWords = 4096;      // P-bit words of the lowest node ids kept in shared memory
 constexpr int kProjThreads = 256;         // selected Gaussians per projection tile
 constexpr uint64_t kSpinLimit = 1ull << 24;   // bounded spin-waits
 

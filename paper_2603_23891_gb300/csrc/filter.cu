@@ -106,86 +106,58 @@ void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits,
 // Ancestor filter + compaction (persistent, dynamic tiles, decoupled look-back)
 // ---------------------------------------------------------------------------
 
-// Ancestor filter of one node with P: does any node of AP(n) (parent first) pass
-// R&L?  The path is read in batches of 8 independent loads, then the 8 P bits
-// are gathered together, so a walk costs ceil(depth / 8) x 2 round trips.
-__device__ __forceinline__ bool ancestor_blocked(const DevTree& t, const uint32_t* __restrict__ pbits,
-                                                 uint32_t n)
+// Ancestor filter (§3.2): sel(n) = P(n) and no node of AP(n) has P.  One node per
+// lane, a warp per 32-node word of the bit arrays (grid-stride over words, the
+// next word's P bits prefetched).  A node with P reads up to 16 levels of its
+// ancestor path in one batch of independent loads, then the ancestors' P bits,
+// so a walk costs two dependent round trips for trees up to 16 levels deep.
+// The P bits of the lowest kAncCacheWords * 32 node ids sit in shared memory:
+// with level-major ids those are the upper levels every path crosses.
+__device__ __forceinline__ bool ancestor_blocked16(const DevTree& t, const uint32_t* __restrict__ pbits,
+                                                   const uint32_t* s_pb, uint32_t cached_words,
+                                                   uint32_t n)
 {
-    for (uint32_t k0 = 0; k0 < t.depth; k0 += 8) {
-        uint32_t a[8];
+    for (uint32_t k0 = 0; k0 < t.depth; k0 += 16) {
+        uint32_t a[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
+        for (int q = 0; q < 16; ++q)
             a[q] = (k0 + q < t.depth) ? __ldg(t.ap + (size_t)(k0 + q) * t.n_pad + n) : kApPad;
-        uint32_t w[8];
+        uint32_t w[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) w[q] = a[q] != kApPad ? __ldg(pbits + (a[q] >> 5)) : 0u;
-        bool end = false;
+        for (int q = 0; q < 16; ++q) {
+            const uint32_t wi = a[q] >> 5;
+            w[q] = a[q] == kApPad ? 0u : (wi < cached_words ? s_pb[wi] : __ldg(pbits + wi));
+        }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if (a[q] == kApPad) { end = true; break; }
+        for (int q = 0; q < 16; ++q) {
+            if (a[q] == kApPad) return false;
             if ((w[q] >> (a[q] & 31)) & 1u) return true;
         }
-        if (end) return false;
     }
     return false;
 }
 
-// Ancestor filter (§3.2): sel(n) = P(n) and no node of AP(n) has P.  One node per
-// lane, a warp per 32-node word of the bit arrays; two words per warp iteration
-// so that two nodes' ancestor-path loads are in flight per lane.  No barriers.
 __global__ void __launch_bounds__(256) filter_anc_kernel(DevTree t, const uint32_t* __restrict__ pbits,
                                                          uint32_t* __restrict__ selbits)
 {
+    __shared__ uint32_t s_pb[kAncCacheWords];
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t n_words = t.n_pad >> 5;
-    const uint32_t warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t cw = n_words < (uint32_t)kAncCacheWords ? n_words : (uint32_t)kAncCacheWords;
+    for (uint32_t i = threadIdx.x; i < cw; i += blockDim.x) s_pb[i] = __ldg(pbits + i);
+    __syncthreads();
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t w0 = warp_g * 2; w0 < n_words; w0 += n_warps * 2) {
-        const uint32_t w1 = w0 + 1;                       // n_words is even (n_pad % 4096 == 0)
-        const uint32_t pw0 = __ldg(pbits + w0), pw1 = __ldg(pbits + w1);
-        const uint32_t n0 = (w0 << 5) + lane, n1 = (w1 << 5) + lane;
-        bool k0 = (pw0 >> lane) & 1u, k1 = (pw1 >> lane) & 1u;
-        if (k0 && k1) {
-            // both lanes walk: interleave the two paths' loads
-            for (uint32_t kb = 0; kb < t.depth && (k0 || k1); kb += 8) {
-                uint32_t a0[8], a1[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const bool in = kb + q < t.depth;
-                    a0[q] = (in && k0) ? __ldg(t.ap + (size_t)(kb + q) * t.n_pad + n0) : kApPad;
-                    a1[q] = (in && k1) ? __ldg(t.ap + (size_t)(kb + q) * t.n_pad + n1) : kApPad;
-                }
-                uint32_t b0[8], b1[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    b0[q] = a0[q] != kApPad ? __ldg(pbits + (a0[q] >> 5)) : 0u;
-                    b1[q] = a1[q] != kApPad ? __ldg(pbits + (a1[q] >> 5)) : 0u;
-                }
-                bool end0 = !k0, end1 = !k1;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (!end0) {
-                        if (a0[q] == kApPad) end0 = true;
-                        else if ((b0[q] >> (a0[q] & 31)) & 1u) { k0 = false; end0 = true; }
-                    }
-                    if (!end1) {
-                        if (a1[q] == kApPad) end1 = true;
-                        else if ((b1[q] >> (a1[q] & 31)) & 1u) { k1 = false; end1 = true; }
-                    }
-                }
-                if (end0 && end1) break;
-            }
-        } else {
-            if (k0) k0 = !ancestor_blocked(t, pbits, n0);
-            if (k1) k1 = !ancestor_blocked(t, pbits, n1);
-        }
-        k0 = k0 && n0 < t.n;
-        k1 = k1 && n1 < t.n;
-        const uint32_t s0 = __ballot_sync(0xffffffffu, k0);
-        const uint32_t s1 = __ballot_sync(0xffffffffu, k1);
-        if (lane == 0) selbits[w0] = s0;
-        if (lane == 1) selbits[w1] = s1;
+    uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t pw = w < n_words ? __ldg(pbits + w) : 0u;
+    for (; w < n_words; w += n_warps) {
+        const uint32_t wn = w + n_warps;
+        const uint32_t pw_next = wn < n_words ? __ldg(pbits + wn) : 0u;
+        const uint32_t n = (w << 5) + lane;
+        bool keep = ((pw >> lane) & 1u) && n < t.n;
+        if (keep) keep = !ancestor_blocked16(t, pbits, s_pb, cw, n);
+        const uint32_t b = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) selbits[w] = b;
+        pw = pw_next;
     }
 }
 
@@ -193,7 +165,7 @@ void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbit
                        cudaStream_t s)
 {
     const uint32_t n_words = t.n_pad >> 5;
-    int need = (int)((n_words / 2 * 32 + 255) / 256);
+    int need = (int)((n_words * 32 + 255) / 256);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     filter_anc_kernel<<<blocks, 256, 0, s>>>(t, pbits, selbits);

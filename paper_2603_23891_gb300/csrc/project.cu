@@ -109,43 +109,39 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
         const uint32_t tile = s_tile;
         if (tile >= n_tiles) break;
         const uint32_t m = tile * kProjThreads + tid;
-        uint32_t cnt = 0;
+        const bool valid = m < M;
+        // ---- 1. everything that decides the pair count (decision-exact binary32)
+        uint32_t cnt = 0, n = 0;
         int32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-        uint32_t dbits = 0;
-        if (m < M) {
-            const uint32_t n = __ldg(sel + m);
+        float mx = 0.0f, my = 0.0f, mz = 0.0f, vz = 0.0f, u = 0.0f, v = 0.0f;
+        float A = 0.0f, B = 0.0f, C = 0.0f, radius = 0.0f, a0 = 0.0f, lthr = 0.0f;
+        if (valid) {
+            n = __ldg(sel + m);
             const size_t np = t.n_pad;
-            const float mx = __ldg(t.mu + n), my = __ldg(t.mu + np + n), mz = __ldg(t.mu + 2 * np + n);
-            float vx, vy, vz, txtz = 0.0f, tytz = 0.0f;
-            camera_space(cam, mx, my, mz, vx, vy, vz);
-            const bool inf = frustum_test(cam, vx, vy, vz, txtz, tytz);
+            mx = __ldg(t.mu + n);
+            my = __ldg(t.mu + np + n);
+            mz = __ldg(t.mu + 2 * np + n);
             float s6[6];
 #pragma unroll
             for (int q = 0; q < 6; ++q) s6[q] = __ldg(t.cov + q * np + n);
+            a0 = __ldg(t.opacity + n);
+            const float ln_a0 = __ldg(t.ln_opacity + n);
+            float vx, vy, txtz = 0.0f, tytz = 0.0f;
+            camera_space(cam, mx, my, mz, vx, vy, vz);
+            const bool inf = frustum_test(cam, vx, vy, vz, txtz, tytz);
             float a = 0.0f, b = 0.0f, c = 0.0f, lam = 0.0f;
             if (inf) ewa_cov2d(cam, vz, txtz, tytz, s6, a, b, c, lam);
-            const float u = fa(fm(cam.fx, fd(vx, vz)), cam.cx);
-            const float v = fa(fm(cam.fy, fd(vy, vz)), cam.cy);
+            u = fa(fm(cam.fx, fd(vx, vz)), cam.cx);
+            v = fa(fm(cam.fy, fd(vy, vz)), cam.cy);
             const float det = fs(fm(a, c), fm(b, b));
-            const float a0 = __ldg(t.opacity + n);
-            const float ln_a0 = __ldg(t.ln_opacity + n);
-            const float lthr = fs(-5.5412635451584258f, ln_a0);   // -ln 255 - ln alpha0
-
-            // colour: direction from the camera centre, SH basis, + 0.5, clamp at 0
-            float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
-            const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-            dx *= il; dy *= il; dz *= il;
-            float rgb[3];
-            sh_colour(t.sh + (size_t)n * t.sh_stride, (int)t.sh_degree, dx, dy, dz, rgb);
-            float A = 0.0f, B = 0.0f, C = 0.0f, radius = 0.0f;
+            lthr = fs(-5.5412635451584258f, ln_a0);   // -ln 255 - ln alpha0
             if (inf && det > 0.0f) {
                 A = fd(c, det);
                 B = fd(-b, det);
                 C = fd(a, det);
                 // 3-sigma radius, or the radius where alpha0 e^{-r^2/(2 lambda)} = tau,
                 // capped at 3 sigma; alpha0 <= tau emits nothing (§3.3)
-                const float r3 = fm(3.0f, fsq(lam));
-                float r = r3;
+                float r = fm(3.0f, fsq(lam));
                 bool drop = false;
                 if (cam.shrink) {
                     const float g = fm(2.0f, fs(ln_a0, cam.ln_tau));
@@ -162,13 +158,8 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
                     if (x1 > x0 && y1 > y0) cnt = (uint32_t)((x1 - x0) * (y1 - y0));
                 }
             }
-            dbits = __float_as_uint(vz);
-            float4* out = reinterpret_cast<float4*>(splat + (size_t)m * kSplatStride);
-            out[0] = make_float4(u, v, A, B);
-            out[1] = make_float4(C, lthr, a0, vz);
-            out[2] = make_float4(rgb[0], rgb[1], rgb[2], radius);
         }
-        // block exclusive scan of cnt
+        // ---- 2. block scan of the pair counts, publish the tile aggregate
         uint32_t incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -198,20 +189,31 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
                 if (tile == n_tiles - 1) st->n_pairs = (unsigned long long)prefix + total;
             }
         }
+        // ---- 3. colour and splat record (overlaps the look-back of warp 0)
+        if (valid) {
+            float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
+            const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= il; dy *= il; dz *= il;
+            float rgb[3];
+            sh_colour(t.sh + (size_t)n * t.sh_stride, (int)t.sh_degree, dx, dy, dz, rgb);
+            float4* out = reinterpret_cast<float4*>(splat + (size_t)m * kSplatStride);
+            out[0] = make_float4(u, v, A, B);
+            out[1] = make_float4(C, lthr, a0, vz);
+            out[2] = make_float4(rgb[0], rgb[1], rgb[2], radius);
+        }
         __syncthreads();
-        // Warp-cooperative emission: the warp's pairs are numbered 0..wtot-1 in
-        // (Gaussian, row-major tile) order and written by consecutive lanes, so
-        // stores are contiguous.  Pair q belongs to the lane whose inclusive
-        // count first exceeds q (binary search over the warp's scan).
+        // ---- 4. warp-cooperative emission: the warp's pairs are numbered 0..wtot-1
+        // in (Gaussian, row-major tile) order and written by consecutive lanes.
+        // Pair q belongs to the lane whose inclusive count first exceeds q.
         {
-            const unsigned long long wfirst = (unsigned long long)s_prefix + off + 0ull;
+            const unsigned long long wfirst = (unsigned long long)s_prefix + off;
             const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
             const uint32_t excl = incl - cnt;
             const int32_t rw = x1 - x0;
-            if (lane == 0 && wfirst + wtot > cap && wtot) set_status(st, kErrCapacity, 0x300u);
+            const uint32_t dbits = __float_as_uint(vz);
+            if (lane == 0 && wtot && wfirst + wtot > cap) set_status(st, kErrCapacity, 0x300u);
             for (uint32_t q0 = 0; q0 < wtot; q0 += 32) {
                 const uint32_t q = q0 + lane;
-                // owner: smallest lane L with incl(L) > q
                 uint32_t lo = 0;
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1) {

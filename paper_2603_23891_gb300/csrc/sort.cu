@@ -70,7 +70,7 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* tm
     return off + incl - v;
 }
 
-__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(
+__global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(
     const unsigned long long* __restrict__ in_k, const uint32_t* __restrict__ in_v,
     unsigned long long* __restrict__ out_k, uint32_t* __restrict__ out_v, unsigned long long cap,
     int pass, unsigned long long* lookback, FrameState* st)
@@ -102,18 +102,11 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(
         const uint32_t base = tile * kSortTile + warp * (kSortTileItems * 32);
 
         unsigned long long k[kSortTileItems];
-        uint32_t v[kSortTileItems];
         uint32_t rank[kSortTileItems];
 #pragma unroll
         for (int i = 0; i < kSortTileItems; ++i) {
             const uint32_t idx = base + i * 32 + lane;
-            if (idx < n) {
-                k[i] = __ldg(in_k + idx);
-                v[i] = __ldg(in_v + idx);
-            } else {
-                k[i] = ~0ull;
-                v[i] = 0;
-            }
+            k[i] = idx < n ? __ldg(in_k + idx) : ~0ull;
         }
         // stable local ranking: order (warp, item, lane) is the input order
 #pragma unroll
@@ -187,7 +180,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(
                 const uint32_t d = (uint32_t)((k[i] >> shift) & 0xFFu);
                 const uint32_t pos = S.lbase[d] + S.whist[warp][d] + rank[i];
                 S.keys[pos] = k[i];
-                S.vals[pos] = v[i];
+                S.vals[pos] = __ldg(in_v + idx);    // values are read once, at staging
             }
         }
         __syncthreads();
