@@ -181,15 +181,18 @@ __device__ __forceinline__ void ewa_cov2d(const DevCamera& cam, float vz, float 
 // ---------------------------------------------------------------------
 // bounded look-back / spin helpers
 // ---------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+// Look-back entries carry their whole payload (epoch tag, flag, count) in one
+// 64-bit word and publish no other data, so relaxed device-scope accesses
+// suffice (no acquire / release ordering is needed around them).
+__device__ __forceinline__ unsigned long long ld_lb_u64(const unsigned long long* p)
 {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
+__device__ __forceinline__ void st_lb_u64(unsigned long long* p, unsigned long long v)
 {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // look-back entry: [63:34] epoch (30 bits) | [33:32] flag | [31:0] value
@@ -231,7 +234,7 @@ __device__ __forceinline__ uint32_t warp_lookback(const unsigned long long* lb, 
         bool ready = true, incl = true;
         uint32_t val = 0;
         if (j >= 0) {
-            const unsigned long long e = ld_acquire_u64(lb + j);
+            const unsigned long long e = ld_lb_u64(lb + j);
             const unsigned long long flag = (e >> 32) & 3ull;
             ready = ((uint32_t)(e >> 34) == tg) && flag != 0;
             incl = flag == kFlagIncl;

@@ -178,11 +178,11 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
         if (warp == 0) {
             uint32_t prefix = 0;
             if (tile == 0) {
-                if (lane == 0) st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, total));
+                if (lane == 0) st_lb_u64(lookback + tile, lb_pack(tag, kFlagIncl, total));
             } else {
-                if (lane == 0) st_release_u64(lookback + tile, lb_pack(tag, kFlagAgg, total));
+                if (lane == 0) st_lb_u64(lookback + tile, lb_pack(tag, kFlagAgg, total));
                 prefix = warp_lookback(lookback, tile, tag, st, 0x200u);
-                if (lane == 0) st_release_u64(lookback + tile, lb_pack(tag, kFlagIncl, prefix + total));
+                if (lane == 0) st_lb_u64(lookback + tile, lb_pack(tag, kFlagIncl, prefix + total));
             }
             if (lane == 0) {
                 s_prefix = prefix;

@@ -108,13 +108,20 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(
             const uint32_t idx = base + i * 32 + lane;
             k[i] = idx < n ? __ldg(in_k + idx) : ~0ull;
         }
-        // stable local ranking: order (warp, item, lane) is the input order
+        // stable local ranking: order (warp, item, lane) is the input order.  The
+        // lanes holding the same digit are found with one ballot per digit bit.
 #pragma unroll
         for (int i = 0; i < kSortTileItems; ++i) {
             const uint32_t idx = base + i * 32 + lane;
             const bool valid = idx < n;
-            const uint32_t d = valid ? (uint32_t)((k[i] >> shift) & 0xFFu) : 256u;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t d = (uint32_t)((k[i] >> shift) & 0xFFu);
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int bit = 0; bit < 8; ++bit) {
+                const bool on = (d >> bit) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, on);
+                peers &= on ? bb : ~bb;
+            }
             uint32_t b = 0;
             if (valid) b = S.whist[warp][d];
             __syncwarp();
@@ -135,10 +142,10 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(
         unsigned long long* lb = lookback + (size_t)tile * 256 + tid;
         uint32_t prefix = 0;
         if (tile == 0) {
-            st_release_u64(lb, lb_pack(tag, kFlagIncl, cnt));
+            st_lb_u64(lb, lb_pack(tag, kFlagIncl, cnt));
         } else {
             // each round trip reads this digit's entry of up to 8 preceding tiles at once
-            st_release_u64(lb, lb_pack(tag, kFlagAgg, cnt));
+            st_lb_u64(lb, lb_pack(tag, kFlagAgg, cnt));
             const uint32_t tg = tag & 0x3FFFFFFFu;
             int j = (int)tile - 1;
             uint64_t spins = 0;
@@ -146,7 +153,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(
                 unsigned long long e[kLookbackRows];
 #pragma unroll
                 for (int q = 0; q < kLookbackRows; ++q)
-                    e[q] = (j - q >= 0) ? ld_acquire_u64(lookback + (size_t)(j - q) * 256 + tid) : 0ull;
+                    e[q] = (j - q >= 0) ? ld_lb_u64(lookback + (size_t)(j - q) * 256 + tid) : 0ull;
                 int used = 0;
                 bool done = false;
 #pragma unroll
@@ -165,7 +172,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(
                 }
                 j -= used;
             }
-            st_release_u64(lb, lb_pack(tag, kFlagIncl, prefix + cnt));
+            st_lb_u64(lb, lb_pack(tag, kFlagIncl, prefix + cnt));
         }
         uint32_t tile_total;
         const uint32_t lb_start = block_excl_scan_256(cnt, S.scan_tmp, tile_total);
