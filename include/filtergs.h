@@ -233,6 +233,26 @@ int fgs_calibrate_gtc(fgs_ctx* ctx, void* stream, const fgs_camera* views, int n
  * `stream`.  Asynchronous.  Errors: FGS_ERR_ARG, FGS_ERR_CUDA. */
 int fgs_eval_exp(const float* x, float* y, uint64_t n, void* stream);
 
+/* Allocation-free compaction of selection bits (no counterpart in the paper:
+ * a service for callers that cannot allocate device memory, e.g. a host
+ * application that owns every allocation, code running during CUDA stream
+ * capture, or a real-time loop that may not allocate after start-up).
+ * Writes the indices of the set bits of selbits[n_words] (bit b of word w is
+ * index 32 w + b) in ascending order to ids_out, and their number to
+ * count_out[0] (0xFFFFFFFF if a bounded device wait timed out).  All pointers
+ * are device pointers; ids_out must hold every set bit (at most 32 * n_words
+ * indices).  Runs the render path's compaction kernel, but its scratch (look-back
+ * words and a small state block, 512 KiB + 256 B) is a static device array of
+ * the library, so the call allocates nothing.  Limit: n_words <= 2^26
+ * (2^31 indices); larger inputs return FGS_ERR_ARG before any launch.  The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (other streams, other threads) race;
+ * serialise them.  Asynchronous on `stream` (the current device's).  Errors:
+ * FGS_ERR_ARG, FGS_ERR_CUDA. */
+int fgs_compact_selection_noalloc(const uint32_t* selbits, uint64_t n_words, uint32_t* ids_out,
+                                  uint32_t* count_out, void* stream);
+
 /* Wait for the stream and return any latched device status, then clear it. */
 int fgs_sync(fgs_ctx* ctx, void* stream);
 

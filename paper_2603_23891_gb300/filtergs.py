@@ -36,7 +36,7 @@ EXPORTED = ["fgs_version", "fgs_create", "fgs_destroy", "fgs_last_error", "fgs_s
             "fgs_load_tree", "fgs_set_camera", "fgs_set_shrink", "fgs_filter", "fgs_render",
             "fgs_stage_times", "fgs_stage_count", "fgs_get_pairs", "fgs_get_splats",
             "fgs_calibrate_view", "fgs_calibrate_gtc", "fgs_sync", "fgs_validate_tree",
-            "fgs_eval_exp"]
+            "fgs_eval_exp", "fgs_compact_selection_noalloc"]
 
 
 class FgsError(RuntimeError):
@@ -102,6 +102,7 @@ def lib():
         "fgs_sync": ([vp, vp], i32),
         "fgs_validate_tree": ([C.POINTER(fgs_tree), C.c_char_p, C.c_size_t], i32),
         "fgs_eval_exp": ([vp, vp, u64, vp], i32),
+        "fgs_compact_selection_noalloc": ([vp, u64, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -197,6 +198,14 @@ def fgs_eval_exp(x, y, stream=None):
     code = lib().fgs_eval_exp(_ptr(x), _ptr(y), n, stream)
     if code != FGS_OK:
         raise FgsError(code, "fgs_eval_exp failed")
+
+
+def fgs_compact_selection_noalloc(selbits, n_words: int, ids_out, count_out, stream=None) -> int:
+    """Allocation-free compaction of device selection bits (see the C header).
+
+    For callers that cannot allocate device memory; returns the status code."""
+    return lib().fgs_compact_selection_noalloc(_ptr(selbits), n_words, _ptr(ids_out),
+                                               _ptr(count_out), stream)
 
 
 def fgs_load_tree(ctx, tree):
