@@ -195,7 +195,6 @@ def run_ours(args):
     K = args.steps
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    slot0 = filtergs.fgs_stage_count(r.ctx)
     clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
@@ -207,7 +206,7 @@ def run_ours(args):
         flush.zero_()                                     # evict L2 between steps
         r.set_camera(cams[my_poses[k % len(my_poses)]])
         ev_s[k].record(stream)
-        r.render(rgb, Tt, stage_events=True)
+        r.render(rgb, Tt)
         ev_e[k].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -215,8 +214,16 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(K)]
-    stage_ms = np.array([filtergs.fgs_stage_times(r.ctx, (slot0 + k) % 256) for k in range(K)])
     total_ms = float(sum(step_ms))
+    # per-stage durations: the same K steps again, with events between the stages
+    # (events between kernels stop the launch overlap, so this pass is separate)
+    slot0 = filtergs.fgs_stage_count(r.ctx)
+    for k in range(K):
+        flush.zero_()
+        r.set_camera(cams[my_poses[k % len(my_poses)]])
+        r.render(rgb, Tt, stage_events=True)
+    torch.cuda.synchronize()
+    stage_ms = np.array([filtergs.fgs_stage_times(r.ctx, (slot0 + k) % 256) for k in range(K)])
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

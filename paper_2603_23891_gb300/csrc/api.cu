@@ -45,8 +45,7 @@ struct fgs_ctx {
     std::string err;
     fgs_params params{};
     // occupancy (resident blocks per SM)
-    int occ_pred = 1, occ_anc = 1, occ_compact = 1, occ_proj = 1, occ_hist = 1, occ_sort = 1,
-        occ_ranges = 1;
+    int occ_pred = 1, occ_anc = 1, occ_compact = 1, occ_proj = 1, occ_sort = 1, occ_ranges = 1;
     // tree
     bool has_tree = false;
     DevTree tree{};
@@ -243,7 +242,7 @@ int enqueue_front(fgs_ctx* c, const DevCamera& dc, cudaStream_t s, cudaEvent_t* 
     ++launches;
     if (ev) cudaEventRecord(ev[3], s);
     launches += launch_sort(c->keys0, c->vals0, c->keys1, c->vals1, c->pair_cap, dc.sort_passes,
-                            c->lb_sort, c->st, c->sms * c->occ_hist, c->sms * c->occ_sort, s);
+                            c->lb_sort, c->st, c->sms * c->occ_sort, s);
     c->sorted_in_1 = (dc.sort_passes & 1) != 0;
     if (ev) cudaEventRecord(ev[4], s);
     launch_tile_ranges(c->sorted_in_1 ? c->keys1 : c->keys0, c->pair_cap, c->ranges, c->st,
@@ -306,7 +305,6 @@ int fgs_create(fgs_ctx** out, int device)
     c->occ_anc = occ_filter_anc();
     c->occ_compact = occ_compact();
     c->occ_proj = occ_project();
-    c->occ_hist = occ_sort_hist();
     c->occ_sort = occ_sort_pass();
     c->occ_ranges = occ_tile_ranges();
     c->params.tau_R = 3.0f;

@@ -113,15 +113,14 @@ __device__ __forceinline__ uint32_t stage_vals(uint32_t* dst, uint64_t* bar, int
     return s0 - a0;
 }
 
-// Warps of a CTA cover 8 x 4 pixel blocks of the tile (tile_w / 8 across).
-__device__ __forceinline__ void warp_origin(const DevCamera& cam, uint32_t tile, uint32_t w,
+// Warps of a CTA cover 8 x 4 pixel blocks of the tile (tile_w / 8 across);
+// (tx0, ty0) is the tile's first pixel.
+__device__ __forceinline__ void warp_origin(const DevCamera& cam, int32_t tx0, int32_t ty0, uint32_t w,
                                             int32_t& x0, int32_t& y0)
 {
-    const uint32_t tx = tile % (uint32_t)cam.tiles_x, ty = tile / (uint32_t)cam.tiles_x;
-    const uint32_t wpr = (uint32_t)(cam.tile_w >> 3);
-    const uint32_t wx = w % wpr, wy = w / wpr;
-    x0 = (int32_t)(tx * cam.tile_w + wx * 8);
-    y0 = (int32_t)(ty * cam.tile_h + wy * 4);
+    const uint32_t sh = (uint32_t)cam.tile_shift_x - 3u;       // log2(warps per tile row)
+    x0 = tx0 + (int32_t)((w & ((1u << sh) - 1u)) << 3);
+    y0 = ty0 + (int32_t)((w >> sh) << 2);
 }
 
 // Which warps of the tile may hold a pixel whose binary32 power reaches the
@@ -132,8 +131,10 @@ __device__ __forceinline__ void warp_origin(const DevCamera& cam, uint32_t tile,
 // plus one pixel, which covers it for cond(Q) < 1e4 (cond(Q) <= tr^2 / det).
 // Beyond that, or for a singular Q, every warp keeps the Gaussian.  A warp left
 // out of the mask would have skipped the Gaussian at every one of its pixels.
-__device__ __forceinline__ uint32_t warp_mask(const DevCamera& cam, uint32_t tile, float u, float v,
-                                              float A, float B, float C, float lthr)
+// Warp column c spans pixel centres tx0 + 8c + [0.5, 7.5], row r spans
+// ty0 + 4r + [0.5, 3.5]; the mask is the block of columns x rows the box meets.
+__device__ __forceinline__ uint32_t warp_mask(const DevCamera& cam, int32_t tx0, int32_t ty0, float u,
+                                              float v, float A, float B, float C, float lthr)
 {
     if (!(lthr <= 0.0f)) return 0u;             // alpha0 < 1/255: no pixel can pass
     const float det = A * C - B * B;
@@ -142,15 +143,17 @@ __device__ __forceinline__ uint32_t warp_mask(const DevCamera& cam, uint32_t til
     const float sq = fmaf(-2.1f, lthr, 1e-4f);  // 1.05 * (-2 lthr) + 1e-4
     const float ex = sqrtf(sq * C / det) + 1.0f;
     const float ey = sqrtf(sq * A / det) + 1.0f;
+    const int32_t sh = cam.tile_shift_x - 3;    // log2(warps per tile row)
+    const int32_t ncol = 1 << sh, nrow = 8 >> sh;
+    const float ux = u - (float)tx0, vy = v - (float)ty0;
+    const int32_t c_lo = max(0, (int32_t)ceilf((ux - ex - 7.5f) * 0.125f));
+    const int32_t c_hi = min(ncol - 1, (int32_t)floorf((ux + ex - 0.5f) * 0.125f));
+    const int32_t r_lo = max(0, (int32_t)ceilf((vy - ey - 3.5f) * 0.25f));
+    const int32_t r_hi = min(nrow - 1, (int32_t)floorf((vy + ey - 0.5f) * 0.25f));
+    if (c_lo > c_hi || r_lo > r_hi) return 0u;
+    const uint32_t cols = ((2u << c_hi) - 1u) & ~((1u << c_lo) - 1u);
     uint32_t mask = 0;
-#pragma unroll
-    for (uint32_t w = 0; w < 8; ++w) {
-        int32_t x0, y0;
-        warp_origin(cam, tile, w, x0, y0);
-        const float px0 = (float)x0 + 0.5f, px1 = (float)x0 + 7.5f;
-        const float py0 = (float)y0 + 0.5f, py1 = (float)y0 + 3.5f;
-        if (px0 <= u + ex && px1 >= u - ex && py0 <= v + ey && py1 >= v - ey) mask |= 1u << w;
-    }
+    for (int32_t r = r_lo; r <= r_hi; ++r) mask |= cols << (r << sh);
     return mask;
 }
 
@@ -168,12 +171,16 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
     __shared__ double s_red[8];
     const uint32_t tile = blockIdx.x;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t tx0 = (int32_t)(tile % (uint32_t)cam.tiles_x) * cam.tile_w;
+    const int32_t ty0 = (int32_t)(tile / (uint32_t)cam.tiles_x) * cam.tile_h;
     int32_t wx0, wy0;
-    warp_origin(cam, tile, warp, wx0, wy0);
+    warp_origin(cam, tx0, ty0, warp, wx0, wy0);
     const int32_t x = wx0 + (int32_t)(lane & 7);
     const int32_t y = wy0 + (int32_t)(lane >> 3);
     const bool inside = x < cam.width && y < cam.height;
     const float px = fa((float)x, 0.5f), py = fa((float)y, 0.5f);
+    grid_dep_wait();
+    grid_dep_trigger();
     const uint2 rg = ranges[tile];
     const uint32_t M = st->M;
     const uint32_t s = rg.x, e = rg.y;
@@ -203,7 +210,7 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
             S.g0[tid] = a;
             S.g1[tid] = b;
             S.g2[tid] = __ldg(g + 2);
-            S.wmask[tid] = warp_mask(cam, tile, a.x, a.y, a.z, a.w, b.x, b.y);
+            S.wmask[tid] = warp_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
         }
         __syncthreads();
         // this warp's ordered list of the chunk entries that can reach its pixels
@@ -294,15 +301,16 @@ void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* val
                   const float* splat, float* rgb, float* T, FrameState* st, cudaStream_t s)
 {
     const int n_tiles = cam.tiles_x * cam.tiles_y;
-    blend_kernel<false><<<n_tiles, 256, 0, s>>>(cam, ranges, vals, splat, rgb, T, nullptr, nullptr,
-                                                st);
+    launch_pdl(blend_kernel<false>, n_tiles, 256, 0, s, cam, ranges, vals, splat, rgb, T,
+               (float*)nullptr, (float*)nullptr, st);
 }
 
 void launch_blend_kpc(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
                       const float* splat, float* kpc, float* G, FrameState* st, cudaStream_t s)
 {
     const int n_tiles = cam.tiles_x * cam.tiles_y;
-    blend_kernel<true><<<n_tiles, 256, 0, s>>>(cam, ranges, vals, splat, nullptr, nullptr, kpc, G, st);
+    launch_pdl(blend_kernel<true>, n_tiles, 256, 0, s, cam, ranges, vals, splat, (float*)nullptr,
+               (float*)nullptr, kpc, G, st);
 }
 
 __global__ void eval_exp_kernel(const float* __restrict__ x, float* __restrict__ y, uint64_t n)

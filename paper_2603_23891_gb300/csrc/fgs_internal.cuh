@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace fgs {
 
 constexpr int kStages = 6;
@@ -203,6 +205,18 @@ __device__ __forceinline__ unsigned long long lb_pack(uint32_t epoch, unsigned l
     return ((unsigned long long)(epoch & 0x3FFFFFFFu) << 34) | (flag << 32) | v;
 }
 
+// Programmatic dependent launch: the frame's kernels are launched with
+// programmatic stream serialisation, so a kernel's blocks may start while its
+// predecessor drains.  Every kernel calls grid_dep_wait() before it touches
+// anything a predecessor wrote (it returns once the predecessor grid has
+// completed and its writes are visible), and grid_dep_trigger() once it no
+// longer needs to hold the next kernel back.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void set_status(FrameState* st, int code, uint32_t info)
 {
     if (atomicCAS(&st->status, 0, code) == 0) st->status_info = info;
@@ -262,12 +276,29 @@ __device__ __forceinline__ uint32_t warp_lookback(const unsigned long long* lb, 
 // ---------------------------------------------------------------------
 // host launchers (one per kernel family)
 // ---------------------------------------------------------------------
+// Launch with programmatic stream serialisation (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t s, Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Resident blocks per SM of each persistent / grid-stride kernel (occupancy API).
 int occ_filter_pred();
 int occ_filter_anc();
 int occ_compact();
 int occ_project();
-int occ_sort_hist();
 int occ_sort_pass();
 int occ_tile_ranges();
 size_t sort_smem_bytes();
@@ -287,10 +318,10 @@ void launch_project_emit(const DevTree& t, const DevCamera& cam, const uint32_t*
                          int blocks, cudaStream_t s);
 // Sorts keys0/vals0 in place through keys1/vals1 (an even number of passes
 // leaves the result in keys0/vals0; an odd number in keys1/vals1).
+// The digit histograms of all passes are accumulated during key emission.
 int launch_sort(unsigned long long* keys0, uint32_t* vals0, unsigned long long* keys1,
                 uint32_t* vals1, unsigned long long cap, int passes,
-                unsigned long long* lookback, FrameState* st, int hist_blocks, int sort_blocks,
-                cudaStream_t s);
+                unsigned long long* lookback, FrameState* st, int sort_blocks, cudaStream_t s);
 void launch_tile_ranges(const unsigned long long* keys, unsigned long long cap, uint2* ranges,
                         const FrameState* st, int blocks, cudaStream_t s);
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,

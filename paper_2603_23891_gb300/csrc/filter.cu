@@ -16,6 +16,8 @@ namespace fgs {
 
 __global__ void frame_begin_kernel(FrameState* st, uint2* ranges, int n_tiles)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid == 0) {
         st->epoch = st->epoch + 1;
@@ -32,7 +34,7 @@ void launch_frame_begin(FrameState* st, uint2* ranges, int n_tiles, cudaStream_t
 {
     int blocks = (n_tiles + 255) / 256;
     blocks = blocks < 8 ? 8 : blocks;
-    frame_begin_kernel<<<blocks, 256, 0, s>>>(st, ranges, n_tiles);
+    launch_pdl(frame_begin_kernel, blocks, 256, 0, s, st, ranges, n_tiles);
 }
 
 // ---------------------------------------------------------------------------
@@ -40,6 +42,8 @@ void launch_frame_begin(FrameState* st, uint2* ranges, int n_tiles, cudaStream_t
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) filter_pred_kernel(DevTree t, DevCamera cam, uint32_t* pbits)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     const uint32_t n_chunks = t.n_pad >> 2;               // multiple of 32
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -99,7 +103,7 @@ void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits,
     int need = (int)((n_chunks + 255) / 256);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    filter_pred_kernel<<<blocks, 256, 0, s>>>(t, cam, pbits);
+    launch_pdl(filter_pred_kernel, blocks, 256, 0, s, t, cam, pbits);
 }
 
 // ---------------------------------------------------------------------------
@@ -141,6 +145,8 @@ __global__ void __launch_bounds__(256) filter_anc_kernel(DevTree t, const uint32
                                                          uint32_t* __restrict__ selbits)
 {
     __shared__ uint32_t s_pb[kAncCacheWords];
+    grid_dep_wait();
+    grid_dep_trigger();
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t n_words = t.n_pad >> 5;
     const uint32_t cw = n_words < (uint32_t)kAncCacheWords ? n_words : (uint32_t)kAncCacheWords;
@@ -168,7 +174,7 @@ void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbit
     int need = (int)((n_words * 32 + 255) / 256);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    filter_anc_kernel<<<blocks, 256, 0, s>>>(t, pbits, selbits);
+    launch_pdl(filter_anc_kernel, blocks, 256, 0, s, t, pbits, selbits);
 }
 
 // Stream compaction of the selection bits into ascending node ids.  Tiles of
@@ -180,6 +186,8 @@ __global__ void __launch_bounds__(256) compact_kernel(const uint32_t* __restrict
 {
     __shared__ uint32_t s_warp_tot[8];
     __shared__ uint32_t s_tile, s_prefix;
+    grid_dep_wait();
+    grid_dep_trigger();
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n_tiles = (n_words + kCompactWords - 1) / kCompactWords;
     const uint32_t tag = st->epoch * 16u + 0u;
@@ -252,7 +260,7 @@ void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel,
     const int n_tiles = (int)((n_words + kCompactWords - 1) / kCompactWords);
     if (blocks > n_tiles) blocks = n_tiles;
     if (blocks < 1) blocks = 1;
-    compact_kernel<<<blocks, 256, 0, s>>>(selbits, n_words, sel, lookback, st);
+    launch_pdl(compact_kernel, blocks, 256, 0, s, selbits, n_words, sel, lookback, st);
 }
 
 int occ_filter_pred()

@@ -2,7 +2,8 @@
 // emission (§3.1, §3.3) on sm_103a.
 //
 // One thread per selected Gaussian, 256 per tile, persistent blocks taking
-// tiles from a ticket counter.  Each thread computes the splat record (centre,
+// tiles from a ticket counter.  The radix digit histograms of every emitted key
+// (all sort passes) are accumulated here, per block in shared memory.  Each thread computes the splat record (centre,
 // conic, log-domain skip threshold, opacity, depth, colour, footprint radius),
 // its tile rectangle and pair count; a block scan plus a decoupled look-back
 // across tiles gives every Gaussian its first pair slot, so pairs are emitted
@@ -96,7 +97,12 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
 {
     __shared__ uint32_t s_warp_tot[kProjThreads / 32];
     __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_hist[kMaxSortPasses][256];   // radix digit histograms of emitted keys
+    grid_dep_wait();
+    grid_dep_trigger();
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < kMaxSortPasses * 256; i += kProjThreads) (&s_hist[0][0])[i] = 0;
+    const int passes = cam.sort_passes;
     const uint32_t M = st->M;
     const uint32_t n_tiles = (M + kProjThreads - 1) / kProjThreads;
     const uint32_t tag = st->epoch * 16u + 1u;
@@ -233,13 +239,21 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
                         const int32_t ty = o_y0 + k / o_rw;
                         const int32_t tx = o_x0 + k % o_rw;
                         const unsigned long long tl = (unsigned long long)(ty * cam.tiles_x + tx);
-                        keys[idx] = (tl << 32) | o_d;
+                        const unsigned long long key = (tl << 32) | o_d;
+                        keys[idx] = key;
                         vals[idx] = o_m;
+                        for (int p = 0; p < passes; ++p)
+                            atomicAdd(&s_hist[p][(uint32_t)(key >> (8 * p)) & 0xFFu], 1u);
                     }
                 }
             }
         }
         __syncthreads();
+    }
+    // flush this block's digit histograms (non-zero bins only)
+    for (int i = tid; i < passes * 256; i += kProjThreads) {
+        const uint32_t c = (&s_hist[0][0])[i];
+        if (c) atomicAdd(&st->hist[0][0] + i, c);
     }
 }
 
@@ -249,8 +263,8 @@ void launch_project_emit(const DevTree& t, const DevCamera& cam, const uint32_t*
                          int blocks, cudaStream_t s)
 {
     if (blocks < 1) blocks = 1;
-    project_emit_kernel<<<blocks, kProjThreads, 0, s>>>(t, cam, sel, splat, keys, vals, cap,
-                                                        lookback, st);
+    launch_pdl(project_emit_kernel, blocks, kProjThreads, 0, s, t, cam, sel, splat, keys, vals, cap,
+               lookback, st);
 }
 
 int occ_project()

@@ -2,8 +2,9 @@
 // and per-tile ranges of the sorted list (sm_103a).
 //
 // Design after Adinets & Merrill, "Onesweep: A Faster Least Significant Digit
-// Radix Sort for GPUs" (2022): one upfront pass computes the digit histograms
-// of every 8-bit digit, then each digit pass is a single sweep in which a
+// Radix Sort for GPUs" (2022): the digit histograms of every 8-bit digit are
+// known up front (accumulated while the keys are emitted), then each digit
+// pass is a single sweep in which a
 // block ranks its tile of 4096 keys locally (warp match + per-warp counters,
 // stable), publishes its per-digit counts, looks back over preceding tiles for
 // their counts (decoupled look-back, bounded spins) and scatters through
@@ -12,28 +13,6 @@
 #include "fgs_internal.cuh"
 
 namespace fgs {
-
-__global__ void __launch_bounds__(256) sort_hist_kernel(const unsigned long long* __restrict__ keys,
-                                                        unsigned long long cap, int passes,
-                                                        FrameState* st)
-{
-    __shared__ uint32_t h[kMaxSortPasses][256];
-    for (int i = threadIdx.x; i < kMaxSortPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
-    __syncthreads();
-    unsigned long long n = st->n_pairs;
-    n = n < cap ? n : cap;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += stride) {
-        const unsigned long long k = __ldg(keys + i);
-        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFFu], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
-        const uint32_t c = (&h[0][0])[i];
-        if (c) atomicAdd(&st->hist[0][0] + i, c);
-    }
-}
 
 struct SortSmem {
     uint32_t whist[kSortThreads / 32][256];   // per-warp digit counters, then warp offsets
@@ -77,6 +56,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
+    grid_dep_wait();
+    grid_dep_trigger();
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t shift = 8u * (uint32_t)pass;
     unsigned long long nll = st->n_pairs;
@@ -207,22 +188,17 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(
 
 int launch_sort(unsigned long long* keys0, uint32_t* vals0, unsigned long long* keys1,
                 uint32_t* vals1, unsigned long long cap, int passes,
-                unsigned long long* lookback, FrameState* st, int hist_blocks, int sort_blocks,
-                cudaStream_t s)
+                unsigned long long* lookback, FrameState* st, int sort_blocks, cudaStream_t s)
 {
     cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(SortSmem));
-    int launches = 0;
-    sort_hist_kernel<<<hist_blocks, 256, 0, s>>>(keys0, cap, passes, st);
-    ++launches;
     for (int p = 0; p < passes; ++p) {
         const bool even = (p & 1) == 0;
-        sort_pass_kernel<<<sort_blocks, kSortThreads, sizeof(SortSmem), s>>>(
-            even ? keys0 : keys1, even ? vals0 : vals1, even ? keys1 : keys0, even ? vals1 : vals0,
-            cap, p, lookback, st);
-        ++launches;
+        launch_pdl(sort_pass_kernel, sort_blocks, kSortThreads, sizeof(SortSmem), s,
+                   even ? keys0 : keys1, even ? vals0 : vals1, even ? keys1 : keys0,
+                   even ? vals1 : vals0, cap, p, lookback, st);
     }
-    return launches;
+    return passes;
 }
 
 size_t sort_smem_bytes() { return sizeof(SortSmem); }
@@ -231,6 +207,8 @@ __global__ void tile_ranges_kernel(const unsigned long long* __restrict__ keys,
                                    unsigned long long cap, uint2* __restrict__ ranges,
                                    const FrameState* st)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     unsigned long long nll = st->n_pairs;
     nll = nll < cap ? nll : cap;
     const uint32_t n = (uint32_t)nll;
@@ -246,14 +224,7 @@ void launch_tile_ranges(const unsigned long long* keys, unsigned long long cap, 
                         const FrameState* st, int blocks, cudaStream_t s)
 {
     if (blocks < 1) blocks = 1;
-    tile_ranges_kernel<<<blocks, 256, 0, s>>>(keys, cap, ranges, st);
-}
-
-int occ_sort_hist()
-{
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sort_hist_kernel, 256, 0);
-    return b > 0 ? b : 1;
+    launch_pdl(tile_ranges_kernel, blocks, 256, 0, s, keys, cap, ranges, st);
 }
 
 int occ_sort_pass()
