@@ -45,7 +45,8 @@ struct fgs_ctx {
     std::string err;
     fgs_params params{};
     // occupancy (resident blocks per SM)
-    int occ_pred = 1, occ_anc = 1, occ_compact = 1, occ_proj = 1, occ_sort = 1, occ_ranges = 1;
+    int occ_pred = 1, occ_anc = 1, occ_compact = 1, occ_proj = 1, occ_emit = 1, occ_sort = 1,
+        occ_ranges = 1;
     // tree
     bool has_tree = false;
     DevTree tree{};
@@ -62,7 +63,8 @@ struct fgs_ctx {
     uint32_t* sel = nullptr;
     float* splat = nullptr;
     unsigned long long* lb_compact = nullptr;
-    unsigned long long* lb_project = nullptr;
+    uint4* foot = nullptr;          // per selected Gaussian: rect, pair count, depth bits
+    uint32_t* tile_total = nullptr; // pair total per 256 selected Gaussians
     // pair-sized buffers
     uint64_t pair_cap = 0;
     unsigned long long* keys0 = nullptr;
@@ -155,7 +157,8 @@ int ensure_nodes(fgs_ctx* c, size_t n_pad)
     if ((r = grow(c, (void**)&c->sel, n_pad * 4))) return r;
     if ((r = grow(c, (void**)&c->splat, n_pad * kSplatStride * 4))) return r;
     if ((r = grow(c, (void**)&c->lb_compact, (n_pad / 32 / kCompactWords + 2) * 8))) return r;
-    if ((r = grow(c, (void**)&c->lb_project, (n_pad / kProjThreads + 2) * 8))) return r;
+    if ((r = grow(c, (void**)&c->foot, n_pad * sizeof(uint4)))) return r;
+    if ((r = grow(c, (void**)&c->tile_total, (n_pad / kProjThreads + 8) * 4))) return r;
     c->node_cap = n_pad;
     return FGS_OK;
 }
@@ -237,9 +240,9 @@ int enqueue_front(fgs_ctx* c, const DevCamera& dc, cudaStream_t s, cudaEvent_t* 
                    c->sms * c->occ_compact, s);
     launches += 2;
     if (ev) cudaEventRecord(ev[2], s);
-    launch_project_emit(c->tree, dc, c->sel, c->splat, c->keys0, c->vals0, c->pair_cap,
-                        c->lb_project, c->st, c->sms * c->occ_proj, s);
-    ++launches;
+    launch_project_emit(c->tree, dc, c->sel, c->splat, c->foot, c->tile_total, c->keys0, c->vals0,
+                        c->pair_cap, c->st, c->sms * c->occ_proj, c->sms * c->occ_emit, s);
+    launches += 2;
     if (ev) cudaEventRecord(ev[3], s);
     launches += launch_sort(c->keys0, c->vals0, c->keys1, c->vals1, c->pair_cap, dc.sort_passes,
                             c->lb_sort, c->st, c->sms * c->occ_sort, s);
@@ -305,6 +308,7 @@ int fgs_create(fgs_ctx** out, int device)
     c->occ_anc = occ_filter_anc();
     c->occ_compact = occ_compact();
     c->occ_proj = occ_project();
+    c->occ_emit = occ_emit();
     c->occ_sort = occ_sort_pass();
     c->occ_ranges = occ_tile_ranges();
     c->params.tau_R = 3.0f;
@@ -332,7 +336,7 @@ int fgs_destroy(fgs_ctx* c)
     if (!c) return FGS_OK;
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
-    void* bufs[] = {c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->lb_project,
+    void* bufs[] = {c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->foot, c->tile_total,
                     c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->lb_sort, c->ranges,
                     c->G, c->img, c->st};
     for (void* p : bufs) free_ptr(p);

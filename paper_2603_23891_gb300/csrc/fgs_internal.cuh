@@ -27,6 +27,7 @@ constexpr int kFilterTile = 4096;         // node arrays are padded to a multipl
 constexpr int kCompactWords = 1024;       // 32-bit selection words per compaction tile (32K nodes)
 constexpr int kAncCacheWords = 4096;      // P-bit words of the lowest node ids kept in shared memory
 constexpr int kProjThreads = 256;         // selected Gaussians per projection tile
+constexpr int kEmitTiles = 4;             // projection tiles per emission block
 constexpr uint64_t kSpinLimit = 1ull << 24;   // bounded spin-waits
 
 // device status codes (mirrors FGS_ERR_* of the C ABI)
@@ -80,7 +81,7 @@ struct FrameState {
 };
 
 // Ticket slots
-enum : int { kTicketCompact = 0, kTicketProject = 1, kTicketSortBase = 2 };
+enum : int { kTicketCompact = 0, kTicketSortBase = 2 };
 
 // ---------------------------------------------------------------------
 // decision-exact binary32 helpers
@@ -299,6 +300,7 @@ int occ_filter_pred();
 int occ_filter_anc();
 int occ_compact();
 int occ_project();
+int occ_emit();
 int occ_sort_pass();
 int occ_tile_ranges();
 size_t sort_smem_bytes();
@@ -313,9 +315,9 @@ void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbit
 void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel,
                     unsigned long long* lookback, FrameState* st, int blocks, cudaStream_t s);
 void launch_project_emit(const DevTree& t, const DevCamera& cam, const uint32_t* sel,
-                         float* splat, unsigned long long* keys, uint32_t* vals,
-                         unsigned long long cap, unsigned long long* lookback, FrameState* st,
-                         int blocks, cudaStream_t s);
+                         float* splat, uint4* foot, uint32_t* tile_total,
+                         unsigned long long* keys, uint32_t* vals, unsigned long long cap,
+                         FrameState* st, int proj_blocks, int emit_blocks, cudaStream_t s);
 // Sorts keys0/vals0 in place through keys1/vals1 (an even number of passes
 // leaves the result in keys0/vals0; an odd number in keys1/vals1).
 // The digit histograms of all passes are accumulated during key emission.

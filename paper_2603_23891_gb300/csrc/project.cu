@@ -1,13 +1,12 @@
 // Projection, SH colour, scene-adaptive shrinking and Gaussian-tile key
 // emission (§3.1, §3.3) on sm_103a.
 //
-// One thread per selected Gaussian, 256 per tile, persistent blocks taking
-// tiles from a ticket counter.  The radix digit histograms of every emitted key
-// (all sort passes) are accumulated here, per block in shared memory.  Each thread computes the splat record (centre,
-// conic, log-domain skip threshold, opacity, depth, colour, footprint radius),
-// its tile rectangle and pair count; a block scan plus a decoupled look-back
-// across tiles gives every Gaussian its first pair slot, so pairs are emitted
-// in selection order (the tie-break of the stable (tile | depth) sort).
+// Two passes.  project_kernel: one thread per selected Gaussian computes the
+// splat record (centre, conic, log-domain skip threshold, opacity, depth,
+// colour, footprint radius), its tile rectangle and pair count, and each tile
+// of 256 Gaussians its pair total.  emit_kernel: exclusive prefixes of those
+// totals give every Gaussian its first pair slot, so pairs are emitted in
+// selection order (the tie-break of the stable (tile | depth) sort).
 #include "fgs_internal.cuh"
 
 namespace fgs {
@@ -90,57 +89,46 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi)
 
 }  // namespace
 
-__global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
+// Pass 1: one thread per selected Gaussian.  Writes the splat record, a 16-byte
+// footprint record {x0, x1, y0, y1 (u16), pair count, depth bits} and, per tile
+// of 256 Gaussians, the tile's pair total.  No inter-block dependency.
+__global__ void __launch_bounds__(kProjThreads) project_kernel(
     DevTree t, DevCamera cam, const uint32_t* __restrict__ sel, float* __restrict__ splat,
-    unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals, unsigned long long cap,
-    unsigned long long* lookback, FrameState* st)
+    uint4* __restrict__ foot, uint32_t* __restrict__ tile_total, FrameState* st)
 {
     __shared__ uint32_t s_warp_tot[kProjThreads / 32];
-    __shared__ uint32_t s_tile, s_prefix;
-    __shared__ uint32_t s_hist[kMaxSortPasses][256];   // radix digit histograms of emitted keys
     grid_dep_wait();
     grid_dep_trigger();
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < kMaxSortPasses * 256; i += kProjThreads) (&s_hist[0][0])[i] = 0;
-    const int passes = cam.sort_passes;
     const uint32_t M = st->M;
     const uint32_t n_tiles = (M + kProjThreads - 1) / kProjThreads;
-    const uint32_t tag = st->epoch * 16u + 1u;
     const float fw = (float)cam.tile_w, fh = (float)cam.tile_h;
     const float ftx = (float)cam.tiles_x, fty = (float)cam.tiles_y;
 
-    for (;;) {
-        if (tid == 0) s_tile = atomicAdd(&st->tickets[kTicketProject], 1u);
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= n_tiles) break;
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint32_t m = tile * kProjThreads + tid;
-        const bool valid = m < M;
-        // ---- 1. everything that decides the pair count (decision-exact binary32)
-        uint32_t cnt = 0, n = 0;
-        int32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-        float mx = 0.0f, my = 0.0f, mz = 0.0f, vz = 0.0f, u = 0.0f, v = 0.0f;
-        float A = 0.0f, B = 0.0f, C = 0.0f, radius = 0.0f, a0 = 0.0f, lthr = 0.0f;
-        if (valid) {
-            n = __ldg(sel + m);
+        uint32_t cnt = 0;
+        if (m < M) {
+            // ---- decision-exact binary32: frustum, EWA covariance, footprint
+            const uint32_t n = __ldg(sel + m);
             const size_t np = t.n_pad;
-            mx = __ldg(t.mu + n);
-            my = __ldg(t.mu + np + n);
-            mz = __ldg(t.mu + 2 * np + n);
+            const float mx = __ldg(t.mu + n), my = __ldg(t.mu + np + n), mz = __ldg(t.mu + 2 * np + n);
             float s6[6];
 #pragma unroll
             for (int q = 0; q < 6; ++q) s6[q] = __ldg(t.cov + q * np + n);
-            a0 = __ldg(t.opacity + n);
+            const float a0 = __ldg(t.opacity + n);
             const float ln_a0 = __ldg(t.ln_opacity + n);
-            float vx, vy, txtz = 0.0f, tytz = 0.0f;
+            float vx, vy, vz, txtz = 0.0f, tytz = 0.0f;
             camera_space(cam, mx, my, mz, vx, vy, vz);
             const bool inf = frustum_test(cam, vx, vy, vz, txtz, tytz);
             float a = 0.0f, b = 0.0f, c = 0.0f, lam = 0.0f;
             if (inf) ewa_cov2d(cam, vz, txtz, tytz, s6, a, b, c, lam);
-            u = fa(fm(cam.fx, fd(vx, vz)), cam.cx);
-            v = fa(fm(cam.fy, fd(vy, vz)), cam.cy);
+            const float u = fa(fm(cam.fx, fd(vx, vz)), cam.cx);
+            const float v = fa(fm(cam.fy, fd(vy, vz)), cam.cy);
             const float det = fs(fm(a, c), fm(b, b));
-            lthr = fs(-5.5412635451584258f, ln_a0);   // -ln 255 - ln alpha0
+            const float lthr = fs(-5.5412635451584258f, ln_a0);   // -ln 255 - ln alpha0
+            float A = 0.0f, B = 0.0f, C = 0.0f, radius = 0.0f;
+            int32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0;
             if (inf && det > 0.0f) {
                 A = fd(c, det);
                 B = fd(-b, det);
@@ -164,39 +152,9 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
                     if (x1 > x0 && y1 > y0) cnt = (uint32_t)((x1 - x0) * (y1 - y0));
                 }
             }
-        }
-        // ---- 2. block scan of the pair counts, publish the tile aggregate
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t up = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= (uint32_t)o) incl += up;
-        }
-        if (lane == 31) s_warp_tot[warp] = incl;
-        __syncthreads();
-        uint32_t off = 0, total = 0;
-#pragma unroll
-        for (int w = 0; w < kProjThreads / 32; ++w) {
-            const uint32_t tw = s_warp_tot[w];
-            off += (w < (int)warp) ? tw : 0u;
-            total += tw;
-        }
-        if (warp == 0) {
-            uint32_t prefix = 0;
-            if (tile == 0) {
-                if (lane == 0) st_lb_u64(lookback + tile, lb_pack(tag, kFlagIncl, total));
-            } else {
-                if (lane == 0) st_lb_u64(lookback + tile, lb_pack(tag, kFlagAgg, total));
-                prefix = warp_lookback(lookback, tile, tag, st, 0x200u);
-                if (lane == 0) st_lb_u64(lookback + tile, lb_pack(tag, kFlagIncl, prefix + total));
-            }
-            if (lane == 0) {
-                s_prefix = prefix;
-                if (tile == n_tiles - 1) st->n_pairs = (unsigned long long)prefix + total;
-            }
-        }
-        // ---- 3. colour and splat record (overlaps the look-back of warp 0)
-        if (valid) {
+            foot[m] = make_uint4((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16),
+                                 cnt, __float_as_uint(vz));
+            // ---- colour (FMA allowed: decides nothing)
             float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
             const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
             dx *= il; dy *= il; dz *= il;
@@ -207,19 +165,85 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
             out[1] = make_float4(C, lthr, a0, vz);
             out[2] = make_float4(rgb[0], rgb[1], rgb[2], radius);
         }
+        const uint32_t wsum = warp_sum_u32(cnt);
+        if (lane == 0) s_warp_tot[warp] = wsum;
         __syncthreads();
-        // ---- 4. warp-cooperative emission: the warp's pairs are numbered 0..wtot-1
-        // in (Gaussian, row-major tile) order and written by consecutive lanes.
-        // Pair q belongs to the lane whose inclusive count first exceeds q.
-        {
-            const unsigned long long wfirst = (unsigned long long)s_prefix + off;
+        if (tid == 0) {
+            uint32_t tot = 0;
+#pragma unroll
+            for (int w = 0; w < kProjThreads / 32; ++w) tot += s_warp_tot[w];
+            tile_total[tile] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+// Pass 2: pair slots and key emission.  Block b takes kEmitTiles consecutive
+// Gaussian tiles; its first slot is the sum of all earlier tile totals (a block
+// reduction, no waiting on other blocks).  Within a tile a block scan orders
+// the Gaussians, and each warp writes its pairs with consecutive lanes on
+// consecutive slots.  The radix digit histograms of all sort passes are
+// accumulated here, per block in shared memory.
+__global__ void __launch_bounds__(kProjThreads) emit_kernel(
+    DevCamera cam, const uint4* __restrict__ foot, const uint32_t* __restrict__ tile_total,
+    unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals, unsigned long long cap,
+    FrameState* st)
+{
+    __shared__ uint32_t s_warp_tot[kProjThreads / 32];
+    __shared__ unsigned long long s_red[kProjThreads / 32];
+    __shared__ uint32_t s_hist[kMaxSortPasses][256];
+    grid_dep_wait();
+    grid_dep_trigger();
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int passes = cam.sort_passes;
+    for (int i = tid; i < kMaxSortPasses * 256; i += kProjThreads) (&s_hist[0][0])[i] = 0;
+    const uint32_t M = st->M;
+    const uint32_t n_tiles = (M + kProjThreads - 1) / kProjThreads;
+    const uint32_t n_groups = (n_tiles + kEmitTiles - 1) / kEmitTiles;
+    bool any = false;
+    for (uint32_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        any = true;
+        const uint32_t t0 = g * kEmitTiles;
+        // exclusive prefix of the group: sum of all earlier tile totals
+        unsigned long long part = 0;
+        for (uint32_t i = tid; i < t0; i += kProjThreads) part += __ldg(tile_total + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) s_red[warp] = part;
+        __syncthreads();
+        unsigned long long prefix = 0;
+#pragma unroll
+        for (int w = 0; w < kProjThreads / 32; ++w) prefix += s_red[w];
+        for (uint32_t tile = t0; tile < t0 + kEmitTiles && tile < n_tiles; ++tile) {
+            const uint32_t m = tile * kProjThreads + tid;
+            uint4 f = make_uint4(0, 0, 0, 0);
+            if (m < M) f = __ldg(foot + m);
+            const uint32_t cnt = f.z;
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t up = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += up;
+            }
+            if (lane == 31) s_warp_tot[warp] = incl;
+            __syncthreads();
+            uint32_t off = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < kProjThreads / 32; ++w) {
+                const uint32_t tw = s_warp_tot[w];
+                off += (w < (int)warp) ? tw : 0u;
+                total += tw;
+            }
+            const unsigned long long wfirst = prefix + off;
             const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
             const uint32_t excl = incl - cnt;
+            const int32_t x0 = (int32_t)(f.x & 0xFFFFu), x1 = (int32_t)(f.x >> 16);
+            const int32_t y0 = (int32_t)(f.y & 0xFFFFu);
             const int32_t rw = x1 - x0;
-            const uint32_t dbits = __float_as_uint(vz);
             if (lane == 0 && wtot && wfirst + wtot > cap) set_status(st, kErrCapacity, 0x300u);
             for (uint32_t q0 = 0; q0 < wtot; q0 += 32) {
                 const uint32_t q = q0 + lane;
+                // owner of pair q: smallest lane whose inclusive count exceeds q
                 uint32_t lo = 0;
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1) {
@@ -230,7 +254,7 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
                 const int32_t o_x0 = __shfl_sync(0xffffffffu, x0, lo);
                 const int32_t o_rw = __shfl_sync(0xffffffffu, rw, lo);
                 const int32_t o_y0 = __shfl_sync(0xffffffffu, y0, lo);
-                const uint32_t o_d = __shfl_sync(0xffffffffu, dbits, lo);
+                const uint32_t o_d = __shfl_sync(0xffffffffu, f.w, lo);
                 const uint32_t o_m = __shfl_sync(0xffffffffu, m, lo);
                 if (q < wtot) {
                     const unsigned long long idx = wfirst + q;
@@ -247,10 +271,13 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
                     }
                 }
             }
+            prefix += total;
+            if (tile == n_tiles - 1 && tid == 0) st->n_pairs = prefix;
+            __syncthreads();
         }
-        __syncthreads();
     }
-    // flush this block's digit histograms (non-zero bins only)
+    if (!any) return;
+    __syncthreads();
     for (int i = tid; i < passes * 256; i += kProjThreads) {
         const uint32_t c = (&s_hist[0][0])[i];
         if (c) atomicAdd(&st->hist[0][0] + i, c);
@@ -258,19 +285,29 @@ __global__ void __launch_bounds__(kProjThreads) project_emit_kernel(
 }
 
 void launch_project_emit(const DevTree& t, const DevCamera& cam, const uint32_t* sel,
-                         float* splat, unsigned long long* keys, uint32_t* vals,
-                         unsigned long long cap, unsigned long long* lookback, FrameState* st,
-                         int blocks, cudaStream_t s)
+                         float* splat, uint4* foot, uint32_t* tile_total,
+                         unsigned long long* keys, uint32_t* vals, unsigned long long cap,
+                         FrameState* st, int proj_blocks, int emit_blocks, cudaStream_t s)
 {
-    if (blocks < 1) blocks = 1;
-    launch_pdl(project_emit_kernel, blocks, kProjThreads, 0, s, t, cam, sel, splat, keys, vals, cap,
-               lookback, st);
+    if (proj_blocks < 1) proj_blocks = 1;
+    if (emit_blocks < 1) emit_blocks = 1;
+    launch_pdl(project_kernel, proj_blocks, kProjThreads, 0, s, t, cam, sel, splat, foot, tile_total,
+               st);
+    launch_pdl(emit_kernel, emit_blocks, kProjThreads, 0, s, cam, (const uint4*)foot,
+               (const uint32_t*)tile_total, keys, vals, cap, st);
 }
 
 int occ_project()
 {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, project_emit_kernel, kProjThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, project_kernel, kProjThreads, 0);
+    return b > 0 ? b : 1;
+}
+
+int occ_emit()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, emit_kernel, kProjThreads, 0);
     return b > 0 ? b : 1;
 }
 
