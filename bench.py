@@ -248,6 +248,24 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
+    # traversal-free filter vs the serial level-by-level baseline (Eq. 3 / Table 2),
+    # same poses, wall time of each call on an idle stream
+    filt_par, filt_lw, lw_levels = [], [], 0
+    sel_buf = np.zeros(tree.n, np.uint32)
+    m_buf = np.zeros(1, np.uint32)
+    for k in my_poses[: min(16, len(my_poses))]:
+        r.set_camera(cams[k])
+        for rep in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            filtergs.fgs_filter(r.ctx, r.stream, sel_buf, tree.n, m_buf, 0)
+            t1 = time.perf_counter()
+            lw_levels = filtergs.fgs_filter_levelwise(r.ctx, r.stream, sel_buf, tree.n, m_buf, 0)
+            t2 = time.perf_counter()
+            if rep == 1:
+                filt_par.append((t1 - t0) * 1e3)
+                filt_lw.append((t2 - t1) * 1e3)
+
     frames = K * world
     fps = frames / (total_ms / 1e3)
     result = None
@@ -297,6 +315,12 @@ def run_ours(args):
             "e2e": {"value": round(frames / e2e_s, 2), "unit": "frames/s",
                     "h2d_bytes_per_step": cam_bytes, "d2h_bytes_per_step": img_bytes},
             "gpu_launches": int(K * launches),
+            "filter_vs_levelwise": {
+                "parallel_ms": round(float(np.median(filt_par)), 4),
+                "levelwise_ms": round(float(np.median(filt_lw)), 4),
+                "levels": lw_levels,
+                "speedup": round(float(np.median(filt_lw) / np.median(filt_par)), 2),
+                "how": "host wall time per call incl. result copy-out, median over poses"},
             "clocks": clk,
             "calibration_s": round(calib_s, 3),
             "wall_s_timed": round(wall, 4),

@@ -60,6 +60,9 @@ extern "C" {
 
 #define FGS_N_STAGES 6             /* filter-R&L, ancestor+compact, project+keys, sort, ranges, blend */
 
+/* fgs_render_batch flags (FGS_RENDER_STATS also applies) */
+#define FGS_BATCH_GRAPH 4u         /* replay the batch as one captured CUDA graph */
+
 typedef struct fgs_ctx fgs_ctx;
 
 /* LoD tree in structure-of-arrays form, HOST pointers (§3.1 "Hierarchical
@@ -109,6 +112,8 @@ typedef struct fgs_params {
     int32_t tile_w, tile_h;   /* tile size in pixels: 64x4, 32x8, 16x16 (default) or 8x32 */
     float bg[3];              /* background colour added as T * bg */
     uint64_t pair_capacity;   /* max Gaussian-tile pairs per frame (0 = keep current / default) */
+    int32_t blend_warp_w;     /* blend block shape: warps of 8x4 (8, default; 0 = 8) or 4x8 (4) pixels */
+    int32_t reserved;
 } fgs_params;
 
 typedef struct fgs_stats {
@@ -174,6 +179,18 @@ int fgs_set_shrink(fgs_ctx* ctx, int mode, float tau, float ln_tau);
  * (synchronising). */
 int fgs_filter(fgs_ctx* ctx, void* stream, uint32_t* sel_out, uint32_t cap, uint32_t* M_out,
                int out_is_device);
+
+/* Comparison baseline of §3.2 (Eq. 3): the serial level-by-level selection
+ * that the traversal-free filter replaces.  From the root, one kernel per tree
+ * level evaluates R&L for the current frontier; a node that passes is
+ * selected, otherwise its children form the next frontier.  The host reads the
+ * frontier size after every level (one launch and one synchronisation per
+ * level).  Returns the same selection as fgs_filter (ascending ids, up to cap;
+ * *M_out = M), and the number of levels visited in *levels_out (may be NULL).
+ * Synchronising (host round trip per level) whatever out_is_device says.
+ * Errors as fgs_filter. */
+int fgs_filter_levelwise(fgs_ctx* ctx, void* stream, uint32_t* sel_out, uint32_t cap,
+                         uint32_t* M_out, int out_is_device, uint32_t* levels_out);
 
 /* Render one frame of the current camera: filter, project, shrink, emit keys,
  * sort, tile ranges, blend.  rgb_out: float [3][H][W] planar colour
@@ -252,6 +269,41 @@ int fgs_eval_exp(const float* x, float* y, uint64_t n, void* stream);
  * FGS_ERR_ARG, FGS_ERR_CUDA. */
 int fgs_compact_selection_noalloc(const uint32_t* selbits, uint64_t n_words, uint32_t* ids_out,
                                   uint32_t* count_out, void* stream);
+
+/* Batched multi-view form (next form beside §3.2-§3.3's single view: many
+ * views of uneven resolution per call).  Set-up for n_views (1..64) cameras
+ * (host array): tile_shapes (may be NULL = the context's tile and blend warp
+ * shape) holds {tile_w, tile_h, blend_warp_w} per view; sel_capacity / pair_capacity bound the selected
+ * entries and Gaussian-tile pairs of the whole batch (0 = defaults: views x
+ * nodes up to 64 Mi entries, 128 Mi pairs).  Allocates the batch buffers.
+ * The batch keeps the context's tau_R, background and shrink mode as they are
+ * at each fgs_render_batch call.  Errors: FGS_ERR_ARG, FGS_ERR_STATE (no
+ * tree), FGS_ERR_NOMEM. */
+int fgs_batch_setup(fgs_ctx* ctx, const fgs_camera* views, int n_views, const int32_t* tile_shapes,
+                    uint64_t sel_capacity, uint64_t pair_capacity);
+
+/* Replace the batch's cameras (same count and resolutions; host array). */
+int fgs_batch_set_cameras(fgs_ctx* ctx, const fgs_camera* views, int n_views);
+
+/* Pixel offset of every view's image in the batch outputs: offsets_out[v]
+ * (n_views + 1 values, host).  View v's colour planes start at
+ * rgb_out + 3 * offsets_out[v] ([3][H_v][W_v]) and its transmittance at
+ * T_out + offsets_out[v]; offsets_out[n_views] is the total pixel count. */
+int fgs_batch_image_offsets(const fgs_ctx* ctx, uint64_t* offsets_out);
+
+/* Render every view of the batch with one pass of the kernels over all views:
+ * multi-view R&L and Ancestor filters (each node and ancestor path read once
+ * for all views), one compaction, projection and key emission with global
+ * tile ids, one (global tile | depth) radix sort, one blend launch over all
+ * views' tiles.  Per view the result equals fgs_render with the same camera
+ * and tile shape.  rgb_out / T_out are DEVICE buffers of 3 * total and total
+ * pixels (see fgs_batch_image_offsets); T_out may be NULL.  flags:
+ * FGS_BATCH_GRAPH replays a CUDA graph captured on first use for these output
+ * pointers (re-captured when they change); FGS_RENDER_STATS synchronises and
+ * fills st (n_selected, n_pairs over the batch).  Asynchronous otherwise.
+ * Errors: FGS_ERR_STATE (no set-up), FGS_ERR_CAPACITY (with STATS), CUDA. */
+int fgs_render_batch(fgs_ctx* ctx, void* stream, float* rgb_out, float* T_out, uint32_t flags,
+                     fgs_stats* st);
 
 /* Wait for the stream and return any latched device status, then clear it. */
 int fgs_sync(fgs_ctx* ctx, void* stream);

@@ -51,6 +51,14 @@ struct fgs_ctx {
     bool has_tree = false;
     DevTree tree{};
     void* tree_mem = nullptr;
+    // children (CSR) for the level-wise baseline, and its frontiers
+    uint32_t root = 0;
+    uint32_t* child_start = nullptr;
+    uint32_t* children = nullptr;
+    uint32_t* frontier0 = nullptr;
+    uint32_t* frontier1 = nullptr;
+    uint32_t* d_counter = nullptr;
+    uint32_t* h_counter = nullptr;   // pinned
     // camera / shrink
     bool has_cam = false;
     fgs_camera cam{};
@@ -90,9 +98,37 @@ struct fgs_ctx {
     // last frame
     bool have_frame = false;
     bool sorted_in_1 = false;
+    // batched multi-view state
+    struct Batch {
+        int V = 0;
+        std::vector<fgs_camera> cams;
+        std::vector<int32_t> tile_w, tile_h, warp_w;
+        std::vector<uint32_t> tile_base;          // V + 1
+        std::vector<unsigned long long> img_off;  // V + 1 (pixels)
+        uint32_t total_tiles = 0;
+        int passes = 0;
+        uint64_t sel_cap = 0, pair_cap = 0;
+        DevCamera* d_cams = nullptr;
+        DevCamera* h_cams = nullptr;              // pinned staging
+        uint32_t* d_tile_base = nullptr;
+        unsigned long long* d_img_off = nullptr;
+        uint32_t *pbits = nullptr, *selbits = nullptr, *sel = nullptr, *tile_total = nullptr;
+        float* splat = nullptr;
+        uint4* foot = nullptr;
+        unsigned long long *keys0 = nullptr, *keys1 = nullptr, *lb_compact = nullptr, *lb_sort = nullptr;
+        uint32_t *vals0 = nullptr, *vals1 = nullptr;
+        uint2* ranges = nullptr;
+        FrameState* st = nullptr;
+        cudaGraphExec_t graph = nullptr;
+        float* graph_rgb = nullptr;
+        float* graph_T = nullptr;
+        bool sorted_in_1 = false;
+    } batch;
 };
 
 namespace {
+
+bool finite_all(const float* p, size_t n);
 
 int fail(fgs_ctx* c, int code, const char* fmt, ...)
 {
@@ -214,7 +250,47 @@ DevCamera make_devcam(const fgs_ctx* c, bool force_shrink_off)
     const int tiles = d.tiles_x * d.tiles_y;
     const int tile_bits = ilog2(tiles);
     d.sort_passes = 4 + (tile_bits + 7) / 8;
+    d.warp_shift = c->params.blend_warp_w == 4 ? 2 : 3;
     return d;
+}
+
+DevCamera make_devcam_for(const fgs_ctx* c, const fgs_camera& cam, int tile_w, int tile_h, int warp_w)
+{
+    DevCamera d{};
+    std::memcpy(d.R, cam.R, sizeof d.R);
+    std::memcpy(d.t, cam.t, sizeof d.t);
+    d.fx = cam.fx;
+    d.fy = cam.fy;
+    d.cx = cam.cx;
+    d.cy = cam.cy;
+    d.tan_half_x = cam.tan_half_x;
+    d.tan_half_y = cam.tan_half_y;
+    std::memcpy(d.campos, cam.campos, sizeof d.campos);
+    d.width = cam.width;
+    d.height = cam.height;
+    d.tile_w = tile_w;
+    d.tile_h = tile_h;
+    d.tile_shift_x = ilog2(tile_w);
+    d.tile_shift_y = ilog2(tile_h);
+    d.tiles_x = (d.width + tile_w - 1) / tile_w;
+    d.tiles_y = (d.height + tile_h - 1) / tile_h;
+    d.tau_R = c->params.tau_R;
+    d.shrink = c->shrink;
+    d.tau = c->tau;
+    d.ln_tau = c->ln_tau;
+    std::memcpy(d.bg, c->params.bg, sizeof d.bg);
+    d.sort_passes = 0;
+    d.warp_shift = warp_w == 4 ? 2 : 3;
+    return d;
+}
+
+bool valid_camera(const fgs_camera* cam)
+{
+    return finite_all(cam->R, 9) && finite_all(cam->t, 3) && finite_all(cam->campos, 3) &&
+           std::isfinite(cam->fx) && std::isfinite(cam->fy) && std::isfinite(cam->cx) &&
+           std::isfinite(cam->cy) && cam->fx > 0 && cam->fy > 0 && cam->tan_half_x > 0 &&
+           cam->tan_half_y > 0 && std::isfinite(cam->tan_half_x) && std::isfinite(cam->tan_half_y) &&
+           cam->width >= 1 && cam->height >= 1 && cam->width <= 16384 && cam->height <= 16384;
 }
 
 int check_ready(fgs_ctx* c)
@@ -236,7 +312,7 @@ int enqueue_front(fgs_ctx* c, const DevCamera& dc, cudaStream_t s, cudaEvent_t* 
     launches += 2;
     if (ev) cudaEventRecord(ev[1], s);
     launch_filter_anc(c->tree, c->pbits, c->selbits, c->sms * c->occ_anc, s);
-    launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->lb_compact, c->st,
+    launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->tree.n_pad, c->lb_compact, c->st,
                    c->sms * c->occ_compact, s);
     launches += 2;
     if (ev) cudaEventRecord(ev[2], s);
@@ -314,6 +390,7 @@ int fgs_create(fgs_ctx** out, int device)
     c->params.tau_R = 3.0f;
     c->params.tile_w = 16;
     c->params.tile_h = 16;
+    c->params.blend_warp_w = 8;
     c->params.bg[0] = c->params.bg[1] = c->params.bg[2] = 0.0f;
     c->params.pair_capacity = kDefaultPairCap;
     int r = FGS_OK;
@@ -336,11 +413,22 @@ int fgs_destroy(fgs_ctx* c)
     if (!c) return FGS_OK;
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
-    void* bufs[] = {c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->foot, c->tile_total,
+    void* bufs[] = {c->child_start, c->children, c->frontier0, c->frontier1, c->d_counter,
+                    c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->foot, c->tile_total,
                     c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->lb_sort, c->ranges,
                     c->G, c->img, c->st};
     for (void* p : bufs) free_ptr(p);
+    {
+        auto& b = c->batch;
+        void* bb[] = {b.d_cams, b.d_tile_base, b.d_img_off, b.pbits, b.selbits, b.sel, b.tile_total,
+                      b.splat, b.foot, b.keys0, b.keys1, b.lb_compact, b.lb_sort, b.vals0, b.vals1,
+                      b.ranges, b.st};
+        for (void* p : bb) free_ptr(p);
+        if (b.h_cams) cudaFreeHost(b.h_cams);
+        if (b.graph) cudaGraphExecDestroy(b.graph);
+    }
     if (c->st_host) cudaFreeHost(c->st_host);
+    if (c->h_counter) cudaFreeHost(c->h_counter);
     if (c->ev_ready)
         for (int i = 0; i < kEventSlots; ++i)
             for (int k = 0; k <= kStages; ++k) cudaEventDestroy(c->ev[i][k]);
@@ -358,12 +446,17 @@ int fgs_set_params(fgs_ctx* c, const fgs_params* p)
         p->tile_w < 8 || p->tile_h < 4)
         return fail(c, FGS_ERR_ARG, "tile %dx%d must be 64x4, 32x8, 16x16 or 8x32", p->tile_w,
                     p->tile_h);
+    const int ww = p->blend_warp_w ? p->blend_warp_w : 8;
+    if ((ww != 8 && ww != 4) || p->tile_h < 32 / ww)
+        return fail(c, FGS_ERR_ARG, "blend warp width %d not supported for tile %dx%d", ww, p->tile_w,
+                    p->tile_h);
     if (!finite_all(p->bg, 3)) return fail(c, FGS_ERR_ARG, "background not finite");
     if (p->pair_capacity > kMaxPairCap) return fail(c, FGS_ERR_ARG, "pair capacity too large");
     DeviceGuard g(c->device);
     c->params.tau_R = p->tau_R;
     c->params.tile_w = p->tile_w;
     c->params.tile_h = p->tile_h;
+    c->params.blend_warp_w = ww;
     std::memcpy(c->params.bg, p->bg, sizeof p->bg);
     if (p->pair_capacity) {
         int r = ensure_pairs(c, p->pair_capacity);
@@ -513,6 +606,26 @@ int fgs_load_tree(fgs_ctx* c, const fgs_tree* t)
     dt.ap = (const uint32_t*)(base + o_ap);
     int r = ensure_nodes(c, n_pad);
     if (r) return r;
+    // children lists (CSR, ascending ids) for the level-wise baseline
+    {
+        std::vector<uint32_t> start(N + 1, 0), kids(N > 1 ? N - 1 : 1), fill;
+        for (uint64_t n = 0; n < N; ++n) {
+            if (t->parent[n] >= 0) start[t->parent[n] + 1]++;
+            else c->root = (uint32_t)n;
+        }
+        for (uint64_t n = 0; n < N; ++n) start[n + 1] += start[n];
+        fill.assign(start.begin(), start.end() - 1);
+        for (uint64_t n = 0; n < N; ++n)
+            if (t->parent[n] >= 0) kids[fill[t->parent[n]]++] = (uint32_t)n;
+        if ((r = grow(c, (void**)&c->child_start, (N + 1) * 4))) return r;
+        if ((r = grow(c, (void**)&c->children, kids.size() * 4))) return r;
+        if ((r = grow(c, (void**)&c->frontier0, N * 4))) return r;
+        if ((r = grow(c, (void**)&c->frontier1, N * 4))) return r;
+        if (!c->d_counter && (r = grow(c, (void**)&c->d_counter, 16))) return r;
+        if (!c->h_counter) FGS_CUDA(c, cudaMallocHost((void**)&c->h_counter, 16));
+        FGS_CUDA(c, cudaMemcpy(c->child_start, start.data(), (N + 1) * 4, cudaMemcpyHostToDevice));
+        FGS_CUDA(c, cudaMemcpy(c->children, kids.data(), kids.size() * 4, cudaMemcpyHostToDevice));
+    }
     c->has_tree = true;
     return FGS_OK;
 }
@@ -573,10 +686,60 @@ int fgs_filter(fgs_ctx* c, void* stream, uint32_t* sel_out, uint32_t cap, uint32
     launch_frame_begin(c->st, c->ranges, dc.tiles_x * dc.tiles_y, s);
     launch_filter_pred(c->tree, dc, c->pbits, c->sms * c->occ_pred, s);
     launch_filter_anc(c->tree, c->pbits, c->selbits, c->sms * c->occ_anc, s);
-    launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->lb_compact, c->st,
+    launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->tree.n_pad, c->lb_compact, c->st,
                    c->sms * c->occ_compact, s);
     FGS_CUDA(c, cudaGetLastError());
     c->have_frame = false;
+    if (out_is_device) {
+        const size_t n = std::min<size_t>(cap, c->tree.n);
+        if (n) FGS_CUDA(c, cudaMemcpyAsync(sel_out, c->sel, n * 4, cudaMemcpyDeviceToDevice, s));
+        FGS_CUDA(c, cudaMemcpyAsync(M_out, &c->st->M, 4, cudaMemcpyDeviceToDevice, s));
+        return FGS_OK;
+    }
+    if ((r = read_state(c, s))) return r;
+    const uint32_t M = c->st_host->M;
+    *M_out = M;
+    const size_t n = std::min<size_t>(cap, M);
+    if (n) FGS_CUDA(c, cudaMemcpy(sel_out, c->sel, n * 4, cudaMemcpyDeviceToHost));
+    if ((r = latched_status(c))) {
+        clear_status(c, s);
+        return r;
+    }
+    if (M > cap) return fail(c, FGS_ERR_CAPACITY, "selection of %u exceeds cap %u", M, cap);
+    return FGS_OK;
+}
+
+int fgs_filter_levelwise(fgs_ctx* c, void* stream, uint32_t* sel_out, uint32_t cap, uint32_t* M_out,
+                         int out_is_device, uint32_t* levels_out)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!sel_out || !M_out) return fail(c, FGS_ERR_ARG, "null output");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const DevCamera dc = make_devcam(c, false);
+    launch_frame_begin(c->st, c->ranges, dc.tiles_x * dc.tiles_y, s);
+    FGS_CUDA(c, cudaMemsetAsync(c->selbits, 0, c->tree.n_pad / 32 * 4, s));
+    c->h_counter[0] = c->root;
+    FGS_CUDA(c, cudaMemcpyAsync(c->frontier0, c->h_counter, 4, cudaMemcpyHostToDevice, s));
+    uint32_t n_front = 1, levels = 0;
+    uint32_t* cur = c->frontier0;
+    uint32_t* nxt = c->frontier1;
+    while (n_front > 0 && levels <= c->tree.depth + 1) {
+        FGS_CUDA(c, cudaMemsetAsync(c->d_counter, 0, 4, s));
+        launch_levelwise_step(c->tree, dc, c->child_start, c->children, cur, n_front, nxt,
+                              c->d_counter, c->selbits, s);
+        FGS_CUDA(c, cudaMemcpyAsync(c->h_counter, c->d_counter, 4, cudaMemcpyDeviceToHost, s));
+        FGS_CUDA(c, cudaStreamSynchronize(s));     // one synchronisation per level (Eq. 3)
+        n_front = c->h_counter[0];
+        std::swap(cur, nxt);
+        ++levels;
+    }
+    launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->tree.n_pad, c->lb_compact, c->st,
+                   c->sms * c->occ_compact, s);
+    FGS_CUDA(c, cudaGetLastError());
+    c->have_frame = false;
+    if (levels_out) *levels_out = levels;
     if (out_is_device) {
         const size_t n = std::min<size_t>(cap, c->tree.n);
         if (n) FGS_CUDA(c, cudaMemcpyAsync(sel_out, c->sel, n * 4, cudaMemcpyDeviceToDevice, s));
@@ -783,6 +946,197 @@ int fgs_eval_exp(const float* x, float* y, uint64_t n, void* stream)
     if (n == 0) return FGS_OK;
     launch_eval_exp(x, y, n, (cudaStream_t)stream);
     return cudaGetLastError() == cudaSuccess ? FGS_OK : FGS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// batched multi-view form
+// ---------------------------------------------------------------------------
+int fgs_batch_setup(fgs_ctx* c, const fgs_camera* views, int n_views, const int32_t* tile_shapes,
+                    uint64_t sel_capacity, uint64_t pair_capacity)
+{
+    if (!c || !views || n_views < 1 || n_views > 64) return FGS_ERR_ARG;
+    if (!c->has_tree) return fail(c, FGS_ERR_STATE, "no tree loaded");
+    for (int v = 0; v < n_views; ++v)
+        if (!valid_camera(views + v)) return fail(c, FGS_ERR_ARG, "view %d: invalid camera", v);
+    if ((uint64_t)n_views * c->tree.n_pad >= (1ull << 32))
+        return fail(c, FGS_ERR_ARG, "views x nodes exceeds 2^32 selection entries");
+    DeviceGuard g(c->device);
+    auto& b = c->batch;
+    if (b.graph) {
+        cudaGraphExecDestroy(b.graph);
+        b.graph = nullptr;
+    }
+    b.V = n_views;
+    b.cams.assign(views, views + n_views);
+    b.tile_w.assign(n_views, c->params.tile_w);
+    b.tile_h.assign(n_views, c->params.tile_h);
+    b.warp_w.assign(n_views, c->params.blend_warp_w);
+    if (tile_shapes) {
+        for (int v = 0; v < n_views; ++v) {
+            const int tw = tile_shapes[3 * v], th = tile_shapes[3 * v + 1];
+            const int ww = tile_shapes[3 * v + 2] ? tile_shapes[3 * v + 2] : 8;
+            if (!is_pow2(tw) || !is_pow2(th) || tw * th != 256 || tw < 8 || th < 4 ||
+                (ww != 8 && ww != 4) || th < 32 / ww)
+                return fail(c, FGS_ERR_ARG, "view %d: tile %dx%d / warp %d not supported", v, tw, th, ww);
+            b.tile_w[v] = tw;
+            b.tile_h[v] = th;
+            b.warp_w[v] = ww;
+        }
+    }
+    b.tile_base.assign(n_views + 1, 0);
+    b.img_off.assign(n_views + 1, 0);
+    for (int v = 0; v < n_views; ++v) {
+        const uint32_t tx = (views[v].width + b.tile_w[v] - 1) / b.tile_w[v];
+        const uint32_t ty = (views[v].height + b.tile_h[v] - 1) / b.tile_h[v];
+        b.tile_base[v + 1] = b.tile_base[v] + tx * ty;
+        b.img_off[v + 1] = b.img_off[v] + (unsigned long long)views[v].width * views[v].height;
+    }
+    b.total_tiles = b.tile_base[n_views];
+    b.passes = 4 + (ilog2((int)b.total_tiles) + 7) / 8;
+    if (b.passes > kMaxSortPasses) return fail(c, FGS_ERR_ARG, "too many tiles in the batch");
+    const uint64_t sel_cap = sel_capacity ? sel_capacity : std::min<uint64_t>((uint64_t)n_views * c->tree.n_pad, 64ull << 20);
+    const uint64_t pair_cap = pair_capacity ? pair_capacity : (128ull << 20);
+    if (pair_cap > kMaxPairCap) return fail(c, FGS_ERR_ARG, "pair capacity too large");
+    const size_t n_words = c->tree.n_pad / 32;
+    int r;
+    if ((r = grow(c, (void**)&b.d_cams, sizeof(DevCamera) * n_views))) return r;
+    if (!b.h_cams) FGS_CUDA(c, cudaMallocHost((void**)&b.h_cams, sizeof(DevCamera) * 64));
+    if ((r = grow(c, (void**)&b.d_tile_base, 4 * (n_views + 1)))) return r;
+    if ((r = grow(c, (void**)&b.d_img_off, 8 * (n_views + 1)))) return r;
+    if ((r = grow(c, (void**)&b.pbits, 4 * n_words * n_views))) return r;
+    if ((r = grow(c, (void**)&b.selbits, 4 * n_words * n_views))) return r;
+    if ((r = grow(c, (void**)&b.lb_compact, 8 * (n_words * n_views / kCompactWords + 2)))) return r;
+    if (sel_cap != b.sel_cap) {
+        if ((r = grow(c, (void**)&b.sel, 4 * sel_cap))) return r;
+        if ((r = grow(c, (void**)&b.splat, 4 * kSplatStride * sel_cap))) return r;
+        if ((r = grow(c, (void**)&b.foot, sizeof(uint4) * sel_cap))) return r;
+        if ((r = grow(c, (void**)&b.tile_total, 4 * (sel_cap / kProjThreads + 8)))) return r;
+        b.sel_cap = sel_cap;
+    }
+    if (pair_cap != b.pair_cap) {
+        const size_t n = pair_cap + 8;
+        if ((r = grow(c, (void**)&b.keys0, 8 * n))) return r;
+        if ((r = grow(c, (void**)&b.keys1, 8 * n))) return r;
+        if ((r = grow(c, (void**)&b.vals0, 4 * n))) return r;
+        if ((r = grow(c, (void**)&b.vals1, 4 * n))) return r;
+        if ((r = grow(c, (void**)&b.lb_sort, 8 * 256 * (pair_cap / kSortTile + 2)))) return r;
+        b.pair_cap = pair_cap;
+    }
+    if ((r = grow(c, (void**)&b.ranges, sizeof(uint2) * b.total_tiles))) return r;
+    if (!b.st) {
+        if ((r = grow(c, (void**)&b.st, sizeof(FrameState)))) return r;
+    }
+    FGS_CUDA(c, cudaMemcpy(b.d_tile_base, b.tile_base.data(), 4 * (n_views + 1), cudaMemcpyHostToDevice));
+    FGS_CUDA(c, cudaMemcpy(b.d_img_off, b.img_off.data(), 8 * (n_views + 1), cudaMemcpyHostToDevice));
+    return FGS_OK;
+}
+
+int fgs_batch_set_cameras(fgs_ctx* c, const fgs_camera* views, int n_views)
+{
+    if (!c || !views) return FGS_ERR_ARG;
+    auto& b = c->batch;
+    if (b.V == 0) return fail(c, FGS_ERR_STATE, "no batch set up");
+    if (n_views != b.V) return fail(c, FGS_ERR_ARG, "batch has %d views", b.V);
+    for (int v = 0; v < n_views; ++v) {
+        if (!valid_camera(views + v)) return fail(c, FGS_ERR_ARG, "view %d: invalid camera", v);
+        if (views[v].width != b.cams[v].width || views[v].height != b.cams[v].height)
+            return fail(c, FGS_ERR_ARG, "view %d: resolution differs from the batch set-up", v);
+    }
+    b.cams.assign(views, views + n_views);
+    return FGS_OK;
+}
+
+int fgs_batch_image_offsets(const fgs_ctx* c, uint64_t* offsets_out)
+{
+    if (!c || !offsets_out) return FGS_ERR_ARG;
+    const auto& b = c->batch;
+    if (b.V == 0) return FGS_ERR_STATE;
+    for (int v = 0; v <= b.V; ++v) offsets_out[v] = b.img_off[v];
+    return FGS_OK;
+}
+
+namespace {
+
+void enqueue_batch(fgs_ctx* c, float* rgb, float* T, cudaStream_t s)
+{
+    auto& b = c->batch;
+    launch_batch_front(c->tree, b.d_cams, b.V, b.total_tiles, b.d_tile_base, b.passes, b.pbits,
+                       b.selbits, b.sel, (uint32_t)b.sel_cap, b.splat, b.foot, b.tile_total, b.keys0, b.vals0, b.keys1,
+                       b.vals1, b.pair_cap, b.lb_compact, b.lb_sort, b.ranges, b.st, c->sms, s);
+    b.sorted_in_1 = (b.passes & 1) != 0;
+    launch_batch_blend(b.d_cams, b.V, b.total_tiles, b.d_tile_base, b.d_img_off, b.ranges,
+                       b.sorted_in_1 ? b.vals1 : b.vals0, b.splat, rgb, T, b.st, s);
+}
+
+}  // namespace
+
+int fgs_render_batch(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, uint32_t flags,
+                     fgs_stats* st)
+{
+    if (!c || !rgb_out) return FGS_ERR_ARG;
+    auto& b = c->batch;
+    if (b.V == 0) return fail(c, FGS_ERR_STATE, "no batch set up");
+    if (!c->has_tree) return fail(c, FGS_ERR_STATE, "no tree loaded");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int v = 0; v < b.V; ++v) {
+        DevCamera d = make_devcam_for(c, b.cams[v], b.tile_w[v], b.tile_h[v], b.warp_w[v]);
+        d.sort_passes = b.passes;
+        b.h_cams[v] = d;
+    }
+    FGS_CUDA(c, cudaMemcpyAsync(b.d_cams, b.h_cams, sizeof(DevCamera) * b.V, cudaMemcpyHostToDevice, s));
+    const int launches = 8 + b.passes;
+    if (flags & FGS_BATCH_GRAPH) {
+        if (!b.graph || b.graph_rgb != rgb_out || b.graph_T != T_out) {
+            if (b.graph) {
+                cudaGraphExecDestroy(b.graph);
+                b.graph = nullptr;
+            }
+            cudaStream_t cs;
+            FGS_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            FGS_CUDA(c, cudaStreamSynchronize(s));
+            cudaGraph_t graph = nullptr;
+            FGS_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            enqueue_batch(c, rgb_out, T_out, cs);
+            const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+            cudaStreamDestroy(cs);
+            if (ce != cudaSuccess)
+                return fail(c, FGS_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+            const cudaError_t ie = cudaGraphInstantiate(&b.graph, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess)
+                return fail(c, FGS_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ie));
+            b.graph_rgb = rgb_out;
+            b.graph_T = T_out;
+        }
+        FGS_CUDA(c, cudaGraphLaunch(b.graph, s));
+    } else {
+        enqueue_batch(c, rgb_out, T_out, s);
+    }
+    FGS_CUDA(c, cudaGetLastError());
+    if (st) {
+        std::memset(st, 0, sizeof *st);
+        st->n_launches = (uint32_t)launches;
+    }
+    if (flags & FGS_RENDER_STATS) {
+        FGS_CUDA(c, cudaMemcpyAsync(c->st_host, b.st, sizeof(FrameState), cudaMemcpyDeviceToHost, s));
+        FGS_CUDA(c, cudaStreamSynchronize(s));
+        if (st) {
+            st->n_selected = c->st_host->M;
+            st->n_pairs = c->st_host->n_pairs;
+            st->device_status = c->st_host->status;
+        }
+        if (c->st_host->status) {
+            const int code = c->st_host->status == kErrCapacity ? FGS_ERR_CAPACITY : FGS_ERR_TIMEOUT;
+            FGS_CUDA(c, cudaMemsetAsync(&b.st->status, 0, 8, s));
+            return fail(c, code, "batch: device status %d (N_P %llu, selected %u)", c->st_host->status,
+                        (unsigned long long)c->st_host->n_pairs, c->st_host->M);
+        }
+        if (c->st_host->M > b.sel_cap)
+            return fail(c, FGS_ERR_CAPACITY, "batch selection %u exceeds capacity %llu", c->st_host->M,
+                        (unsigned long long)b.sel_cap);
+    }
+    return FGS_OK;
 }
 
 int fgs_sync(fgs_ctx* c, void* stream)

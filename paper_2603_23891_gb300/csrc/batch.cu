@@ -1,0 +1,357 @@
+// Batched multi-view form of the render path (many views of uneven resolution
+// per call, sm_103a).
+//
+// All views go through one sequence of kernels instead of one sequence per view:
+//  * bpred_kernel    R&L (§3.2) for every view: each node's centre and covariance
+//                    are read once and tested against all V cameras;
+//  * banc_kernel     Ancestor filter per view: a node's ancestor path AP is read
+//                    once for all views in which the node passed R&L;
+//  * compaction      the per-view selection bits are one concatenated bit array
+//                    [V][words]; the render path's compaction kernel turns it into
+//                    global entries v * n_pad + node (ascending: view, then node);
+//  * bproject / bemit projection, shrink and key emission with a global tile id
+//                    (the view's first tile + the tile), so one stable radix sort
+//                    of (global tile | depth) keys orders every view at once;
+//  * tile ranges, then bblend over all views' tiles; a CTA finds its view by
+//    binary search over the views' first tiles and blends with that camera.
+// Per view, selection, pairs, their order and every pixel are those of the
+// single-view path with the same camera and tile shape.
+#include "blend_impl.cuh"
+#include "project_impl.cuh"
+
+namespace fgs {
+
+constexpr int kMaxBatchViews = 64;
+
+__global__ void bframe_begin_kernel(FrameState* st, uint2* ranges, uint32_t n_tiles)
+{
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        st->epoch = st->epoch + 1;
+        st->M = 0;
+        st->n_pairs = 0;
+    }
+    if (tid < 16) st->tickets[tid] = 0;
+    for (uint32_t i = tid; i < kMaxSortPasses * 256; i += gridDim.x * blockDim.x) (&st->hist[0][0])[i] = 0;
+    for (uint32_t i = tid; i < n_tiles; i += gridDim.x * blockDim.x) ranges[i] = make_uint2(0, 0);
+}
+
+// R&L for V views: 4 consecutive nodes per thread, cameras in shared memory.
+__global__ void __launch_bounds__(256) bpred_kernel(DevTree t, const DevCamera* __restrict__ cams,
+                                                    int V, uint32_t* __restrict__ pbits)
+{
+    __shared__ DevCamera s_cam[kMaxBatchViews];
+    for (int i = threadIdx.x; i < V * (int)(sizeof(DevCamera) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(s_cam)[i] = reinterpret_cast<const uint32_t*>(cams)[i];
+    __syncthreads();
+    const uint32_t n_chunks = t.n_pad >> 2;
+    const uint32_t n_words = t.n_pad >> 5;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_chunks; i += stride) {
+        const uint32_t n0 = i << 2;
+        const float4 mx = __ldg(reinterpret_cast<const float4*>(t.mu) + i);
+        const float4 my = __ldg(reinterpret_cast<const float4*>(t.mu + t.n_pad) + i);
+        const float4 mz = __ldg(reinterpret_cast<const float4*>(t.mu + 2 * (size_t)t.n_pad) + i);
+        const uint32_t leaf = (__ldg(t.leaf_bits + (i >> 3)) >> ((i & 7) << 2)) & 0xFu;
+        const float xs[4] = {mx.x, mx.y, mx.z, mx.w};
+        const float ys[4] = {my.x, my.y, my.z, my.w};
+        const float zs[4] = {mz.x, mz.y, mz.z, mz.w};
+        float4 cv[6];
+        bool have_cov = false;
+        for (int v = 0; v < V; ++v) {
+            const DevCamera& cam = s_cam[v];
+            float vz[4], txtz[4], tytz[4];
+            uint32_t inf = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float vx, vy;
+                camera_space(cam, xs[k], ys[k], zs[k], vx, vy, vz[k]);
+                txtz[k] = tytz[k] = 0.0f;
+                const bool in = (n0 + k < t.n) && frustum_test(cam, vx, vy, vz[k], txtz[k], tytz[k]);
+                inf |= (uint32_t)in << k;
+            }
+            uint32_t pnib = inf & leaf;
+            const uint32_t need = inf & ~leaf;
+            if (need) {
+                if (!have_cov) {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q)
+                        cv[q] = __ldg(reinterpret_cast<const float4*>(t.cov + q * (size_t)t.n_pad) + i);
+                    have_cov = true;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!((need >> k) & 1u)) continue;
+                    float s6[6];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q)
+                        s6[q] = k == 0 ? cv[q].x : k == 1 ? cv[q].y : k == 2 ? cv[q].z : cv[q].w;
+                    float a, b, cc, lam;
+                    ewa_cov2d(cam, vz[k], txtz[k], tytz[k], s6, a, b, cc, lam);
+                    if (fm(3.0f, fsq(lam)) <= cam.tau_R) pnib |= 1u << k;
+                }
+            }
+            uint32_t w = pnib << ((lane & 7) << 2);
+            w |= __shfl_xor_sync(0xffffffffu, w, 1);
+            w |= __shfl_xor_sync(0xffffffffu, w, 2);
+            w |= __shfl_xor_sync(0xffffffffu, w, 4);
+            if ((lane & 7) == 0) pbits[(size_t)v * n_words + (i >> 3)] = w;
+        }
+    }
+}
+
+// Ancestor filter for V views: the path is read once per node, then checked
+// against the P bits of every view in which the node passed.
+__global__ void __launch_bounds__(256) banc_kernel(DevTree t, int V, const uint32_t* __restrict__ pbits,
+                                                   uint32_t* __restrict__ selbits)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t n_words = t.n_pad >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_words; w += n_warps) {
+        const uint32_t n = (w << 5) + lane;
+        uint64_t mine = 0;                        // bit v: P in view v
+        for (int v = 0; v < V; ++v)
+            if ((__ldg(pbits + (size_t)v * n_words + w) >> lane) & 1u) mine |= 1ull << v;
+        if (n >= t.n) mine = 0;
+        uint64_t keep = mine;
+        if (mine) {
+            uint32_t a[16];
+            for (uint32_t k0 = 0; k0 < t.depth && keep; k0 += 16) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    a[q] = (k0 + q < t.depth) ? __ldg(t.ap + (size_t)(k0 + q) * t.n_pad + n) : kApPad;
+                uint64_t left = keep;
+                while (left) {
+                    const int v = __ffsll((long long)left) - 1;
+                    left &= left - 1;
+                    const uint32_t* pv = pbits + (size_t)v * n_words;
+                    bool blocked = false;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        if (a[q] == kApPad) break;
+                        if ((__ldg(pv + (a[q] >> 5)) >> (a[q] & 31)) & 1u) { blocked = true; break; }
+                    }
+                    if (blocked) keep &= ~(1ull << v);
+                }
+                if (a[15] == kApPad) break;
+            }
+        }
+        for (int v = 0; v < V; ++v) {
+            const uint32_t b = __ballot_sync(0xffffffffu, (keep >> v) & 1ull);
+            if (lane == (uint32_t)(v & 31)) selbits[(size_t)v * n_words + w] = b;
+        }
+    }
+}
+
+// Projection of every selected entry g (entry = view * n_pad + node).
+__global__ void __launch_bounds__(kProjThreads) bproject_kernel(
+    DevTree t, const DevCamera* __restrict__ cams, int V, const uint32_t* __restrict__ sel,
+    float* __restrict__ splat, uint4* __restrict__ foot, uint32_t* __restrict__ tile_total,
+    FrameState* st)
+{
+    __shared__ DevCamera s_cam[kMaxBatchViews];
+    __shared__ uint32_t s_warp_tot[kProjThreads / 32];
+    for (int i = threadIdx.x; i < V * (int)(sizeof(DevCamera) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(s_cam)[i] = reinterpret_cast<const uint32_t*>(cams)[i];
+    __syncthreads();
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t M = st->M;
+    const uint32_t n_tiles = (M + kProjThreads - 1) / kProjThreads;
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint32_t m = tile * kProjThreads + tid;
+        uint32_t cnt = 0;
+        if (m < M) {
+            const uint32_t e = __ldg(sel + m);
+            const uint32_t v = e / t.n_pad;
+            cnt = proj::project_one(t, s_cam[v], e - v * t.n_pad, m, splat, foot);
+        }
+        const uint32_t wsum = warp_sum_u32(cnt);
+        if (lane == 0) s_warp_tot[warp] = wsum;
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t tot = 0;
+#pragma unroll
+            for (int w = 0; w < kProjThreads / 32; ++w) tot += s_warp_tot[w];
+            tile_total[tile] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+// Key emission with global tile ids (same slots and order rules as emit_kernel).
+__global__ void __launch_bounds__(kProjThreads) bemit_kernel(
+    const DevCamera* __restrict__ cams, const uint32_t* __restrict__ tile_base, uint32_t n_pad,
+    int passes, const uint32_t* __restrict__ sel, const uint4* __restrict__ foot,
+    const uint32_t* __restrict__ tile_total, unsigned long long* __restrict__ keys,
+    uint32_t* __restrict__ vals, unsigned long long cap, FrameState* st)
+{
+    __shared__ uint32_t s_warp_tot[kProjThreads / 32];
+    __shared__ unsigned long long s_red[kProjThreads / 32];
+    __shared__ uint32_t s_hist[kMaxSortPasses][256];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < kMaxSortPasses * 256; i += kProjThreads) (&s_hist[0][0])[i] = 0;
+    const uint32_t M = st->M;
+    const uint32_t n_tiles = (M + kProjThreads - 1) / kProjThreads;
+    const uint32_t n_groups = (n_tiles + kEmitTiles - 1) / kEmitTiles;
+    bool any = false;
+    for (uint32_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        any = true;
+        const uint32_t t0 = g * kEmitTiles;
+        unsigned long long part = 0;
+        for (uint32_t i = tid; i < t0; i += kProjThreads) part += __ldg(tile_total + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) s_red[warp] = part;
+        __syncthreads();
+        unsigned long long prefix = 0;
+#pragma unroll
+        for (int w = 0; w < kProjThreads / 32; ++w) prefix += s_red[w];
+        for (uint32_t tile = t0; tile < t0 + kEmitTiles && tile < n_tiles; ++tile) {
+            const uint32_t m = tile * kProjThreads + tid;
+            uint4 f = make_uint4(0, 0, 0, 0);
+            uint32_t tiles_x = 1, tbase = 0;
+            if (m < M) {
+                f = __ldg(foot + m);
+                const uint32_t v = __ldg(sel + m) / n_pad;
+                tiles_x = (uint32_t)cams[v].tiles_x;
+                tbase = __ldg(tile_base + v);
+            }
+            const uint32_t cnt = f.z;
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t up = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += up;
+            }
+            if (lane == 31) s_warp_tot[warp] = incl;
+            __syncthreads();
+            uint32_t off = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < kProjThreads / 32; ++w) {
+                const uint32_t tw = s_warp_tot[w];
+                off += (w < (int)warp) ? tw : 0u;
+                total += tw;
+            }
+            const unsigned long long wfirst = prefix + off;
+            const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t excl = incl - cnt;
+            const int32_t x0 = (int32_t)(f.x & 0xFFFFu), x1 = (int32_t)(f.x >> 16);
+            const int32_t y0 = (int32_t)(f.y & 0xFFFFu);
+            const int32_t rw = x1 - x0;
+            if (lane == 0 && wtot && wfirst + wtot > cap) set_status(st, kErrCapacity, 0x310u);
+            for (uint32_t q0 = 0; q0 < wtot; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                uint32_t lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t probe = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                    if (probe <= q) lo += step;
+                }
+                const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, lo);
+                const int32_t o_x0 = __shfl_sync(0xffffffffu, x0, lo);
+                const int32_t o_rw = __shfl_sync(0xffffffffu, rw, lo);
+                const int32_t o_y0 = __shfl_sync(0xffffffffu, y0, lo);
+                const uint32_t o_d = __shfl_sync(0xffffffffu, f.w, lo);
+                const uint32_t o_m = __shfl_sync(0xffffffffu, m, lo);
+                const uint32_t o_tx = __shfl_sync(0xffffffffu, tiles_x, lo);
+                const uint32_t o_tb = __shfl_sync(0xffffffffu, tbase, lo);
+                if (q < wtot) {
+                    const unsigned long long idx = wfirst + q;
+                    if (idx < cap) {
+                        const int32_t k = (int32_t)(q - o_excl);
+                        const uint32_t ty = (uint32_t)(o_y0 + k / o_rw);
+                        const uint32_t tx = (uint32_t)(o_x0 + k % o_rw);
+                        const unsigned long long tl = (unsigned long long)(o_tb + ty * o_tx + tx);
+                        const unsigned long long key = (tl << 32) | o_d;
+                        keys[idx] = key;
+                        vals[idx] = o_m;
+                        for (int p = 0; p < passes; ++p)
+                            atomicAdd(&s_hist[p][(uint32_t)(key >> (8 * p)) & 0xFFu], 1u);
+                    }
+                }
+            }
+            prefix += total;
+            if (tile == n_tiles - 1 && tid == 0) st->n_pairs = prefix;
+            __syncthreads();
+        }
+    }
+    if (!any) return;
+    __syncthreads();
+    for (int i = tid; i < passes * 256; i += kProjThreads) {
+        const uint32_t c = (&s_hist[0][0])[i];
+        if (c) atomicAdd(&st->hist[0][0] + i, c);
+    }
+}
+
+// Blend every tile of every view; the CTA's view is found by binary search.
+__global__ void __launch_bounds__(256) bblend_kernel(const DevCamera* __restrict__ cams, int V,
+                                                     const uint32_t* __restrict__ tile_base,
+                                                     const unsigned long long* __restrict__ img_off,
+                                                     const uint2* __restrict__ ranges,
+                                                     const uint32_t* __restrict__ vals,
+                                                     const float* __restrict__ splat,
+                                                     float* __restrict__ rgb, float* __restrict__ Tout,
+                                                     FrameState* st)
+{
+    __shared__ __align__(128) blendk::BlendSmem<false> S;
+    __shared__ double s_red[8];
+    __shared__ DevCamera s_cam;
+    const uint32_t gtile = blockIdx.x;
+    int lo = 0, hi = V;                            // largest v with tile_base[v] <= gtile
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(tile_base + mid) <= gtile) lo = mid;
+        else hi = mid;
+    }
+    const int v = lo;
+    for (int i = threadIdx.x; i < (int)(sizeof(DevCamera) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(&s_cam)[i] = reinterpret_cast<const uint32_t*>(cams + v)[i];
+    __syncthreads();
+    const unsigned long long o = __ldg(img_off + v);
+    blendk::blend_tile<false>(s_cam, gtile - __ldg(tile_base + v), gtile, S, s_red, ranges, vals, splat,
+                              rgb + 3 * o, Tout ? Tout + o : nullptr, nullptr, nullptr, st);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_batch_front(const DevTree& t, const DevCamera* cams, int V, uint32_t total_tiles,
+                        const uint32_t* tile_base, int passes, uint32_t* pbits, uint32_t* selbits,
+                        uint32_t* sel, uint32_t sel_cap, float* splat, uint4* foot, uint32_t* tile_total,
+                        unsigned long long* keys0, uint32_t* vals0, unsigned long long* keys1,
+                        uint32_t* vals1, unsigned long long cap, unsigned long long* lb_compact,
+                        unsigned long long* lb_sort, uint2* ranges, FrameState* st, int sms,
+                        cudaStream_t s)
+{
+    const uint32_t n_words = t.n_pad >> 5;
+    int b0 = (int)((total_tiles + 255) / 256);
+    bframe_begin_kernel<<<b0 < 8 ? 8 : b0, 256, 0, s>>>(st, ranges, total_tiles);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bpred_kernel, 256, 0);
+    bpred_kernel<<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(t, cams, V, pbits);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, banc_kernel, 256, 0);
+    banc_kernel<<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(t, V, pbits, selbits);
+    launch_compact(selbits, (uint32_t)((size_t)n_words * V), sel, sel_cap, lb_compact, st,
+                   sms * occ_compact(), s);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bproject_kernel, kProjThreads, 0);
+    bproject_kernel<<<sms * (occ > 0 ? occ : 1), kProjThreads, 0, s>>>(t, cams, V, sel, splat, foot,
+                                                                       tile_total, st);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bemit_kernel, kProjThreads, 0);
+    bemit_kernel<<<sms * (occ > 0 ? occ : 1), kProjThreads, 0, s>>>(cams, tile_base, t.n_pad, passes,
+                                                                    sel, foot, tile_total, keys0, vals0,
+                                                                    cap, st);
+    launch_sort(keys0, vals0, keys1, vals1, cap, passes, lb_sort, st, sms * occ_sort_pass(), s);
+    const bool odd = (passes & 1) != 0;
+    launch_tile_ranges(odd ? keys1 : keys0, cap, ranges, st, sms * occ_tile_ranges(), s);
+}
+
+void launch_batch_blend(const DevCamera* cams, int V, uint32_t total_tiles, const uint32_t* tile_base,
+                        const unsigned long long* img_off, const uint2* ranges, const uint32_t* vals,
+                        const float* splat, float* rgb, float* T, FrameState* st, cudaStream_t s)
+{
+    bblend_kernel<<<total_tiles, 256, 0, s>>>(cams, V, tile_base, img_off, ranges, vals, splat, rgb, T, st);
+}
+
+}  // namespace fgs

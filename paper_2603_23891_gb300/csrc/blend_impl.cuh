@@ -1,0 +1,292 @@
+// Per-tile blending machinery shared by the single-view and the batched blend
+// kernels (see blend.cu for the design).
+#pragma once
+
+#include "fgs_internal.cuh"
+
+namespace fgs {
+namespace blendk {
+
+
+
+
+constexpr int kChunk = 256;
+constexpr int kValsSlots = kChunk + 8;     // aligned superset of one chunk
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// 1D bulk copy global -> shared; src, dst 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <bool kKpc>
+struct BlendSmem {
+    uint32_t vals[kValsSlots];
+    float4 g0[kChunk];          // u, v, A, B
+    float4 g1[kChunk];          // C, lthr, alpha0, depth
+    float4 g2[kChunk];          // r, g, b, radius
+    uint32_t wmask[kChunk];     // bit w: warp w's pixels can reach the skip threshold
+    uint16_t wlist[8][kChunk];  // per-warp list of chunk entries, in order
+    float kpc_w[kKpc ? 8 : 1][kKpc ? kChunk : 1];   // per-warp partial KPC (Eq. 5)
+    uint64_t bar;
+    int timed_out;
+};
+
+// Bring chunk [s0, e0) of the sorted values into shared memory with one TMA bulk
+// copy of the 16-byte aligned superset [s0 & ~3, (e0 + 3) & ~3).  Returns the
+// offset of s0 inside the staged copy.  Called by all threads; thread 0 issues
+// the copy and waits on the mbarrier (bounded).
+__device__ __forceinline__ uint32_t stage_vals(uint32_t* dst, uint64_t* bar, int* timed_out,
+                                               const uint32_t* vals, uint32_t s0, uint32_t e0,
+                                               uint32_t& phase, FrameState* st)
+{
+    const uint32_t a0 = s0 & ~3u;
+    const uint32_t a1 = (e0 + 3u) & ~3u;
+    const uint32_t bytes = (a1 - a0) * 4u;
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, bytes);
+        tma_bulk_g2s(dst, vals + a0, bytes, bar);
+        uint64_t spins = 0;
+        while (!mbar_try_wait(bar, phase)) {
+            if (++spins > kSpinLimit) {
+                *timed_out = 1;
+                set_status(st, kErrTimeout, 0x500u);
+                break;
+            }
+        }
+    }
+    phase ^= 1u;
+    __syncthreads();
+    return s0 - a0;
+}
+
+// Warps of a CTA cover ww x wh pixel blocks of the tile, ww = 1 << warp_shift
+// (8 or 4), wh = 32 / ww, tile_w / ww of them across; (tx0, ty0) is the tile's
+// first pixel.
+__device__ __forceinline__ void warp_origin(const DevCamera& cam, int32_t tx0, int32_t ty0, uint32_t w,
+                                            int32_t& x0, int32_t& y0)
+{
+    const uint32_t sh = (uint32_t)(cam.tile_shift_x - cam.warp_shift);   // log2(warps per row)
+    x0 = tx0 + (int32_t)((w & ((1u << sh) - 1u)) << cam.warp_shift);
+    y0 = ty0 + (int32_t)((w >> sh) << (5 - cam.warp_shift));
+}
+
+// Which warps of the tile may hold a pixel whose binary32 power reaches the
+// Gaussian's skip threshold lthr.  Exactly, power >= lthr is the ellipse
+// d^T Q d <= s with Q = [[A, B], [B, C]] and s = -2 lthr, whose bounding box has
+// half-widths sqrt(s C / det Q) and sqrt(s A / det Q).  The rounding error of the
+// binary32 power is below 1e-6 * cond(Q) * |lthr|; the box is enlarged by 5% in s
+// plus one pixel, which covers it for cond(Q) < 1e4 (cond(Q) <= tr^2 / det).
+// Beyond that, or for a singular Q, every warp keeps the Gaussian.  A warp left
+// out of the mask would have skipped the Gaussian at every one of its pixels.
+// Warp column c spans pixel centres tx0 + ww c + [0.5, ww - 0.5], row r spans
+// ty0 + wh r + [0.5, wh - 0.5]; the mask is the block of columns x rows the box
+// meets.
+__device__ __forceinline__ uint32_t warp_mask(const DevCamera& cam, int32_t tx0, int32_t ty0, float u,
+                                              float v, float A, float B, float C, float lthr)
+{
+    if (!(lthr <= 0.0f)) return 0u;             // alpha0 < 1/255: no pixel can pass
+    const float det = A * C - B * B;
+    const float tr = A + C;
+    if (!(det > 0.0f) || tr * tr > 1e4f * det) return 0xFFu;
+    const float sq = fmaf(-2.1f, lthr, 1e-4f);  // 1.05 * (-2 lthr) + 1e-4
+    const float ex = sqrtf(sq * C / det) + 1.0f;
+    const float ey = sqrtf(sq * A / det) + 1.0f;
+    const int32_t sh = cam.tile_shift_x - cam.warp_shift;   // log2(warps per tile row)
+    const int32_t ncol = 1 << sh, nrow = 8 >> sh;
+    const float ww = (float)(1 << cam.warp_shift), wh = (float)(32 >> cam.warp_shift);
+    const float iww = 1.0f / ww, iwh = 1.0f / wh;            // exact: powers of two
+    const float ux = u - (float)tx0, vy = v - (float)ty0;
+    const int32_t c_lo = max(0, (int32_t)ceilf((ux - ex - (ww - 0.5f)) * iww));
+    const int32_t c_hi = min(ncol - 1, (int32_t)floorf((ux + ex - 0.5f) * iww));
+    const int32_t r_lo = max(0, (int32_t)ceilf((vy - ey - (wh - 0.5f)) * iwh));
+    const int32_t r_hi = min(nrow - 1, (int32_t)floorf((vy + ey - 0.5f) * iwh));
+    if (c_lo > c_hi || r_lo > r_hi) return 0u;
+    const uint32_t cols = ((2u << c_hi) - 1u) & ~((1u << c_lo) - 1u);
+    uint32_t mask = 0;
+    for (int32_t r = r_lo; r <= r_hi; ++r) mask |= cols << (r << sh);
+    return mask;
+}
+
+
+// Blend one image tile (the CTA's).  `tile` is the tile in the camera's grid;
+// `gtile` indexes ranges and G_out (the same for one view; the batch's global
+// tile id).  rgb / Tout are the camera's own image planes.
+template <bool kKpc>
+__device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, uint32_t gtile,
+                                           BlendSmem<kKpc>& S, double* s_red,
+                                           const uint2* __restrict__ ranges,
+                                           const uint32_t* __restrict__ vals,
+                                           const float* __restrict__ splat, float* __restrict__ rgb,
+                                           float* __restrict__ Tout, float* __restrict__ kpc_out,
+                                           float* __restrict__ G_out, FrameState* st)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t tx0 = (int32_t)(tile % (uint32_t)cam.tiles_x) * cam.tile_w;
+    const int32_t ty0 = (int32_t)(tile / (uint32_t)cam.tiles_x) * cam.tile_h;
+    int32_t wx0, wy0;
+    warp_origin(cam, tx0, ty0, warp, wx0, wy0);
+    const int32_t x = wx0 + (int32_t)(lane & ((1u << cam.warp_shift) - 1u));
+    const int32_t y = wy0 + (int32_t)(lane >> cam.warp_shift);
+    const bool inside = x < cam.width && y < cam.height;
+    const float px = fa((float)x, 0.5f), py = fa((float)y, 0.5f);
+    const uint2 rg = ranges[gtile];
+    const uint32_t M = st->M;
+    const uint32_t s = rg.x, e = rg.y;
+
+    if (tid == 0) {
+        mbar_init(&S.bar, 1);
+        S.timed_out = 0;
+    }
+    __syncthreads();
+
+    float T = 1.0f;
+    float3 Cacc = make_float3(0.0f, 0.0f, 0.0f);
+    bool done = !inside;
+    uint32_t phase = 0;
+    double kpc_acc = 0.0;      // this thread's share of the tile's KPC sum (fixed order)
+
+    for (uint32_t s0 = s; s0 < e; s0 += kChunk) {
+        const uint32_t e0 = min(e, s0 + kChunk);
+        const uint32_t cnt = e0 - s0;
+        const uint32_t off = stage_vals(S.vals, &S.bar, &S.timed_out, vals, s0, e0, phase, st);
+        if (S.timed_out) break;
+        if (tid < cnt) {
+            uint32_t m = S.vals[off + tid];
+            if (m >= M) m = 0;      // only after a failed sort (status already latched)
+            const float4* g = reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride);
+            const float4 a = __ldg(g), b = __ldg(g + 1);
+            S.g0[tid] = a;
+            S.g1[tid] = b;
+            S.g2[tid] = __ldg(g + 2);
+            S.wmask[tid] = warp_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
+        }
+        __syncthreads();
+        // this warp's ordered list of the chunk entries that can reach its pixels
+        uint32_t wcnt = 0;
+        for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            const bool mine = j < cnt && ((S.wmask[j] >> warp) & 1u);
+            const uint32_t b = __ballot_sync(0xffffffffu, mine);
+            if (mine) S.wlist[warp][wcnt + __popc(b & ((1u << lane) - 1u))] = (uint16_t)j;
+            wcnt += __popc(b);
+        }
+        __syncwarp();
+        for (uint32_t i = 0; i < wcnt; ++i) {
+            if (!kKpc && __all_sync(0xffffffffu, done)) break;
+            const uint32_t j = S.wlist[warp][i];
+            float w = 0.0f;
+            if (!done) {
+                const float4 g0 = S.g0[j];
+                const float4 g1 = S.g1[j];
+                const float dx = fs(g0.x, px);
+                const float dy = fs(g0.y, py);
+                const float p1 = fm(fm(g0.z, dx), dx);
+                const float p2 = fm(fm(g1.x, dy), dy);
+                const float p3 = fm(fm(g0.w, dx), dy);
+                const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
+                if (!(power > 0.0f || power < g1.y)) {
+                    float alpha = fm(g1.z, exp_cw(power));
+                    alpha = alpha < 0.99f ? alpha : 0.99f;
+                    const float Tn = fm(T, fs(1.0f, alpha));
+                    if (Tn < 0.0001f) {
+                        done = true;            // stop before adding this Gaussian
+                    } else {
+                        const float4 g2 = S.g2[j];
+                        w = alpha * T;
+                        Cacc.x = fmaf(g2.x, w, Cacc.x);
+                        Cacc.y = fmaf(g2.y, w, Cacc.y);
+                        Cacc.z = fmaf(g2.z, w, Cacc.z);
+                        T = Tn;
+                    }
+                }
+            }
+            if (kKpc) {
+                // Eq. 5: sum of alpha * T over the warp's pixels for this pair
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                if (lane == 0) S.kpc_w[warp][j] = w;
+            }
+        }
+        if (kKpc) {
+            __syncthreads();
+            if (tid < cnt) {
+                const uint32_t msk = S.wmask[tid];
+                float k = 0.0f;
+#pragma unroll
+                for (int w8 = 0; w8 < 8; ++w8)
+                    if ((msk >> w8) & 1u) k += S.kpc_w[w8][tid];
+                kpc_out[s0 + tid] = k;
+                kpc_acc += (double)k;
+            }
+        }
+        const int n_done = __syncthreads_count(done);
+        if (!kKpc && n_done == (int)blockDim.x) break;
+    }
+    if (inside && rgb) {
+        const size_t hw = (size_t)cam.width * cam.height;
+        const size_t pix = (size_t)y * cam.width + x;
+        rgb[pix] = fmaf(T, cam.bg[0], Cacc.x);
+        rgb[hw + pix] = fmaf(T, cam.bg[1], Cacc.y);
+        rgb[2 * hw + pix] = fmaf(T, cam.bg[2], Cacc.z);
+        if (Tout) Tout[pix] = T;
+    }
+    if (kKpc) {
+        // Eq. 6: G = mean KPC over the tile's pairs; fixed-order block reduction
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) kpc_acc += __shfl_xor_sync(0xffffffffu, kpc_acc, o);
+        if (lane == 0) s_red[warp] = kpc_acc;
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t n = e - s;
+            double sum = 0.0;
+            for (int w8 = 0; w8 < 8; ++w8) sum += s_red[w8];
+            G_out[gtile] = n > 0 ? (float)(sum / (double)n) : __int_as_float(0x7fc00000);
+        }
+    }
+}
+
+
+}  // namespace blendk
+}  // namespace fgs

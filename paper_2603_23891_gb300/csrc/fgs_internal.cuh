@@ -21,7 +21,7 @@ constexpr int kSplatStride = 12;          // floats per splat record (48 B)
 constexpr int kSortTileItems = 16;        // keys per thread in a sort tile
 constexpr int kSortThreads = 256;
 constexpr int kSortTile = kSortTileItems * kSortThreads;   // 4096 keys
-constexpr int kMaxSortPasses = 6;         // 48 key bits: 32 depth + up to 16 tile bits
+constexpr int kMaxSortPasses = 8;         // 64-bit keys: 32 depth bits + up to 32 (global) tile bits
 constexpr int kLookbackRows = 8;          // predecessor tiles read per look-back round trip
 constexpr int kFilterTile = 4096;         // node arrays are padded to a multiple of this
 constexpr int kCompactWords = 1024;       // 32-bit selection words per compaction tile (32K nodes)
@@ -50,6 +50,7 @@ struct DevCamera {
     float tau, ln_tau;
     float bg[3];
     int32_t sort_passes;
+    int32_t warp_shift;        // blend warps cover (1 << warp_shift) x (32 >> warp_shift) pixels
 };
 
 // Tree on the device (SoA; arrays padded to a multiple of 128 nodes).
@@ -312,7 +313,8 @@ void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits,
                         cudaStream_t s);
 void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, int blocks,
                        cudaStream_t s);
-void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel,
+// Writes at most cap ids; more survivors latch FGS_ERR_CAPACITY and M = cap.
+void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel, uint32_t cap,
                     unsigned long long* lookback, FrameState* st, int blocks, cudaStream_t s);
 void launch_project_emit(const DevTree& t, const DevCamera& cam, const uint32_t* sel,
                          float* splat, uint4* foot, uint32_t* tile_total,
@@ -332,5 +334,18 @@ void launch_blend_kpc(const DevCamera& cam, const uint2* ranges, const uint32_t*
                       const float* splat, float* kpc, float* G, FrameState* st, cudaStream_t s);
 
 void launch_eval_exp(const float* x, float* y, uint64_t n, cudaStream_t s);
+void launch_batch_front(const DevTree& t, const DevCamera* cams, int V, uint32_t total_tiles,
+                        const uint32_t* tile_base, int passes, uint32_t* pbits, uint32_t* selbits,
+                        uint32_t* sel, uint32_t sel_cap, float* splat, uint4* foot, uint32_t* tile_total,
+                        unsigned long long* keys0, uint32_t* vals0, unsigned long long* keys1,
+                        uint32_t* vals1, unsigned long long cap, unsigned long long* lb_compact,
+                        unsigned long long* lb_sort, uint2* ranges, FrameState* st, int sms,
+                        cudaStream_t s);
+void launch_batch_blend(const DevCamera* cams, int V, uint32_t total_tiles, const uint32_t* tile_base,
+                        const unsigned long long* img_off, const uint2* ranges, const uint32_t* vals,
+                        const float* splat, float* rgb, float* T, FrameState* st, cudaStream_t s);
+void launch_levelwise_step(const DevTree& t, const DevCamera& cam, const uint32_t* child_start,
+                           const uint32_t* children, const uint32_t* frontier, uint32_t n_front,
+                           uint32_t* next, uint32_t* n_next, uint32_t* selbits, cudaStream_t s);
 
 }  // namespace fgs

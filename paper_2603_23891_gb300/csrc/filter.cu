@@ -182,7 +182,8 @@ void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbit
 // warp-parallel decoupled look-back across tiles give each word its first slot.
 __global__ void __launch_bounds__(256) compact_kernel(const uint32_t* __restrict__ selbits,
                                                       uint32_t n_words, uint32_t* __restrict__ sel,
-                                                      unsigned long long* lookback, FrameState* st)
+                                                      uint32_t cap, unsigned long long* lookback,
+                                                      FrameState* st)
 {
     __shared__ uint32_t s_warp_tot[8];
     __shared__ uint32_t s_tile, s_prefix;
@@ -233,7 +234,12 @@ __global__ void __launch_bounds__(256) compact_kernel(const uint32_t* __restrict
             }
             if (lane == 0) {
                 s_prefix = prefix;
-                if (tile == n_tiles - 1) st->M = prefix + total;
+                if (tile == n_tiles - 1) {
+                    // more survivors than slots: latch the error, keep M within the buffer
+                    const uint32_t m_all = prefix + total;
+                    if (m_all > cap) set_status(st, kErrCapacity, 0x110u);
+                    st->M = m_all < cap ? m_all : cap;
+                }
             }
         }
         __syncthreads();
@@ -248,19 +254,20 @@ __global__ void __launch_bounds__(256) compact_kernel(const uint32_t* __restrict
             const uint32_t wq = __shfl_sync(0xffffffffu, mine, owner);
             if (wq == 0u) continue;
             const uint32_t bq = __shfl_sync(0xffffffffu, p0 + before, owner);
-            if ((wq >> lane) & 1u) sel[bq + __popc(wq & lt)] = ((wbase_warp + q) << 5) + lane;
+            const uint32_t pos = bq + __popc(wq & lt);
+            if (((wq >> lane) & 1u) && pos < cap) sel[pos] = ((wbase_warp + q) << 5) + lane;
         }
         __syncthreads();
     }
 }
 
-void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel,
+void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel, uint32_t cap,
                     unsigned long long* lookback, FrameState* st, int blocks, cudaStream_t s)
 {
     const int n_tiles = (int)((n_words + kCompactWords - 1) / kCompactWords);
     if (blocks > n_tiles) blocks = n_tiles;
     if (blocks < 1) blocks = 1;
-    launch_pdl(compact_kernel, blocks, 256, 0, s, selbits, n_words, sel, lookback, st);
+    launch_pdl(compact_kernel, blocks, 256, 0, s, selbits, n_words, sel, cap, lookback, st);
 }
 
 int occ_filter_pred()

@@ -79,7 +79,8 @@ extern "C" int fgs_compact_selection_noalloc(const uint32_t* selbits, uint64_t n
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     noalloc_begin_kernel<<<1, 1, 0, s>>>(st);
-    launch_compact(selbits, (uint32_t)n_words, ids_out, lookback, st, sms * occ_compact(), s);
+    launch_compact(selbits, (uint32_t)n_words, ids_out, (uint32_t)(n_words * 32u), lookback, st,
+                   sms * occ_compact(), s);
     noalloc_finish_kernel<<<1, 1, 0, s>>>(st, count_out);
     return cudaGetLastError() == cudaSuccess ? FGS_OK : FGS_ERR_CUDA;
 }

@@ -29,6 +29,7 @@ FGS_SHRINK_ON = 1
 FGS_RENDER_STATS = 1
 FGS_RENDER_STAGE_EVENTS = 2
 FGS_N_STAGES = 6
+FGS_BATCH_GRAPH = 4
 STAGE_NAMES = ["filter_rl", "ancestor_compact", "project_keys", "sort", "tile_ranges", "blend"]
 SPLAT_FIELDS = ["u", "v", "A", "B", "C", "lthr", "a0", "depth", "r", "g", "b", "radius"]
 
@@ -36,7 +37,8 @@ EXPORTED = ["fgs_version", "fgs_create", "fgs_destroy", "fgs_last_error", "fgs_s
             "fgs_load_tree", "fgs_set_camera", "fgs_set_shrink", "fgs_filter", "fgs_render",
             "fgs_stage_times", "fgs_stage_count", "fgs_get_pairs", "fgs_get_splats",
             "fgs_calibrate_view", "fgs_calibrate_gtc", "fgs_sync", "fgs_validate_tree",
-            "fgs_eval_exp", "fgs_compact_selection_noalloc"]
+            "fgs_eval_exp", "fgs_compact_selection_noalloc", "fgs_filter_levelwise",
+            "fgs_batch_setup", "fgs_batch_set_cameras", "fgs_batch_image_offsets", "fgs_render_batch"]
 
 
 class FgsError(RuntimeError):
@@ -61,7 +63,8 @@ class fgs_camera(C.Structure):
 
 class fgs_params(C.Structure):
     _fields_ = [("tau_R", C.c_float), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
-                ("bg", C.c_float * 3), ("pair_capacity", C.c_uint64)]
+                ("bg", C.c_float * 3), ("pair_capacity", C.c_uint64), ("blend_warp_w", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class fgs_stats(C.Structure):
@@ -103,6 +106,11 @@ def lib():
         "fgs_validate_tree": ([C.POINTER(fgs_tree), C.c_char_p, C.c_size_t], i32),
         "fgs_eval_exp": ([vp, vp, u64, vp], i32),
         "fgs_compact_selection_noalloc": ([vp, u64, vp, vp, vp], i32),
+        "fgs_filter_levelwise": ([vp, vp, vp, u32, vp, i32, vp], i32),
+        "fgs_batch_setup": ([vp, vp, i32, vp, u64, u64], i32),
+        "fgs_batch_set_cameras": ([vp, vp, i32], i32),
+        "fgs_batch_image_offsets": ([vp, vp], i32),
+        "fgs_render_batch": ([vp, vp, vp, vp, u32, C.POINTER(fgs_stats)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -150,12 +158,14 @@ def fgs_last_error(ctx) -> str:
     return m.decode() if m else ""
 
 
-def make_params(tau_R=3.0, tile=(16, 16), bg=(0.0, 0.0, 0.0), pair_capacity=0) -> fgs_params:
+def make_params(tau_R=3.0, tile=(16, 16), bg=(0.0, 0.0, 0.0), pair_capacity=0,
+                blend_warp_w=8) -> fgs_params:
     p = fgs_params()
     p.tau_R = tau_R
     p.tile_w, p.tile_h = tile
     p.bg[:] = list(bg)
     p.pair_capacity = int(pair_capacity)
+    p.blend_warp_w = int(blend_warp_w)
     return p
 
 
@@ -235,6 +245,41 @@ def fgs_set_shrink(ctx, mode: int, tau: float = 0.0, ln_tau: float = 0.0):
 
 def fgs_filter(ctx, stream, sel_out, cap: int, M_out, out_is_device: int):
     return _check(ctx, lib().fgs_filter(ctx, stream, _ptr(sel_out), cap, _ptr(M_out), out_is_device))
+
+
+def fgs_filter_levelwise(ctx, stream, sel_out, cap: int, M_out, out_is_device: int) -> int:
+    """Serial level-by-level selection (comparison baseline); returns the level count."""
+    lv = np.zeros(1, np.uint32)
+    _check(ctx, lib().fgs_filter_levelwise(ctx, stream, _ptr(sel_out), cap, _ptr(M_out),
+                                           out_is_device, _ptr(lv)))
+    return int(lv[0])
+
+
+def _cams(cams):
+    return (fgs_camera * len(cams))(*[c if isinstance(c, fgs_camera) else make_camera(c) for c in cams])
+
+
+def fgs_batch_setup(ctx, cams, tile_shapes=None, sel_capacity: int = 0, pair_capacity: int = 0):
+    arr = _cams(cams)
+    ts = None if tile_shapes is None else np.ascontiguousarray(np.asarray(tile_shapes, np.int32).ravel())
+    return _check(ctx, lib().fgs_batch_setup(ctx, C.cast(arr, C.c_void_p), len(cams), _ptr(ts),
+                                             sel_capacity, pair_capacity))
+
+
+def fgs_batch_set_cameras(ctx, cams):
+    arr = _cams(cams)
+    return _check(ctx, lib().fgs_batch_set_cameras(ctx, C.cast(arr, C.c_void_p), len(cams)))
+
+
+def fgs_batch_image_offsets(ctx, n_views: int) -> np.ndarray:
+    out = np.zeros(n_views + 1, np.uint64)
+    _check(ctx, lib().fgs_batch_image_offsets(ctx, _ptr(out)))
+    return out
+
+
+def fgs_render_batch(ctx, stream, rgb_out, T_out, flags: int = 0, stats=None):
+    return _check(ctx, lib().fgs_render_batch(ctx, stream, _ptr(rgb_out), _ptr(T_out), flags,
+                                              C.byref(stats) if stats is not None else None))
 
 
 def fgs_render(ctx, stream, rgb_out, T_out, out_is_device: int, flags: int = 0, stats=None):
@@ -325,12 +370,14 @@ class Renderer:
         torch = _torch()
         return C.c_void_p(torch.cuda.current_stream(self.torch_device).cuda_stream)
 
-    def set_params(self, tau_R=None, tile=None, bg=None, pair_capacity=None):
+    def set_params(self, tau_R=None, tile=None, bg=None, pair_capacity=None, blend_warp_w=None):
         p = self.params
         if tau_R is not None:
             p.tau_R = tau_R
         if tile is not None:
             p.tile_w, p.tile_h = tile
+        if blend_warp_w is not None:
+            p.blend_warp_w = blend_warp_w
         if bg is not None:
             p.bg[:] = list(bg)
         p.pair_capacity = int(pair_capacity) if pair_capacity else 0
@@ -357,6 +404,14 @@ class Renderer:
         M = np.zeros(1, np.uint32)
         fgs_filter(self.ctx, self.stream, out, n, M, 0)
         return out[: int(M[0])].copy()
+
+    def filter_levelwise(self):
+        """Serial level-by-level selection (host numpy ids, level count)."""
+        n = self.tree.n
+        out = np.zeros(max(n, 1), np.uint32)
+        M = np.zeros(1, np.uint32)
+        levels = fgs_filter_levelwise(self.ctx, self.stream, out, n, M, 0)
+        return out[: int(M[0])].copy(), levels
 
     def render(self, rgb=None, T=None, stats=False, stage_events=False):
         torch = _torch()
@@ -419,3 +474,32 @@ class Renderer:
 
     def sync(self):
         fgs_sync(self.ctx, self.stream)
+
+    # ---- batched multi-view form
+    def batch_setup(self, cams, tile_shapes=None, sel_capacity=0, pair_capacity=0):
+        fgs_batch_setup(self.ctx, cams, tile_shapes, sel_capacity, pair_capacity)
+        self.batch_cams = list(cams)
+        self.batch_offsets = fgs_batch_image_offsets(self.ctx, len(cams))
+
+    def batch_set_cameras(self, cams):
+        fgs_batch_set_cameras(self.ctx, cams)
+        self.batch_cams = list(cams)
+
+    def render_batch(self, rgb=None, T=None, graph=False, stats=False):
+        """All views at once; returns (rgb, T, stats, views) where views[v] = (rgb_v, T_v)."""
+        torch = _torch()
+        total = int(self.batch_offsets[-1])
+        if rgb is None:
+            rgb = torch.empty(3 * total, dtype=torch.float32, device=self.torch_device)
+        if T is None:
+            T = torch.empty(total, dtype=torch.float32, device=self.torch_device)
+        st = fgs_stats()
+        flags = (FGS_BATCH_GRAPH if graph else 0) | (FGS_RENDER_STATS if stats else 0)
+        fgs_render_batch(self.ctx, self.stream, rgb, T, flags, st)
+        views = []
+        for v, cam in enumerate(self.batch_cams):
+            o = int(self.batch_offsets[v])
+            n = cam.width * cam.height
+            views.append((rgb[3 * o: 3 * o + 3 * n].view(3, cam.height, cam.width),
+                          T[o: o + n].view(cam.height, cam.width)))
+        return rgb, T, st, views

@@ -86,6 +86,8 @@ def test_city_benchmark_configuration(renderer, city):
         g = gpu_frame(renderer, tree, cam, 3.0, shrink=(tau, ln_tau))
         o, p = oracle_frame(tree, cam, 3.0, shrink=(tau, ln_tau), blend=False)
         assert_frame_parity(g, o, check_image=False)
+        sel_lw, _ = renderer.filter_levelwise()
+        assert np.array_equal(sel_lw, o.sel)
         n = cam.width * cam.height
         pix = np.sort(rng.choice(n, size=20000, replace=False))
         rgb, T = oracle.render_pixels(o.splat, o.keys, o.vals, cam, p, pix)

@@ -244,3 +244,21 @@ def test_needles_and_blobs_culling_exact(renderer, seed):
     g = gpu_frame(renderer, t, cam, -1.0)
     o, _ = oracle_frame(t, cam, -1.0)
     assert_frame_parity(g, o)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_levelwise_baseline_selects_same_set(renderer, seed):
+    """The serial level-by-level selection (Eq. 3 scheme) and the traversal-free filter
+    select exactly the oracle's LoD cut (§3.2, Table 3)."""
+    tree = synth.random_small_tree(20 + seed, n_leaves=5000, branching=(2, 8), sh_degree=0,
+                                   extent=25.0, log_scale_mean=-0.8)
+    renderer.load_tree(tree)
+    for cam in orbit_cameras(tree, 3, (200, 150), seed, dist=(10.0, 90.0)):
+        for tau_R in (-1.0, 3.0, 15.0, 1e30):
+            renderer.set_params(tau_R=tau_R)
+            renderer.set_camera(cam)
+            sel_lw, levels = renderer.filter_levelwise()
+            sel = renderer.filter()
+            ref = oracle.filter_dfs(tree, cam, tau_R)
+            assert np.array_equal(sel_lw, ref) and np.array_equal(sel, ref)
+            assert 1 <= levels <= tree.depth + 1
