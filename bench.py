@@ -131,6 +131,89 @@ def blend_alu_peak(sm_mhz, sms):
     return 128.0 * sms * sm_mhz * 1e6
 
 
+OPS_PER_EVAL = 11.0   # dx, dy, 3 x 2 products, sum, scale, subtract
+OPS_PER_HIT = 29.0    # exp (21), alpha and clamp (2), 1 - alpha and T (2), weight + 3 colour FMAs (4)
+
+
+def _kernel_sources_sha(kernel):
+    import hashlib
+    files = {"blend_kernel": ["blend.cu", "blend_impl.cuh", "fgs_internal.cuh"]}.get(kernel)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2603_23891_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.txt: '<kernel> <source sha16> <bytes>'), or None if the
+    kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = _kernel_sources_sha(kernel)
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 3 and parts[0] == kernel and parts[1] == sha:
+            return int(parts[2])
+    return None
+
+
+def run_batched(r, torch, filtergs, args):
+    """Batched multi-view form: 32 views (8 each at 640x360, 1280x720, 1920x1080,
+    3840x2160) over the city tree; autotuned tile / blend-warp shapes, CUDA-graph
+    replay, against the same 32 views rendered one call at a time."""
+    from paper_2603_23891_gb300 import synth
+    cams = synth.city_batch_cameras()
+    t0 = time.time()
+    choice, tuned_ms = r.batch_autotune(cams, sel_capacity=args.batch_sel_cap,
+                                        pair_capacity=args.batch_pair_cap)
+    tune_s = time.time() - t0
+    total = int(r.batch_offsets[-1])
+    rgb = torch.empty(3 * total, dtype=torch.float32, device="cuda")
+    T = torch.empty(total, dtype=torch.float32, device="cuda")
+    _, _, st, _ = r.render_batch(rgb, T, graph=True, stats=True)
+    reps = args.batch_reps
+    for _ in range(2):
+        r.render_batch(rgb, T, graph=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        r.render_batch(rgb, T, graph=True)
+    e1.record()
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / reps
+    # sequential single-view calls, default 16x16 tiles
+    r.set_params(tile=(16, 16), blend_warp_w=8)
+    outs = {}
+    for c in cams:
+        if (c.width, c.height) not in outs:
+            outs[(c.width, c.height)] = (torch.empty((3, c.height, c.width), device="cuda"),
+                                         torch.empty((c.height, c.width), device="cuda"))
+    for c in cams[:4]:
+        r.set_camera(c)
+        r.render(*outs[(c.width, c.height)])
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        for c in cams:
+            r.set_camera(c)
+            r.render(*outs[(c.width, c.height)])
+    e1.record()
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / reps
+    return {"views": len(cams), "views_per_s": round(len(cams) / (batch_ms * 1e-3), 1),
+            "ms_per_batch": round(batch_ms, 3),
+            "sequential_views_per_s": round(len(cams) / (seq_ms * 1e-3), 1),
+            "sequential_ms": round(seq_ms, 3), "speedup": round(seq_ms / batch_ms, 2),
+            "selected_entries": int(st.n_selected), "pairs": int(st.n_pairs),
+            "autotune": {f"{w}x{h}": list(v) for (w, h), v in choice.items()},
+            "autotune_s": round(tune_s, 2), "graph": True}
+
+
 # ----------------------------------------------------------------------------- ours
 
 def run_ours(args):
@@ -266,6 +349,19 @@ def run_ours(args):
                 filt_par.append((t1 - t0) * 1e3)
                 filt_lw.append((t2 - t1) * 1e3)
 
+    # blend work counters (one counting frame per pose, outside the timed region)
+    cnt_evals, cnt_hits, cnt_entries = [], [], []
+    for k in my_poses:
+        r.set_camera(cams[k])
+        _, _, st = r.render(rgb, Tt, count=True)
+        cnt_evals.append(st.blend_evals)
+        cnt_hits.append(st.blend_hits)
+        cnt_entries.append(st.blend_entries)
+
+    batched = None
+    if args.batch and args.workload == "city":
+        batched = run_batched(r, torch, filtergs, args)
+
     frames = K * world
     fps = frames / (total_ms / 1e3)
     result = None
@@ -287,14 +383,23 @@ def run_ours(args):
         dom = STAGES[int(np.argmax(st_mean))]
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         if dom == "blend":
-            # pixel-Gaussian evaluations bound by FP32 issue; report HBM view too
-            dom_rl = {"bound": "hbm", "kernel": "blend_kernel", "achieved": stages[dom]["GB/s"],
-                      "peak": hbm_peak, "unit": "GB/s", "frac": stages[dom]["frac_hbm"],
-                      "traffic": None, "peak_source": peak_src}
+            # issue-bound: FP32 lane operations of the evaluations the kernel performs
+            ops = OPS_PER_EVAL * float(np.mean(cnt_evals)) + OPS_PER_HIT * float(np.mean(cnt_hits))
+            clk_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+            peak_tf = 128.0 * sms * clk_mhz * 1e6 / 1e12
+            ach_tf = ops / (st_mean[STAGES.index("blend")] * 1e-3) / 1e12
+            dom_rl = {"bound": "alu", "kernel": "blend_kernel", "achieved": round(ach_tf, 3),
+                      "peak": round(peak_tf, 3), "unit": "TFLOP/s", "frac": round(ach_tf / peak_tf, 4),
+                      "traffic": profiled_traffic("blend_kernel"),
+                      "peak_source": f"derived: 128 FP32 lanes x {sms} SMs x {clk_mhz:.0f} MHz",
+                      "ops": "FP32 lane operations: 11 per pixel-Gaussian evaluation (power and tests), "
+                             "29 more per evaluation that applies alpha (exp, alpha, T, colour)",
+                      "hbm_view": {"achieved": stages[dom]["GB/s"], "peak": hbm_peak, "unit": "GB/s",
+                                   "frac": stages[dom]["frac_hbm"]}}
         else:
             dom_rl = {"bound": "hbm", "kernel": dom, "achieved": stages[dom]["GB/s"],
                       "peak": hbm_peak, "unit": "GB/s", "frac": stages[dom]["frac_hbm"],
-                      "traffic": None, "peak_source": peak_src}
+                      "traffic": profiled_traffic(dom), "peak_source": peak_src}
         img_bytes = 4 * H * W * 4
         cam_bytes = 4 * 26 + 8
         result = {
@@ -315,6 +420,9 @@ def run_ours(args):
             "e2e": {"value": round(frames / e2e_s, 2), "unit": "frames/s",
                     "h2d_bytes_per_step": cam_bytes, "d2h_bytes_per_step": img_bytes},
             "gpu_launches": int(K * launches),
+            "blend_work_per_frame": {"entries": round(float(np.mean(cnt_entries))),
+                                     "evaluations": round(float(np.mean(cnt_evals))),
+                                     "alpha_applied": round(float(np.mean(cnt_hits)))},
             "filter_vs_levelwise": {
                 "parallel_ms": round(float(np.median(filt_par)), 4),
                 "levelwise_ms": round(float(np.median(filt_lw)), 4),
@@ -323,6 +431,7 @@ def run_ours(args):
                 "how": "host wall time per call incl. result copy-out, median over poses"},
             "clocks": clk,
             "calibration_s": round(calib_s, 3),
+            "batched": batched,
             "wall_s_timed": round(wall, 4),
         }
     r.close()
@@ -424,6 +533,10 @@ def main():
     ap.add_argument("--lambda-g", dest="lambda_g", type=float, default=0.2)
     ap.add_argument("--pair-capacity", type=int, default=64 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--batch-reps", type=int, default=5)
+    ap.add_argument("--batch-sel-cap", type=int, default=96 << 20)
+    ap.add_argument("--batch-pair-cap", type=int, default=256 << 20)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -57,6 +57,7 @@ extern "C" {
 /* fgs_render flags */
 #define FGS_RENDER_STATS 1u        /* fill M and N_P in fgs_stats (synchronises) */
 #define FGS_RENDER_STAGE_EVENTS 2u /* record per-stage CUDA events (see fgs_stage_times) */
+#define FGS_RENDER_COUNT 8u        /* count the blend's work (fgs_stats blend_*); implies STATS */
 
 #define FGS_N_STAGES 6             /* filter-R&L, ancestor+compact, project+keys, sort, ranges, blend */
 
@@ -122,6 +123,9 @@ typedef struct fgs_stats {
     uint64_t n_pairs;         /* N_P: Gaussian-tile pairs (may exceed capacity on error) */
     uint32_t n_launches;      /* kernels this call enqueued */
     int32_t device_status;    /* latched device status (FGS_OK if none) */
+    uint64_t blend_entries;   /* FGS_RENDER_COUNT: per-warp list entries the blend walked */
+    uint64_t blend_evals;     /* FGS_RENDER_COUNT: pixel-Gaussian evaluations (pixels not stopped) */
+    uint64_t blend_hits;      /* FGS_RENDER_COUNT: evaluations that reached alpha / T (exp taken) */
 } fgs_stats;
 
 /* Library version (FGS_VERSION). */

@@ -782,7 +782,10 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
     const size_t hw = (size_t)dc.width * dc.height;
     float* rgb_dst = out_is_device ? rgb_out : c->img;
     float* T_dst = out_is_device ? T_out : (T_out ? c->img + 3 * hw : nullptr);
-    launch_blend(dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, rgb_dst, T_dst, c->st, s);
+    const bool count = (flags & FGS_RENDER_COUNT) != 0;
+    if (count) flags |= FGS_RENDER_STATS;
+    launch_blend(dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, rgb_dst, T_dst, c->st,
+                 count, s);
     ++launches;
     if (ev) cudaEventRecord(ev[6], s);
     FGS_CUDA(c, cudaGetLastError());
@@ -801,6 +804,9 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
             st->n_selected = c->st_host->M;
             st->n_pairs = c->st_host->n_pairs;
             st->device_status = c->st_host->status;
+            st->blend_entries = c->st_host->blend_entries;
+            st->blend_evals = c->st_host->blend_evals;
+            st->blend_hits = c->st_host->blend_hits;
         }
         if ((r = latched_status(c))) {
             clear_status(c, s);

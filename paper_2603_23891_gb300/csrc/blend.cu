@@ -22,7 +22,7 @@ namespace fgs {
 
 using blendk::BlendSmem;
 
-template <bool kKpc>
+template <bool kKpc, bool kCount = false>
 __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* __restrict__ ranges,
                                                     const uint32_t* __restrict__ vals,
                                                     const float* __restrict__ splat,
@@ -34,16 +34,20 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
     __shared__ double s_red[8];
     grid_dep_wait();
     grid_dep_trigger();
-    blendk::blend_tile<kKpc>(cam, blockIdx.x, blockIdx.x, S, s_red, ranges, vals, splat, rgb, Tout,
-                             kpc_out, G_out, st);
+    blendk::blend_tile<kKpc, kCount>(cam, blockIdx.x, blockIdx.x, S, s_red, ranges, vals, splat, rgb,
+                                     Tout, kpc_out, G_out, st);
 }
 
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
-                  const float* splat, float* rgb, float* T, FrameState* st, cudaStream_t s)
+                  const float* splat, float* rgb, float* T, FrameState* st, bool count, cudaStream_t s)
 {
     const int n_tiles = cam.tiles_x * cam.tiles_y;
-    launch_pdl(blend_kernel<false>, n_tiles, 256, 0, s, cam, ranges, vals, splat, rgb, T,
-               (float*)nullptr, (float*)nullptr, st);
+    if (count)
+        launch_pdl(blend_kernel<false, true>, n_tiles, 256, 0, s, cam, ranges, vals, splat, rgb, T,
+                   (float*)nullptr, (float*)nullptr, st);
+    else
+        launch_pdl(blend_kernel<false>, n_tiles, 256, 0, s, cam, ranges, vals, splat, rgb, T,
+                   (float*)nullptr, (float*)nullptr, st);
 }
 
 void launch_blend_kpc(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,

@@ -153,7 +153,7 @@ __device__ __forceinline__ uint32_t warp_mask(const DevCamera& cam, int32_t tx0,
 // Blend one image tile (the CTA's).  `tile` is the tile in the camera's grid;
 // `gtile` indexes ranges and G_out (the same for one view; the batch's global
 // tile id).  rgb / Tout are the camera's own image planes.
-template <bool kKpc>
+template <bool kKpc, bool kCount = false>
 __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, uint32_t gtile,
                                            BlendSmem<kKpc>& S, double* s_red,
                                            const uint2* __restrict__ ranges,
@@ -213,10 +213,15 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
             wcnt += __popc(b);
         }
         __syncwarp();
+        uint32_t c_entries = 0, c_evals = 0, c_hits = 0;
         for (uint32_t i = 0; i < wcnt; ++i) {
             if (!kKpc && __all_sync(0xffffffffu, done)) break;
             const uint32_t j = S.wlist[warp][i];
             float w = 0.0f;
+            if (kCount) {
+                ++c_entries;
+                c_evals += __popc(__ballot_sync(0xffffffffu, !done));
+            }
             if (!done) {
                 const float4 g0 = S.g0[j];
                 const float4 g1 = S.g1[j];
@@ -227,6 +232,7 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
                 const float p3 = fm(fm(g0.w, dx), dy);
                 const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
                 if (!(power > 0.0f || power < g1.y)) {
+                    if (kCount) ++c_hits;
                     float alpha = fm(g1.z, exp_cw(power));
                     alpha = alpha < 0.99f ? alpha : 0.99f;
                     const float Tn = fm(T, fs(1.0f, alpha));
@@ -247,6 +253,14 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
                 if (lane == 0) S.kpc_w[warp][j] = w;
+            }
+        }
+        if (kCount) {
+            c_hits = warp_sum_u32(c_hits);
+            if (lane == 0) {
+                atomicAdd(&st->blend_entries, (unsigned long long)c_entries);
+                atomicAdd(&st->blend_evals, (unsigned long long)c_evals);
+                atomicAdd(&st->blend_hits, (unsigned long long)c_hits);
             }
         }
         if (kKpc) {

@@ -78,6 +78,9 @@ struct FrameState {
     int32_t status;            // latched error (0 = ok)
     uint32_t status_info;
     uint32_t hist[kMaxSortPasses][256];   // radix digit histograms
+    unsigned long long blend_entries;     // warp-list entries walked (counting frames only)
+    unsigned long long blend_evals;       // pixel-Gaussian evaluations (lanes not yet stopped)
+    unsigned long long blend_hits;        // evaluations that reached the alpha / T update
 
 };
 
@@ -328,8 +331,9 @@ int launch_sort(unsigned long long* keys0, uint32_t* vals0, unsigned long long* 
                 unsigned long long* lookback, FrameState* st, int sort_blocks, cudaStream_t s);
 void launch_tile_ranges(const unsigned long long* keys, unsigned long long cap, uint2* ranges,
                         const FrameState* st, int blocks, cudaStream_t s);
+// count: use the counting variant (fills FrameState::blend_* work counters)
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
-                  const float* splat, float* rgb, float* T, FrameState* st, cudaStream_t s);
+                  const float* splat, float* rgb, float* T, FrameState* st, bool count, cudaStream_t s);
 void launch_blend_kpc(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
                       const float* splat, float* kpc, float* G, FrameState* st, cudaStream_t s);
 

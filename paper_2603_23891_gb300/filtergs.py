@@ -28,6 +28,7 @@ FGS_SHRINK_OFF = 0
 FGS_SHRINK_ON = 1
 FGS_RENDER_STATS = 1
 FGS_RENDER_STAGE_EVENTS = 2
+FGS_RENDER_COUNT = 8
 FGS_N_STAGES = 6
 FGS_BATCH_GRAPH = 4
 STAGE_NAMES = ["filter_rl", "ancestor_compact", "project_keys", "sort", "tile_ranges", "blend"]
@@ -69,7 +70,8 @@ class fgs_params(C.Structure):
 
 class fgs_stats(C.Structure):
     _fields_ = [("n_selected", C.c_uint32), ("reserved", C.c_uint32), ("n_pairs", C.c_uint64),
-                ("n_launches", C.c_uint32), ("device_status", C.c_int32)]
+                ("n_launches", C.c_uint32), ("device_status", C.c_int32),
+                ("blend_entries", C.c_uint64), ("blend_evals", C.c_uint64), ("blend_hits", C.c_uint64)]
 
 
 _lib = None
@@ -413,7 +415,7 @@ class Renderer:
         levels = fgs_filter_levelwise(self.ctx, self.stream, out, n, M, 0)
         return out[: int(M[0])].copy(), levels
 
-    def render(self, rgb=None, T=None, stats=False, stage_events=False):
+    def render(self, rgb=None, T=None, stats=False, stage_events=False, count=False):
         torch = _torch()
         H, W = self.cam.height, self.cam.width
         if rgb is None:
@@ -422,6 +424,7 @@ class Renderer:
             T = torch.empty((H, W), dtype=torch.float32, device=self.torch_device)
         st = fgs_stats()
         flags = (FGS_RENDER_STATS if stats else 0) | (FGS_RENDER_STAGE_EVENTS if stage_events else 0)
+        flags |= FGS_RENDER_COUNT if count else 0
         fgs_render(self.ctx, self.stream, rgb, T, 1, flags, st)
         return rgb, T, st
 
@@ -484,6 +487,47 @@ class Renderer:
     def batch_set_cameras(self, cams):
         fgs_batch_set_cameras(self.ctx, cams)
         self.batch_cams = list(cams)
+
+    def batch_autotune(self, cams, candidates=((16, 16, 8), (16, 16, 4), (32, 8, 8), (32, 8, 4)),
+                       reps=3, sel_capacity=0, pair_capacity=0):
+        """Pick {tile_w, tile_h, blend warp width} per resolution class by timing the batch.
+
+        Greedy: all classes start at candidates[0]; each class in turn keeps the
+        candidate with the lowest median batch time (CUDA events, graph replay).
+        Leaves the batch set up with the choice; returns (choice, ms)."""
+        torch = _torch()
+        classes = sorted({(c.width, c.height) for c in cams})
+        choice = {cls: candidates[0] for cls in classes}
+
+        def timed(ch):
+            shapes = [ch[(c.width, c.height)] for c in cams]
+            self.batch_setup(cams, tile_shapes=shapes, sel_capacity=sel_capacity,
+                             pair_capacity=pair_capacity)
+            total = int(self.batch_offsets[-1])
+            rgb = torch.empty(3 * total, dtype=torch.float32, device=self.torch_device)
+            T = torch.empty(total, dtype=torch.float32, device=self.torch_device)
+            self.render_batch(rgb, T, graph=True, stats=True)      # capture + capacity check
+            times = []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                self.render_batch(rgb, T, graph=True)
+                e1.record()
+                torch.cuda.synchronize(self.torch_device)
+                times.append(e0.elapsed_time(e1))
+            return float(np.median(times))
+
+        best = timed(choice)
+        for cls in classes:
+            for cand in candidates[1:]:
+                trial = dict(choice)
+                trial[cls] = cand
+                t = timed(trial)
+                if t < best:
+                    best, choice = t, trial
+        timed(choice)
+        return choice, best
 
     def render_batch(self, rgb=None, T=None, graph=False, stats=False):
         """All views at once; returns (rgb, T, stats, views) where views[v] = (rgb_v, T_v)."""

@@ -262,3 +262,21 @@ def test_levelwise_baseline_selects_same_set(renderer, seed):
             ref = oracle.filter_dfs(tree, cam, tau_R)
             assert np.array_equal(sel_lw, ref) and np.array_equal(sel, ref)
             assert 1 <= levels <= tree.depth + 1
+
+
+def test_blend_counters_consistent(renderer, tiny):
+    """The counting blend variant renders the same image and reports consistent work:
+    alpha-applying evaluations <= evaluations <= 32 x warp-list entries."""
+    import torch
+    tree, cam = tiny
+    renderer.load_tree(tree)
+    renderer.set_params(tau_R=3.0, tile=(16, 16))
+    renderer.set_camera(cam)
+    renderer.shrink(None)
+    rgb0, T0, st0 = renderer.render(stats=True)
+    rgb1, T1, st1 = renderer.render(count=True)
+    torch.cuda.synchronize()
+    assert torch.equal(rgb0, rgb1) and torch.equal(T0, T1)
+    assert st1.n_pairs == st0.n_pairs
+    assert 0 < st1.blend_hits <= st1.blend_evals <= 32 * st1.blend_entries
+    assert st1.blend_entries <= 8 * st1.n_pairs
