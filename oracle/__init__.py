@@ -15,6 +15,11 @@ Every function here follows one passage of the paper:
 * ``pairs``              §3.3 Gaussian-tile key/value pairs sorted by (tile, depth)
 * ``render``             Eq. 2 front-to-back blending, Eq. 5 KPC
 * ``gtc`` / ``tau_from`` Eq. 6, Eq. 7, Eq. 8
+* ``prep_params``        §3.1 3DGS parametrisation -> binary32 attributes
+* ``trace_pixels``       Eq. 2 contributor lists (the frozen decisions)
+* ``diff_render`` / ``diff_grad``  Eq. 1-2 as a binary64 function of the
+                         parameters with the decisions frozen, and its gradient
+                         (``oracle_grad.c``)
 """
 from __future__ import annotations
 
@@ -27,7 +32,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "oracle_grad.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -36,14 +41,14 @@ SPLAT_STRIDE = len(SPLAT_FIELDS)
 
 
 def build_lib(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so beside it (plain gcc, no contraction)."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
-                                              os.path.getmtime(os.path.join(_HERE, "oracle.h")))):
+    """Compile the oracle's C sources into liboracle.so beside them (plain gcc,
+    no contraction)."""
+    newest = max(os.path.getmtime(f) for f in _SRCS + [os.path.join(_HERE, "oracle.h")])
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+           "-fPIC", "-shared", *_SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -107,6 +112,17 @@ def lib():
         L.oracle_render_pixels.restype = C.c_int
         L.oracle_gtc.argtypes = [vp, vp, i64, i32, vp, vp]
         L.oracle_gtc.restype = i32
+        L.oracle_trace_pixels.argtypes = [vp, vp, vp, vp, vp, i64, vp, i64, vp, vp]
+        L.oracle_trace_pixels.restype = i64
+        L.oracle_lnf.argtypes = [C.c_float]
+        L.oracle_lnf.restype = C.c_float
+        L.oracle_prep_params.argtypes = [i32, vp, vp, vp, vp, vp, vp]
+        L.oracle_prep_params.restype = None
+        L.oracle_diff_render.argtypes = [vp, vp, vp, vp, i32, vp, i64, vp, vp, vp]
+        L.oracle_diff_render.restype = C.c_int
+        L.oracle_diff_grad.argtypes = [vp, vp, vp, vp, i32, vp, i64, vp, vp, vp,
+                                       vp, vp, vp, vp, vp]
+        L.oracle_diff_grad.restype = C.c_int
         _lib = L
     return _lib
 
@@ -318,3 +334,146 @@ def calibrate(tree, cams, tau_R: float, lambda_G: float = 0.2, tile=(16, 16)):
         gbars.append(gbar)
     tau, ln_tau = tau_from(gbars, lambda_G)
     return tau, ln_tau, gbars
+
+
+# ---------------------------------------------------------------------------
+# differentiable form
+# ---------------------------------------------------------------------------
+
+class _Params64(C.Structure):
+    _fields_ = [("n", C.c_int32), ("sh_degree", C.c_int32), ("mu", C.c_void_p),
+                ("log_scale", C.c_void_p), ("quat", C.c_void_p), ("logit", C.c_void_p),
+                ("sh", C.c_void_p)]
+
+
+@dataclass
+class GaussParams:
+    """Per-node parameters (3DGS parametrisation): mu [3][N], log_scale [3][N],
+    quat [4][N] (w, x, y, z), logit [N], sh [N][K][3]."""
+    mu: np.ndarray
+    log_scale: np.ndarray
+    quat: np.ndarray
+    logit: np.ndarray
+    sh: np.ndarray
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.logit.shape[0])
+
+    def astype(self, dt) -> "GaussParams":
+        return GaussParams(*[np.ascontiguousarray(getattr(self, k), dt) for k in
+                             ("mu", "log_scale", "quat", "logit", "sh")], self.sh_degree)
+
+    @staticmethod
+    def of_tree(tree) -> "GaussParams":
+        return GaussParams(tree.mu, tree.log_scale, tree.quat, tree.opacity_logit, tree.sh,
+                           tree.sh_degree).astype(np.float32)
+
+
+GRAD_FIELDS = ("mu", "log_scale", "quat", "logit", "sh")
+
+
+def lnf(x) -> np.ndarray:
+    L = lib()
+    x = np.asarray(x, np.float32).ravel()
+    return np.array([L.oracle_lnf(float(v)) for v in x], dtype=np.float32)
+
+
+def prep_params(gp: GaussParams):
+    """Binary32 (cov [6][N], opacity [N], ln_opacity [N]) from the parameters."""
+    g = gp.astype(np.float32)
+    n = g.n
+    cov = np.zeros((6, n), np.float32)
+    op = np.zeros(n, np.float32)
+    lop = np.zeros(n, np.float32)
+    lib().oracle_prep_params(n, _p(g.log_scale), _p(g.quat), _p(g.logit), _p(cov), _p(op), _p(lop))
+    return cov, op, lop
+
+
+def tree_with_params(tree, gp: GaussParams):
+    """The tree's structure with its attributes recomputed from the parameters."""
+    import dataclasses
+    cov, op, lop = prep_params(gp)
+    g = gp.astype(np.float32)
+    return dataclasses.replace(tree, mu=g.mu, cov=cov, opacity=op, ln_opacity=lop, sh=g.sh,
+                               log_scale=g.log_scale, quat=g.quat, opacity_logit=g.logit)
+
+
+def trace_pixels(splat, keys, vals, cam, params: Params, pix: np.ndarray):
+    splat = np.ascontiguousarray(splat, np.float32)
+    keys = np.ascontiguousarray(keys, np.uint64)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    pix = np.ascontiguousarray(pix, np.int64)
+    c, q = _cam(cam), _params(params)
+    L = lib()
+    n = L.oracle_trace_pixels(C.byref(c), C.byref(q), _p(splat), _p(keys), _p(vals),
+                              keys.shape[0], _p(pix), pix.shape[0], None, None)
+    offs = np.zeros(pix.shape[0] + 1, np.int64)
+    ent = np.zeros(max(n, 1), np.uint32)
+    L.oracle_trace_pixels(C.byref(c), C.byref(q), _p(splat), _p(keys), _p(vals), keys.shape[0],
+                          _p(pix), pix.shape[0], _p(offs), _p(ent))
+    return offs, ent[:n]
+
+
+def _p64(gp: GaussParams):
+    g = gp.astype(np.float64)
+    s = _Params64(g.n, g.sh_degree, *[getattr(g, k).ctypes.data for k in GRAD_FIELDS])
+    return g, s
+
+
+def diff_render(gp: GaussParams, sel, cam, bg, pix, offs, ent) -> np.ndarray:
+    """rgb [n_pix][3] of the frozen-decision binary64 forward."""
+    g, s = _p64(gp)
+    sel = np.ascontiguousarray(sel, np.uint32)
+    pix = np.ascontiguousarray(pix, np.int64)
+    bg64 = np.ascontiguousarray(bg, np.float64)
+    out = np.zeros((pix.shape[0], 3), np.float64)
+    c = _cam(cam)
+    r = lib().oracle_diff_render(C.byref(c), _p(bg64), C.byref(s), _p(sel), sel.shape[0],
+                                 _p(pix), pix.shape[0], _p(offs), _p(ent), _p(out))
+    assert r == 0
+    return out
+
+
+def diff_grad(gp: GaussParams, sel, cam, bg, pix, offs, ent, dL) -> dict:
+    """Gradient of sum(dL * rgb) (dL [n_pix][3]) with respect to every parameter."""
+    g, s = _p64(gp)
+    sel = np.ascontiguousarray(sel, np.uint32)
+    pix = np.ascontiguousarray(pix, np.int64)
+    bg64 = np.ascontiguousarray(bg, np.float64)
+    dL = np.ascontiguousarray(dL, np.float64)
+    out = {k: np.zeros_like(getattr(g, k)) for k in GRAD_FIELDS}
+    c = _cam(cam)
+    r = lib().oracle_diff_grad(C.byref(c), _p(bg64), C.byref(s), _p(sel), sel.shape[0],
+                               _p(pix), pix.shape[0], _p(offs), _p(ent), _p(dL),
+                               *[_p(out[k]) for k in GRAD_FIELDS])
+    assert r == 0
+    return out
+
+
+@dataclass
+class GradFrame:
+    frame: Frame
+    pix: np.ndarray
+    offs: np.ndarray
+    ent: np.ndarray
+    rgb: np.ndarray          # [n_pix][3], frozen binary64 forward
+    grads: dict
+
+
+def grad_frame(tree, gp: GaussParams, cam, params: Params, dL_img: np.ndarray,
+               pix: np.ndarray = None) -> GradFrame:
+    """The whole differentiable path for one view: attributes from the
+    parameters, cut, projection, pairs, contributor lists, then the binary64
+    image and the gradient of sum(dL_img * image) (dL_img planar [3][H][W];
+    only the pixels in ``pix`` count, all by default)."""
+    t = tree_with_params(tree, gp)
+    fr = frame(t, cam, params, blend=False)
+    if pix is None:
+        pix = np.arange(cam.width * cam.height, dtype=np.int64)
+    offs, ent = trace_pixels(fr.splat, fr.keys, fr.vals, cam, params, pix)
+    dL = np.asarray(dL_img, np.float64).reshape(3, -1)[:, pix].T
+    rgb = diff_render(gp, fr.sel, cam, params.bg, pix, offs, ent)
+    grads = diff_grad(gp, fr.sel, cam, params.bg, pix, offs, ent, dL)
+    return GradFrame(fr, pix, offs, ent, rgb, grads)

@@ -408,7 +408,8 @@ int64_t oracle_count_pairs_bruteforce(const ocam* c, const oparams* p, const flo
  * 1/255 (tested as power < -ln 255 - ln alpha0); alpha = min(0.99, alpha0 e^power);
  * stop, before adding, at the first Gaussian that would take T below 1e-4. */
 static void blend_pixel(const float* splat, const uint32_t* vals, int64_t b, int64_t e, float px,
-                        float py, double rgb[3], float* T_final, double* kpc)
+                        float py, double rgb[3], float* T_final, double* kpc, uint32_t* rec,
+                        int64_t* n_rec)
 {
     float T = 1.0f;
     double acc[3] = {0.0, 0.0, 0.0};
@@ -423,9 +424,14 @@ static void blend_pixel(const float* splat, const uint32_t* vals, int64_t b, int
         if (power > 0.0f) continue;
         if (power < s[ORACLE_SPLAT_LTHR]) continue;
         float alpha = s[ORACLE_SPLAT_A0] * oracle_expf(power);
+        const int clamped = !(alpha < ALPHA_MAX);
         alpha = alpha < ALPHA_MAX ? alpha : ALPHA_MAX;
         const float Tn = T * (1.0f - alpha);
         if (Tn < T_STOP) break;
+        if (n_rec) {
+            if (rec) rec[*n_rec] = vals[q] | ((uint32_t)clamped << 31);
+            ++*n_rec;
+        }
         const double w = (double)alpha * (double)T;
         acc[0] += (double)s[ORACLE_SPLAT_R] * w;
         acc[1] += (double)s[ORACLE_SPLAT_G] * w;
@@ -465,7 +471,7 @@ int oracle_render(const ocam* c, const oparams* p, const float* splat, const uin
             tile_range(keys, n_pairs, tile, &b, &e);
             double rgb[3];
             float T;
-            blend_pixel(splat, vals, b, e, (float)x + 0.5f, (float)y + 0.5f, rgb, &T, kpc_out);
+            blend_pixel(splat, vals, b, e, (float)x + 0.5f, (float)y + 0.5f, rgb, &T, kpc_out, NULL, NULL);
             for (int ch = 0; ch < 3; ++ch)
                 rgb_out[ch * W * H + y * W + x] = rgb[ch] + (double)T * (double)p->bg[ch];
             T_out[y * W + x] = T;
@@ -486,11 +492,35 @@ int oracle_render_pixels(const ocam* c, const oparams* p, const float* splat,
         tile_range(keys, n_pairs, tile, &b, &e);
         double rgb[3];
         float T;
-        blend_pixel(splat, vals, b, e, (float)x + 0.5f, (float)y + 0.5f, rgb, &T, NULL);
+        blend_pixel(splat, vals, b, e, (float)x + 0.5f, (float)y + 0.5f, rgb, &T, NULL, NULL, NULL);
         for (int ch = 0; ch < 3; ++ch) rgb_out[i * 3 + ch] = rgb[ch] + (double)T * (double)p->bg[ch];
         T_out[i] = T;
     }
     return 0;
+}
+
+int64_t oracle_trace_pixels(const ocam* c, const oparams* p, const float* splat,
+                            const uint64_t* keys, const uint32_t* vals, int64_t n_pairs,
+                            const int64_t* pix, int64_t n_pix, int64_t* offs_out,
+                            uint32_t* ent_out)
+{
+    const int64_t W = c->width;
+    const int32_t tiles_x = (c->width + p->tile_w - 1) / p->tile_w;
+    int64_t total = 0;
+    for (int64_t i = 0; i < n_pix; ++i) {
+        const int64_t x = pix[i] % W, y = pix[i] / W;
+        const uint64_t tile = (uint64_t)(y / p->tile_h) * (uint64_t)tiles_x + (uint64_t)(x / p->tile_w);
+        int64_t b, e;
+        tile_range(keys, n_pairs, tile, &b, &e);
+        double rgb[3];
+        float T;
+        if (offs_out) offs_out[i] = total;
+        /* appends this pixel's contributors at ent_out[total ...] and advances total */
+        blend_pixel(splat, vals, b, e, (float)x + 0.5f, (float)y + 0.5f, rgb, &T, NULL, ent_out,
+                    &total);
+    }
+    if (offs_out) offs_out[n_pix] = total;
+    return total;
 }
 
 /* Eq. 6: G_i = mean KPC over the n_gs pairs keyed to tile i.  Eq. 7: the view

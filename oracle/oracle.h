@@ -118,6 +118,53 @@ int oracle_render_pixels(const ocam* c, const oparams* p, const float* splat,
 int32_t oracle_gtc(const uint64_t* keys, const double* kpc, int64_t n_pairs, int32_t n_tiles,
                    double* G_out, double* Gbar_out);
 
+/* The contributors of each listed pixel (linear indices y*W+x), in blending
+ * order: splat rank | (alpha clamped at 0.99) << 31, for the pairs the Eq. 2
+ * walk adds before it stops.  offs_out[n_pix + 1] (may be NULL) indexes
+ * ent_out (may be NULL: count only).  Returns the number of entries. */
+int64_t oracle_trace_pixels(const ocam* c, const oparams* p, const float* splat,
+                            const uint64_t* keys, const uint32_t* vals, int64_t n_pairs,
+                            const int64_t* pix, int64_t n_pix, int64_t* offs_out,
+                            uint32_t* ent_out);
+
+/* ---- differentiable form (oracle_grad.c) ---------------------------- */
+
+/* Gaussian parameters in binary64: mu[3][n], log_scale[3][n], quat[4][n]
+ * (w, x, y, z; any non-zero norm), logit[n], sh[n][(deg+1)^2][3]. */
+typedef struct {
+    int32_t n;
+    int32_t sh_degree;
+    const double* mu;
+    const double* log_scale;
+    const double* quat;
+    const double* logit;
+    const double* sh;
+} oparams64;
+
+/* ln x (binary32, positive normal x), fixed operation order. */
+float oracle_lnf(float x);
+
+/* Binary32 attributes from binary32 parameters (n nodes): cov[6][n],
+ * opacity[n] = sigmoid(l), ln_opacity[n] = -ln(1 + e^{-l}), l clamped to
+ * [-80, 80]. */
+void oracle_prep_params(int32_t n, const float* log_scale, const float* quat, const float* logit,
+                        float* cov_out, float* opacity_out, float* ln_opacity_out);
+
+/* Image of the listed pixels as a binary64 function of the parameters, with
+ * the cut sel[M] and the contributor lists (oracle_trace_pixels) frozen:
+ * rgb_out[n_pix][3].  Returns 0, -1 if out of memory. */
+int oracle_diff_render(const ocam* c, const double bg[3], const oparams64* P, const uint32_t* sel,
+                       int32_t M, const int64_t* pix, int64_t n_pix, const int64_t* offs,
+                       const uint32_t* ent, double* rgb_out);
+
+/* Gradient of L = sum_i dL[i][ch] rgb[i][ch] for that function, ADDED to
+ * g_mu[3][n], g_ls[3][n], g_q[4][n], g_logit[n], g_sh[n][K][3].  Returns 0,
+ * -1 if out of memory. */
+int oracle_diff_grad(const ocam* c, const double bg[3], const oparams64* P, const uint32_t* sel,
+                     int32_t M, const int64_t* pix, int64_t n_pix, const int64_t* offs,
+                     const uint32_t* ent, const double* dL, double* g_mu, double* g_ls,
+                     double* g_q, double* g_logit, double* g_sh);
+
 #ifdef __cplusplus
 }
 #endif

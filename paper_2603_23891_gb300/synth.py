@@ -525,3 +525,25 @@ def tree_from_gaussians(mu, log_scale, quat, opacity_logit, sh, sh_degree, name=
                       np.asarray(opacity_logit, float).reshape(-1),
                       np.asarray(sh, float).reshape(n, -1, 3), sh_degree, max(n, 2), rng,
                       name=name)
+
+
+def grad_scene(seed: int = 0, n: int = 64, width: int = 32, height: int = 32,
+               sh_degree: int = 3):
+    """Small scene for gradient checks: n Gaussians under one moment-matched root
+    in front of a width x height camera (60 deg FOV, ~12.6 m away), footprints of
+    a few pixels with several layers per pixel; alpha0 in [0.05, 0.9]; base
+    colours in [0.15, 0.85] with small higher-order SH, so no colour clamps."""
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform([-4.0, -2.0, -3.0], [4.0, 2.0, 3.0], size=(n, 3))
+    logs = rng.normal(-0.3, 0.25, size=(n, 3))
+    quat = _random_quats(rng, n)
+    a0 = rng.uniform(0.05, 0.9, size=n)
+    logit = np.log(a0 / (1.0 - a0))
+    k = (sh_degree + 1) ** 2
+    sh = np.zeros((n, k, 3))
+    sh[:, 0, :] = (rng.uniform(0.15, 0.85, size=(n, 3)) - 0.5) / _C0
+    if k > 1:
+        sh[:, 1:, :] = rng.normal(0.0, 0.05, size=(n, k - 1, 3))
+    tree = tree_from_gaussians(mu, logs, quat, logit, sh, sh_degree, name=f"grad-{seed}")
+    cam = look_at_camera([0.0, -12.0, 4.0], [0.0, 0.0, 0.0], width, height, 60.0)
+    return tree, cam
