@@ -309,6 +309,69 @@ int fgs_batch_image_offsets(const fgs_ctx* ctx, uint64_t* offsets_out);
 int fgs_render_batch(fgs_ctx* ctx, void* stream, float* rgb_out, float* T_out, uint32_t flags,
                      fgs_stats* st);
 
+/* ---- differentiable form -----------------------------------------------
+ * The render as a function of per-node Gaussian parameters, in the 3D Gaussian
+ * splatting parametrisation the method builds on (§3.1), and its gradient.
+ * The selection (§3.2 cut), the Gaussian-tile pairs and every skip / stop /
+ * clamp decision of blending (Eq. 2) are held fixed: the gradient is the one
+ * of the image with those discrete choices frozen, as when a cut is trained.
+ *
+ * Parameter arrays are DEVICE pointers on the context's device, n = n_nodes of
+ * the loaded tree, float32, row-major:
+ *   mu[3][n]         centre
+ *   log_scale[3][n]  Sigma = R diag(e^{2 s}) R^T
+ *   quat[4][n]       (w, x, y, z), any non-zero norm; R = R(q / |q|)
+ *   logit[n]         alpha0 = 1 / (1 + e^{-l}), l clamped to [-80, 80]
+ *                    (zero gradient outside)
+ *   sh[n][K][3]      SH coefficients, K = (sh_degree + 1)^2;
+ *                    colour = max(0, 1/2 + sum_k Y_k(d) c_k), d the unit
+ *                    direction from the camera centre
+ * The caller owns them; the library reads (and for grads writes) them during
+ * the call's kernels only. */
+typedef struct fgs_gauss_params {
+    const float* mu;
+    const float* log_scale;
+    const float* quat;
+    const float* logit;
+    const float* sh;
+} fgs_gauss_params;
+
+typedef struct fgs_gauss_grads {
+    float* mu;
+    float* log_scale;
+    float* quat;
+    float* logit;
+    float* sh;
+} fgs_gauss_grads;
+
+#define FGS_BACKWARD_ACCUMULATE 1u  /* add into the gradient arrays instead of overwriting */
+
+/* Recompute the loaded tree's attributes from parameters: mean, Sigma,
+ * alpha0, ln alpha0 (the binary32 values the filter, projection and blending
+ * decide on, in one fixed operation order: Sigma_ij = ((R_i0 s_0) R_j0 +
+ * (R_i1 s_1) R_j1) + (R_i2 s_2) R_j2 with s_k = exp(2 log_scale_k) and the
+ * exp / ln of the library's own binary32 routines) and SH.  The tree
+ * structure (parents, leaves, ancestor paths) is unchanged.  Asynchronous on
+ * `stream`.  Errors: FGS_ERR_STATE (no tree), FGS_ERR_ARG (NULL or non-device
+ * pointer), FGS_ERR_CUDA. */
+int fgs_update_params(fgs_ctx* ctx, void* stream, const fgs_gauss_params* p);
+
+/* Gradient of L = sum over pixels and channels of dL_drgb * rgb for the last
+ * fgs_render of this context (same camera, parameters as passed to the last
+ * fgs_update_params).  dL_drgb: DEVICE [3][H][W] (the layout of fgs_render's
+ * rgb_out).  p: the parameters of that render; g: gradient arrays of the same
+ * shapes (device).  Without FGS_BACKWARD_ACCUMULATE every entry of g is
+ * written (zero for nodes outside the cut); with it, the selected nodes'
+ * gradients are added.  Two kernels: a per-tile blend backward that re-walks
+ * the tile front to back to find each pixel's final transmittance and stop,
+ * then walks back recovering T before each Gaussian as T / (1 - alpha); and a
+ * per-Gaussian chain rule through the conic, the EWA Jacobian, Sigma(q, s),
+ * the sigmoid and the SH basis.  Asynchronous on `stream`.  Errors:
+ * FGS_ERR_STATE (no rendered frame since the last change of tree, camera,
+ * parameters or settings), FGS_ERR_ARG, FGS_ERR_NOMEM, FGS_ERR_CUDA. */
+int fgs_backward(fgs_ctx* ctx, void* stream, const float* dL_drgb, const fgs_gauss_params* p,
+                 const fgs_gauss_grads* g, uint32_t flags);
+
 /* Wait for the stream and return any latched device status, then clear it. */
 int fgs_sync(fgs_ctx* ctx, void* stream);
 

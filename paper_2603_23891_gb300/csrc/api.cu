@@ -95,8 +95,12 @@ struct fgs_ctx {
     bool ev_ready = false;
     cudaEvent_t ev[kEventSlots][kStages + 1];
     uint64_t ev_count = 0;
+    // differentiable form: per selected Gaussian splat gradients
+    float* gsplat = nullptr;
+    size_t gsplat_rows = 0;
     // last frame
     bool have_frame = false;
+    bool frame_is_render = false;   // the last frame came from fgs_render (not a calibration)
     bool sorted_in_1 = false;
     // batched multi-view state
     struct Batch {
@@ -416,7 +420,7 @@ int fgs_destroy(fgs_ctx* c)
     void* bufs[] = {c->child_start, c->children, c->frontier0, c->frontier1, c->d_counter,
                     c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->foot, c->tile_total,
                     c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->lb_sort, c->ranges,
-                    c->G, c->img, c->st};
+                    c->G, c->img, c->st, c->gsplat};
     for (void* p : bufs) free_ptr(p);
     {
         auto& b = c->batch;
@@ -790,6 +794,7 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
     if (ev) cudaEventRecord(ev[6], s);
     FGS_CUDA(c, cudaGetLastError());
     c->have_frame = true;
+    c->frame_is_render = true;
     if (!out_is_device) {
         FGS_CUDA(c, cudaMemcpyAsync(rgb_out, c->img, 3 * hw * 4, cudaMemcpyDeviceToHost, s));
         if (T_out) FGS_CUDA(c, cudaMemcpyAsync(T_out, c->img + 3 * hw, hw * 4, cudaMemcpyDeviceToHost, s));
@@ -894,6 +899,7 @@ int fgs_calibrate_view(fgs_ctx* c, void* stream, double* gbar_out, float* kpc_ou
                      c->st, s);
     FGS_CUDA(c, cudaGetLastError());
     c->have_frame = true;
+    c->frame_is_render = false;
     if ((r = read_state(c, s))) return r;
     if ((r = latched_status(c))) {
         clear_status(c, s);
@@ -952,6 +958,77 @@ int fgs_eval_exp(const float* x, float* y, uint64_t n, void* stream)
     if (n == 0) return FGS_OK;
     launch_eval_exp(x, y, n, (cudaStream_t)stream);
     return cudaGetLastError() == cudaSuccess ? FGS_OK : FGS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// differentiable form
+// ---------------------------------------------------------------------------
+namespace {
+
+bool is_device_ptr(const void* p, int dev)
+{
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
+int check_param_ptrs(fgs_ctx* c, const void* const* ptrs, const char* const* names, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!is_device_ptr(ptrs[i], c->device))
+            return fail(c, FGS_ERR_ARG, "%s is not a device pointer on device %d", names[i], c->device);
+    return FGS_OK;
+}
+
+}  // namespace
+
+int fgs_update_params(fgs_ctx* c, void* stream, const fgs_gauss_params* p)
+{
+    if (!c || !p) return FGS_ERR_ARG;
+    if (!c->has_tree) return fail(c, FGS_ERR_STATE, "no tree loaded");
+    DeviceGuard g(c->device);
+    const void* ptrs[] = {p->mu, p->log_scale, p->quat, p->logit, p->sh};
+    const char* names[] = {"mu", "log_scale", "quat", "logit", "sh"};
+    int r = check_param_ptrs(c, ptrs, names, 5);
+    if (r) return r;
+    c->have_frame = false;
+    const int blocks = (int)std::min<uint64_t>((c->tree.n + 255) / 256, (uint64_t)c->sms * 8);
+    launch_prep_params(c->tree, p->mu, p->log_scale, p->quat, p->logit, p->sh, std::max(blocks, 1),
+                       (cudaStream_t)stream);
+    FGS_CUDA(c, cudaGetLastError());
+    return FGS_OK;
+}
+
+int fgs_backward(fgs_ctx* c, void* stream, const float* dL_drgb, const fgs_gauss_params* p,
+                 const fgs_gauss_grads* gr, uint32_t flags)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!p || !gr) return fail(c, FGS_ERR_ARG, "null parameter or gradient struct");
+    if (!c->have_frame || !c->frame_is_render)
+        return fail(c, FGS_ERR_STATE, "no rendered frame to differentiate");
+    DeviceGuard g(c->device);
+    const void* ptrs[] = {dL_drgb, p->mu, p->log_scale, p->quat, p->logit, p->sh,
+                          gr->mu, gr->log_scale, gr->quat, gr->logit, gr->sh};
+    const char* names[] = {"dL_drgb", "mu", "log_scale", "quat", "logit", "sh",
+                           "grad mu", "grad log_scale", "grad quat", "grad logit", "grad sh"};
+    if ((r = check_param_ptrs(c, ptrs, names, 11))) return r;
+    if (c->gsplat_rows < c->tree.n) {
+        if ((r = grow(c, (void**)&c->gsplat, (size_t)c->tree.n * 12 * sizeof(float)))) return r;
+        c->gsplat_rows = c->tree.n;
+    }
+    const DevCamera dc = make_devcam(c, false);
+    cudaStream_t s = (cudaStream_t)stream;
+    const float* params[5] = {p->mu, p->log_scale, p->quat, p->logit, p->sh};
+    float* grads[5] = {gr->mu, gr->log_scale, gr->quat, gr->logit, gr->sh};
+    launch_backward(c->tree, dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, c->sel, dL_drgb,
+                    c->gsplat, params, grads, (flags & FGS_BACKWARD_ACCUMULATE) != 0, c->sms * 8, c->st, s);
+    FGS_CUDA(c, cudaGetLastError());
+    return FGS_OK;
 }
 
 // ---------------------------------------------------------------------------

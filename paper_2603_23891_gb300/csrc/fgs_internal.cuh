@@ -348,6 +348,12 @@ void launch_batch_front(const DevTree& t, const DevCamera* cams, int V, uint32_t
 void launch_batch_blend(const DevCamera* cams, int V, uint32_t total_tiles, const uint32_t* tile_base,
                         const unsigned long long* img_off, const uint2* ranges, const uint32_t* vals,
                         const float* splat, float* rgb, float* T, FrameState* st, cudaStream_t s);
+void launch_prep_params(const DevTree& t, const float* mu, const float* log_scale, const float* quat,
+                        const float* logit, const float* sh, int blocks, cudaStream_t s);
+void launch_backward(const DevTree& t, const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
+                     const float* splat, const uint32_t* sel, const float* dL_drgb, float* gsplat,
+                     const float* const params[5], float* const grads[5], bool accumulate, int proj_blocks,
+                     FrameState* st, cudaStream_t s);
 void launch_levelwise_step(const DevTree& t, const DevCamera& cam, const uint32_t* child_start,
                            const uint32_t* children, const uint32_t* frontier, uint32_t n_front,
                            uint32_t* next, uint32_t* n_next, uint32_t* selbits, cudaStream_t s);

@@ -39,7 +39,11 @@ EXPORTED = ["fgs_version", "fgs_create", "fgs_destroy", "fgs_last_error", "fgs_s
             "fgs_stage_times", "fgs_stage_count", "fgs_get_pairs", "fgs_get_splats",
             "fgs_calibrate_view", "fgs_calibrate_gtc", "fgs_sync", "fgs_validate_tree",
             "fgs_eval_exp", "fgs_compact_selection_noalloc", "fgs_filter_levelwise",
-            "fgs_batch_setup", "fgs_batch_set_cameras", "fgs_batch_image_offsets", "fgs_render_batch"]
+            "fgs_batch_setup", "fgs_batch_set_cameras", "fgs_batch_image_offsets", "fgs_render_batch",
+            "fgs_update_params", "fgs_backward"]
+
+FGS_BACKWARD_ACCUMULATE = 1
+GRAD_FIELDS = ("mu", "log_scale", "quat", "logit", "sh")
 
 
 class FgsError(RuntimeError):
@@ -66,6 +70,14 @@ class fgs_params(C.Structure):
     _fields_ = [("tau_R", C.c_float), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
                 ("bg", C.c_float * 3), ("pair_capacity", C.c_uint64), ("blend_warp_w", C.c_int32),
                 ("reserved", C.c_int32)]
+
+
+class fgs_gauss_params(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("mu", "log_scale", "quat", "logit", "sh")]
+
+
+class fgs_gauss_grads(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("mu", "log_scale", "quat", "logit", "sh")]
 
 
 class fgs_stats(C.Structure):
@@ -113,6 +125,9 @@ def lib():
         "fgs_batch_set_cameras": ([vp, vp, i32], i32),
         "fgs_batch_image_offsets": ([vp, vp], i32),
         "fgs_render_batch": ([vp, vp, vp, vp, u32, C.POINTER(fgs_stats)], i32),
+        "fgs_update_params": ([vp, vp, C.POINTER(fgs_gauss_params)], i32),
+        "fgs_backward": ([vp, vp, vp, C.POINTER(fgs_gauss_params), C.POINTER(fgs_gauss_grads), u32],
+                         i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -335,6 +350,23 @@ def fgs_sync(ctx, stream):
     return _check(ctx, lib().fgs_sync(ctx, stream))
 
 
+def _gauss_struct(cls, arrays):
+    return cls(*[_ptr(arrays[k]).value for k in GRAD_FIELDS])
+
+
+def fgs_update_params(ctx, stream, params: dict):
+    """params: device arrays keyed by GRAD_FIELDS (mu [3][n], log_scale [3][n],
+    quat [4][n], logit [n], sh [n][K][3])."""
+    p = _gauss_struct(fgs_gauss_params, params)
+    _check(ctx, lib().fgs_update_params(ctx, stream, C.byref(p)))
+
+
+def fgs_backward(ctx, stream, dL_drgb, params: dict, grads: dict, flags: int = 0):
+    p = _gauss_struct(fgs_gauss_params, params)
+    g = _gauss_struct(fgs_gauss_grads, grads)
+    _check(ctx, lib().fgs_backward(ctx, stream, _ptr(dL_drgb), C.byref(p), C.byref(g), flags))
+
+
 # ---------------------------------------------------------------- convenience
 
 def _torch():
@@ -529,6 +561,27 @@ class Renderer:
         timed(choice)
         return choice, best
 
+    # ------------------------------------------------------------ differentiable form
+    def update_params(self, params: dict):
+        """Recompute the loaded tree's attributes from torch CUDA parameter tensors
+        (keys GRAD_FIELDS, float32, contiguous)."""
+        for k in GRAD_FIELDS:
+            t = params[k]
+            if not (t.is_cuda and t.is_contiguous() and t.dtype == _torch().float32):
+                raise ValueError(f"{k}: expected a contiguous float32 CUDA tensor")
+        fgs_update_params(self.ctx, self.stream, params)
+
+    def backward(self, dL_drgb, params: dict, grads: dict = None, accumulate: bool = False):
+        """Gradients of sum(dL_drgb * rgb) for the last render (torch tensors, same
+        shapes as params).  Returns the gradient dict."""
+        torch = _torch()
+        if grads is None:
+            grads = {k: torch.empty_like(params[k]) for k in GRAD_FIELDS}
+        dL = dL_drgb.contiguous()
+        fgs_backward(self.ctx, self.stream, dL, params, grads,
+                     FGS_BACKWARD_ACCUMULATE if accumulate else 0)
+        return grads
+
     def render_batch(self, rgb=None, T=None, graph=False, stats=False):
         """All views at once; returns (rgb, T, stats, views) where views[v] = (rgb_v, T_v)."""
         torch = _torch()
@@ -547,3 +600,45 @@ class Renderer:
             views.append((rgb[3 * o: 3 * o + 3 * n].view(3, cam.height, cam.width),
                           T[o: o + n].view(cam.height, cam.width)))
         return rgb, T, st, views
+
+
+# ---------------------------------------------------------------- autograd
+def _make_render_function():
+    torch = _torch()
+
+    class FilterGSRender(torch.autograd.Function):
+        """rgb [3][H][W] = render(renderer's tree structure and camera; parameters).
+
+        The cut, the pairs and the blending decisions of the forward are held
+        fixed for the backward (hand-written kernels through fgs_backward)."""
+
+        @staticmethod
+        def forward(ctx, renderer, mu, log_scale, quat, logit, sh):
+            params = {k: v.detach().contiguous() for k, v in
+                      zip(GRAD_FIELDS, (mu, log_scale, quat, logit, sh))}
+            renderer.update_params(params)
+            rgb, _, _ = renderer.render()
+            ctx.renderer = renderer
+            ctx.params = params
+            return rgb
+
+        @staticmethod
+        def backward(ctx, grad_rgb):
+            g = ctx.renderer.backward(grad_rgb, ctx.params)
+            return (None,) + tuple(g[k] for k in GRAD_FIELDS)
+
+    return FilterGSRender
+
+
+_render_fn = None
+
+
+def render_differentiable(renderer: "Renderer", mu, log_scale, quat, logit, sh):
+    """Differentiable render of the renderer's current camera (torch autograd).
+
+    The backward must run before the renderer renders again: it differentiates
+    the frame held in the renderer."""
+    global _render_fn
+    if _render_fn is None:
+        _render_fn = _make_render_function()
+    return _render_fn.apply(renderer, mu, log_scale, quat, logit, sh)
