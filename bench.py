@@ -216,6 +216,63 @@ def run_batched(r, torch, filtergs, args):
 
 # ----------------------------------------------------------------------------- ours
 
+def run_backward(r, torch, filtergs, tree, cams, poses, args):
+    """Differentiable form on the workload: parameters -> attributes, render,
+    then the hand-written backward for dL/drgb ~ N(0, 1).  Times the render and
+    the backward per pose (CUDA events, L2 flushed between), in overwrite mode
+    (every node's gradient written: zeros outside the cut) and in accumulate
+    mode (only the cut's gradients added)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    P = {"mu": tree.mu, "log_scale": tree.log_scale, "quat": tree.quat,
+         "logit": tree.opacity_logit, "sh": tree.sh}
+    P = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).to(dev) for k, v in P.items()}
+    G = {k: torch.empty_like(v) for k, v in P.items()}
+    W, H = cams[0].width, cams[0].height
+    dL = torch.randn((3, H, W), generator=torch.Generator(device=dev).manual_seed(0), device=dev)
+    rgb = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    r.update_params(P)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    prep_ms = t0.elapsed_time(t1)
+    poses = poses[: min(16, len(poses))]
+    out = {}
+    for mode, acc in (("overwrite", False), ("accumulate", True)):
+        for w in range(3):
+            r.set_camera(cams[poses[w % len(poses)]])
+            r.render(rgb, keep=True)
+            r.backward(dL, P, G, accumulate=acc)
+        torch.cuda.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in poses]
+        for i, k in enumerate(poses):
+            flush.zero_()
+            r.set_camera(cams[k])
+            ev[i][0].record(stream)
+            r.render(rgb, keep=True)
+            ev[i][1].record(stream)
+            r.backward(dL, P, G, accumulate=acc)
+            ev[i][2].record(stream)
+        torch.cuda.synchronize()
+        fwd = [e[0].elapsed_time(e[1]) for e in ev]
+        bwd = [e[1].elapsed_time(e[2]) for e in ev]
+        out[mode] = {"forward_ms": round(float(np.mean(fwd)), 4),
+                     "backward_ms": round(float(np.mean(bwd)), 4)}
+    n = tree.n
+    K3 = (tree.sh_degree + 1) ** 2 * 3
+    return {"poses": len(poses), "params_per_node": 11 + K3, "nodes": n,
+            "prep_params_ms": round(prep_ms, 4),
+            "overwrite": out["overwrite"], "accumulate": out["accumulate"],
+            "ms_per_frame": out["accumulate"]["backward_ms"],
+            "grad_zeroing_bytes": 4 * (11 + K3) * n,
+            "how": "CUDA events around fgs_render and fgs_backward per pose; dL/drgb ~ N(0,1); "
+                   "overwrite mode also writes zeros for every node outside the cut"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -362,6 +419,13 @@ def run_ours(args):
     if args.batch and args.workload == "city":
         batched = run_batched(r, torch, filtergs, args)
 
+    # last: it replaces the tree's attributes by the binary32 parameter map
+    backward = None
+    if args.backward:
+        r.set_params(tau_R=tau_R, tile=(16, 16), blend_warp_w=8, pair_capacity=args.pair_capacity)
+        r.shrink(tau, ln_tau)
+        backward = run_backward(r, torch, filtergs, tree, cams, my_poses, args)
+
     frames = K * world
     fps = frames / (total_ms / 1e3)
     result = None
@@ -432,6 +496,7 @@ def run_ours(args):
             "clocks": clk,
             "calibration_s": round(calib_s, 3),
             "batched": batched,
+            "backward": backward,
             "wall_s_timed": round(wall, 4),
         }
     r.close()
@@ -534,6 +599,7 @@ def main():
     ap.add_argument("--pair-capacity", type=int, default=64 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--no-backward", dest="backward", action="store_false")
     ap.add_argument("--batch-reps", type=int, default=5)
     ap.add_argument("--batch-sel-cap", type=int, default=96 << 20)
     ap.add_argument("--batch-pair-cap", type=int, default=256 << 20)

@@ -88,6 +88,7 @@ struct fgs_ctx {
     // image staging for host outputs: rgb planes + T
     size_t img_cap = 0;
     float* img = nullptr;
+    uint2* keep = nullptr;          // per pixel: final T bits, stop position (for the backward)
     // frame state
     FrameState* st = nullptr;
     FrameState* st_host = nullptr;
@@ -100,7 +101,7 @@ struct fgs_ctx {
     size_t gsplat_rows = 0;
     // last frame
     bool have_frame = false;
-    bool frame_is_render = false;   // the last frame came from fgs_render (not a calibration)
+    bool frame_kept = false;        // the last frame came from fgs_render with FGS_RENDER_KEEP
     bool sorted_in_1 = false;
     // batched multi-view state
     struct Batch {
@@ -213,6 +214,7 @@ int ensure_tiles(fgs_ctx* c, size_t tiles, size_t pixels)
     }
     if (pixels > c->img_cap) {
         if ((r = grow(c, (void**)&c->img, pixels * 4 * 4))) return r;
+        if ((r = grow(c, (void**)&c->keep, pixels * sizeof(uint2)))) return r;
         c->img_cap = pixels;
     }
     return FGS_OK;
@@ -420,7 +422,7 @@ int fgs_destroy(fgs_ctx* c)
     void* bufs[] = {c->child_start, c->children, c->frontier0, c->frontier1, c->d_counter,
                     c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->foot, c->tile_total,
                     c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->lb_sort, c->ranges,
-                    c->G, c->img, c->st, c->gsplat};
+                    c->G, c->img, c->keep, c->st, c->gsplat};
     for (void* p : bufs) free_ptr(p);
     {
         auto& b = c->batch;
@@ -787,14 +789,15 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
     float* rgb_dst = out_is_device ? rgb_out : c->img;
     float* T_dst = out_is_device ? T_out : (T_out ? c->img + 3 * hw : nullptr);
     const bool count = (flags & FGS_RENDER_COUNT) != 0;
+    const bool keep = (flags & FGS_RENDER_KEEP) && !count;
     if (count) flags |= FGS_RENDER_STATS;
-    launch_blend(dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, rgb_dst, T_dst, c->st,
-                 count, s);
+    launch_blend(dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, rgb_dst, T_dst,
+                 keep ? c->keep : nullptr, c->st, count, s);
     ++launches;
     if (ev) cudaEventRecord(ev[6], s);
     FGS_CUDA(c, cudaGetLastError());
     c->have_frame = true;
-    c->frame_is_render = true;
+    c->frame_kept = keep;
     if (!out_is_device) {
         FGS_CUDA(c, cudaMemcpyAsync(rgb_out, c->img, 3 * hw * 4, cudaMemcpyDeviceToHost, s));
         if (T_out) FGS_CUDA(c, cudaMemcpyAsync(T_out, c->img + 3 * hw, hw * 4, cudaMemcpyDeviceToHost, s));
@@ -899,7 +902,7 @@ int fgs_calibrate_view(fgs_ctx* c, void* stream, double* gbar_out, float* kpc_ou
                      c->st, s);
     FGS_CUDA(c, cudaGetLastError());
     c->have_frame = true;
-    c->frame_is_render = false;
+    c->frame_kept = false;
     if ((r = read_state(c, s))) return r;
     if ((r = latched_status(c))) {
         clear_status(c, s);
@@ -1009,8 +1012,8 @@ int fgs_backward(fgs_ctx* c, void* stream, const float* dL_drgb, const fgs_gauss
     int r = check_ready(c);
     if (r) return r;
     if (!p || !gr) return fail(c, FGS_ERR_ARG, "null parameter or gradient struct");
-    if (!c->have_frame || !c->frame_is_render)
-        return fail(c, FGS_ERR_STATE, "no rendered frame to differentiate");
+    if (!c->have_frame || !c->frame_kept)
+        return fail(c, FGS_ERR_STATE, "no frame rendered with FGS_RENDER_KEEP to differentiate");
     DeviceGuard g(c->device);
     const void* ptrs[] = {dL_drgb, p->mu, p->log_scale, p->quat, p->logit, p->sh,
                           gr->mu, gr->log_scale, gr->quat, gr->logit, gr->sh};
@@ -1025,8 +1028,9 @@ int fgs_backward(fgs_ctx* c, void* stream, const float* dL_drgb, const fgs_gauss
     cudaStream_t s = (cudaStream_t)stream;
     const float* params[5] = {p->mu, p->log_scale, p->quat, p->logit, p->sh};
     float* grads[5] = {gr->mu, gr->log_scale, gr->quat, gr->logit, gr->sh};
-    launch_backward(c->tree, dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, c->sel, dL_drgb,
-                    c->gsplat, params, grads, (flags & FGS_BACKWARD_ACCUMULATE) != 0, c->sms * 8, c->st, s);
+    launch_backward(c->tree, dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, c->keep, c->sel,
+                    dL_drgb, c->gsplat, params, grads, (flags & FGS_BACKWARD_ACCUMULATE) != 0, c->sms, c->st,
+                    s);
     FGS_CUDA(c, cudaGetLastError());
     return FGS_OK;
 }

@@ -6,12 +6,14 @@
 // mean mu, log-scale s, quaternion q (any norm), opacity logit l, SH
 // coefficients; Sigma = R(q/|q|) diag(e^{2s}) R^T, alpha0 = sigmoid(l).
 //
-// blend_bwd_kernel recomputes transmittance instead of storing it: per tile,
-// a forward re-walk finds each pixel's final T and where it stopped, then a
-// back-to-front walk recovers T before each Gaussian as T / (1 - alpha) and
-// accumulates the colour behind it.  Gradients with respect to the splat
-// record (u, v, conic A B C, alpha0, colour) are reduced per warp and added
-// per Gaussian; project_bwd_kernel applies the chain rule to the parameters.
+// The forward blend keeps, per pixel, its final transmittance and the sorted
+// position where it stopped (8 bytes).  blend_bwd_kernel walks each tile back
+// to front from there, recovering T before each Gaussian as T / (1 - alpha)
+// and accumulating the colour behind it; chunks past the last stop of the
+// tile are never loaded.  Gradients with respect to the splat record (u, v,
+// conic A B C, alpha0, colour) are reduced per warp (a transposed reduction:
+// 12 shuffles for 9 values) and added per Gaussian; project_bwd_kernel then
+// applies the chain rule to the parameters.
 #include "blend_impl.cuh"
 #include "project_impl.cuh"
 
@@ -102,9 +104,7 @@ __global__ void __launch_bounds__(256) prep_params_kernel(DevTree t, ParamPtrs p
     float* cov = const_cast<float*>(t.cov);
     float* op = const_cast<float*>(t.opacity);
     float* lop = const_cast<float*>(t.ln_opacity);
-    float* sh = const_cast<float*>(t.sh);
     const size_t np = t.n_pad, N = p.n;
-    const int K3 = (int)((t.sh_degree + 1) * (t.sh_degree + 1) * 3);
     for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < p.n; n += gridDim.x * blockDim.x) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) mu[k * np + n] = p.mu[k * N + n];
@@ -115,7 +115,22 @@ __global__ void __launch_bounds__(256) prep_params_kernel(DevTree t, ParamPtrs p
         const float den = fa(1.0f, exp_cw(-clamp_logit(p.logit[n])));
         op[n] = fd(1.0f, den);
         lop[n] = -ln_cw(den);
-        for (int k = 0; k < K3; ++k) sh[(size_t)n * t.sh_stride + k] = p.sh[(size_t)n * K3 + k];
+    }
+}
+
+// SH coefficients [n][K3] -> the tree's rows of sh_stride floats, one flat
+// coalesced pass over the source (K3 a compile-time constant: the division is
+// a multiply).
+template <int kDeg>
+__global__ void __launch_bounds__(256) prep_sh_kernel(DevTree t, const float* __restrict__ src)
+{
+    constexpr uint64_t K3 = (kDeg + 1) * (kDeg + 1) * 3;
+    float* sh = const_cast<float*>(t.sh);
+    const uint64_t total = (uint64_t)t.n * K3;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t n = i / K3;
+        sh[n * t.sh_stride + (i - n * K3)] = __ldg(src + i);
     }
 }
 
@@ -125,18 +140,53 @@ __global__ void __launch_bounds__(256) prep_params_kernel(DevTree t, ParamPtrs p
 struct BwdSmem {
     blendk::BlendSmem<false> S;
     uint32_t m[256];
+    uint32_t lim[8];
 };
 
-__device__ __forceinline__ float warp_sumf(float v)
+// Sum over the warp of v[0..8], scattered: on return the lane given by
+// lane_component() holds the warp sum of its component.  Recursive halving
+// (xor 16, 8, 4, 2 split the value set, xor 1 completes the sums): 12
+// shuffles instead of 45 for nine butterfly reductions.
+__device__ __forceinline__ float warp_reduce9(const float v[9], uint32_t lane)
 {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float a[5];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int i = 0; i < 5; ++i) {
+        const float lo = v[i], hi = (5 + i < 9) ? v[5 + i] : 0.0f;
+        a[i] = (b4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b4 ? lo : hi, 16);
+    }
+    float b[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float lo = a[i], hi = (3 + i < 5) ? a[3 + i] : 0.0f;
+        b[i] = (b3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8);
+    }
+    float c[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float lo = b[i], hi = (2 + i < 3) ? b[2 + i] : 0.0f;
+        c[i] = (b2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
+    }
+    const float d = (b1 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b1 ? c[0] : c[1], 2);
+    return d + __shfl_xor_sync(0xffffffffu, d, 1);
+}
+
+// Component whose sum warp_reduce9 leaves in this lane (even lanes only; -1 for
+// lanes holding padding or the duplicate odd copy).
+__device__ __forceinline__ int lane_component(uint32_t lane)
+{
+    const int pc = (lane >> 1) & 1;
+    const int pb = 2 * ((lane >> 2) & 1) + pc;
+    const int pa = 3 * ((lane >> 3) & 1) + pb;
+    const int comp = 5 * ((lane >> 4) & 1) + pa;
+    return (!(lane & 1) && pb < 3 && pa < 5 && comp < 9) ? comp : -1;
 }
 
 __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uint2* __restrict__ ranges,
                                                         const uint32_t* __restrict__ vals,
                                                         const float* __restrict__ splat,
+                                                        const uint2* __restrict__ keep,
                                                         const float* __restrict__ dL_drgb,
                                                         float* __restrict__ gsplat, FrameState* st)
 {
@@ -154,19 +204,44 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
     const float px = fa((float)x, 0.5f), py = fa((float)y, 0.5f);
     const uint2 rg = ranges[tile];
     const uint32_t M = st->M;
-    const uint32_t s = rg.x, e = rg.y;
+    const uint32_t s = rg.x;
+    const int comp = lane_component(lane);
+
+    // this pixel's forward outcome: final T, stop position, and dL/dC
+    float T = 1.0f;
+    uint32_t lim = s;
+    float dC[3] = {0.0f, 0.0f, 0.0f};
+    if (inside) {
+        const size_t hw = (size_t)cam.width * cam.height, pix = (size_t)y * cam.width + x;
+        const uint2 kp = keep[pix];
+        T = __uint_as_float(kp.x);
+        lim = kp.y;
+        dC[0] = __ldg(dL_drgb + pix);
+        dC[1] = __ldg(dL_drgb + hw + pix);
+        dC[2] = __ldg(dL_drgb + 2 * hw + pix);
+    }
+    const uint32_t wlim = __reduce_max_sync(0xffffffffu, lim);
+    if (lane == 0) B.lim[warp] = wlim;
     if (tid == 0) {
         blendk::mbar_init(&S.bar, 1);
         S.timed_out = 0;
     }
     __syncthreads();
+    uint32_t e = B.lim[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) e = max(e, B.lim[w]);
+    e = min(e, rg.y);                    // no pixel of the tile reaches past e
     uint32_t phase = 0;
 
-    // load a chunk: values, splat records, culling masks, this warp's list
-    auto load_chunk = [&](uint32_t s0, uint32_t e0, uint32_t& wcnt) -> bool {
+    float Bk[3] = {cam.bg[0] * T, cam.bg[1] * T, cam.bg[2] * T};   // colour behind, absolute
+    float Tc = T;                                                    // transmittance after
+    if (e <= s) return;
+    const uint32_t n_chunks = (e - s + blendk::kChunk - 1) / blendk::kChunk;
+    for (int c = (int)n_chunks - 1; c >= 0; --c) {
+        const uint32_t s0 = s + (uint32_t)c * blendk::kChunk, e0 = min(e, s0 + blendk::kChunk);
         const uint32_t cnt = e0 - s0;
         const uint32_t off = blendk::stage_vals(S.vals, &S.bar, &S.timed_out, vals, s0, e0, phase, st);
-        if (S.timed_out) return false;
+        if (S.timed_out) return;
         if (tid < cnt) {
             uint32_t m = S.vals[off + tid];
             if (m >= M) m = 0;
@@ -179,115 +254,63 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
             B.m[tid] = m;
         }
         __syncthreads();
-        wcnt = 0;
+        // this warp's ordered list of the chunk entries before its last stop
+        uint32_t wcnt = 0;
         for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
             const uint32_t j = j0 + lane;
-            const bool mine = j < cnt && ((S.wmask[j] >> warp) & 1u);
+            const bool mine = j < cnt && s0 + j < wlim && ((S.wmask[j] >> warp) & 1u);
             const uint32_t bb = __ballot_sync(0xffffffffu, mine);
             if (mine) S.wlist[warp][wcnt + __popc(bb & ((1u << lane) - 1u))] = (uint16_t)j;
             wcnt += __popc(bb);
         }
         __syncwarp();
-        return true;
-    };
-
-    // ---- phase 1: forward re-walk (same decisions as the forward) -> final T, stop position
-    float T = 1.0f;
-    bool done = !inside;
-    uint32_t lim = inside ? e : s;
-    for (uint32_t s0 = s; s0 < e; s0 += 256) {
-        const uint32_t e0 = min(e, s0 + 256);
-        uint32_t wcnt;
-        if (!load_chunk(s0, e0, wcnt)) return;
-        for (uint32_t i = 0; i < wcnt && !__all_sync(0xffffffffu, done); ++i) {
+        for (int i = (int)wcnt - 1; i >= 0; --i) {
             const uint32_t j = S.wlist[warp][i];
-            if (done) continue;
-            const float4 g0 = S.g0[j];
-            const float4 g1 = S.g1[j];
-            const float dx = fs(g0.x, px), dy = fs(g0.y, py);
-            const float power = fs(fm(-0.5f, fa(fm(fm(g0.z, dx), dx), fm(fm(g1.x, dy), dy))),
-                                   fm(fm(g0.w, dx), dy));
-            if (power > 0.0f || power < g1.y) continue;
-            float alpha = fm(g1.z, exp_cw(power));
-            alpha = alpha < 0.99f ? alpha : 0.99f;
-            const float Tn = fm(T, fs(1.0f, alpha));
-            if (Tn < 0.0001f) {
-                done = true;
-                lim = s0 + j;
-                continue;
+            float g[9] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            bool any = false;
+            if (s0 + j < lim) {
+                const float4 g0 = S.g0[j];
+                const float4 g1 = S.g1[j];
+                const float dx = fs(g0.x, px), dy = fs(g0.y, py);
+                const float power = fs(fm(-0.5f, fa(fm(fm(g0.z, dx), dx), fm(fm(g1.x, dy), dy))),
+                                       fm(fm(g0.w, dx), dy));
+                if (!(power > 0.0f || power < g1.y)) {
+                    const float ex = exp_cw(power);
+                    const float raw = fm(g1.z, ex);
+                    const bool clamped = !(raw < 0.99f);
+                    const float alpha = clamped ? 0.99f : raw;
+                    const float4 g2 = S.g2[j];
+                    const float iom = __frcp_rn(1.0f - alpha);     // decides nothing
+                    const float Tb = Tc * iom;                      // transmittance before
+                    const float w = alpha * Tb;
+                    const float galpha = dC[0] * (g2.x * Tb - Bk[0] * iom) +
+                                         dC[1] * (g2.y * Tb - Bk[1] * iom) +
+                                         dC[2] * (g2.z * Tb - Bk[2] * iom);
+                    Bk[0] += g2.x * w;
+                    Bk[1] += g2.y * w;
+                    Bk[2] += g2.z * w;
+                    g[6] = w * dC[0];
+                    g[7] = w * dC[1];
+                    g[8] = w * dC[2];
+                    Tc = Tb;
+                    if (!clamped) {
+                        const float gpow = galpha * alpha;         // d alpha / d power = alpha
+                        g[5] = galpha * ex;                        // d alpha / d alpha0 = e^power
+                        g[2] = -0.5f * dx * dx * gpow;             // A
+                        g[3] = -dx * dy * gpow;                    // B
+                        g[4] = -0.5f * dy * dy * gpow;             // C
+                        g[0] = -gpow * (g0.z * dx + g0.w * dy);    // u
+                        g[1] = -gpow * (g1.x * dy + g0.w * dx);    // v
+                    }
+                    any = true;
+                }
             }
-            T = Tn;
+            if (__any_sync(0xffffffffu, any)) {
+                const float v = warp_reduce9(g, lane);
+                if (comp >= 0) atomicAdd(gsplat + (size_t)B.m[j] * kGS + comp, v);
+            }
         }
         __syncthreads();
-    }
-    // ---- phase 2: back-to-front
-    float dC[3] = {0.0f, 0.0f, 0.0f};
-    if (inside) {
-        const size_t hw = (size_t)cam.width * cam.height, pix = (size_t)y * cam.width + x;
-        dC[0] = __ldg(dL_drgb + pix);
-        dC[1] = __ldg(dL_drgb + hw + pix);
-        dC[2] = __ldg(dL_drgb + 2 * hw + pix);
-    }
-    float Bk[3] = {cam.bg[0] * T, cam.bg[1] * T, cam.bg[2] * T};   // colour behind, absolute
-    float Tc = T;                                                    // transmittance after
-    if (e > s) {
-        const uint32_t n_chunks = (e - s + 255) / 256;
-        for (int c = (int)n_chunks - 1; c >= 0; --c) {
-            const uint32_t s0 = s + (uint32_t)c * 256, e0 = min(e, s0 + 256);
-            uint32_t wcnt;
-            if (!load_chunk(s0, e0, wcnt)) return;
-            for (int i = (int)wcnt - 1; i >= 0; --i) {
-                const uint32_t j = S.wlist[warp][i];
-                float g[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-                bool any = false;
-                if (inside && s0 + j < lim) {
-                    const float4 g0 = S.g0[j];
-                    const float4 g1 = S.g1[j];
-                    const float dx = fs(g0.x, px), dy = fs(g0.y, py);
-                    const float power = fs(fm(-0.5f, fa(fm(fm(g0.z, dx), dx), fm(fm(g1.x, dy), dy))),
-                                           fm(fm(g0.w, dx), dy));
-                    if (!(power > 0.0f || power < g1.y)) {
-                        const float ex = exp_cw(power);
-                        const float raw = fm(g1.z, ex);
-                        const bool clamped = !(raw < 0.99f);
-                        const float alpha = clamped ? 0.99f : raw;
-                        const float4 g2 = S.g2[j];
-                        const float om = 1.0f - alpha;
-                        const float Tb = Tc / om;                  // transmittance before
-                        const float col[3] = {g2.x, g2.y, g2.z};
-                        float galpha = 0.0f;
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) {
-                            galpha += dC[ch] * (col[ch] * Tb - Bk[ch] / om);
-                            Bk[ch] += col[ch] * alpha * Tb;
-                            g[6 + ch] = alpha * Tb * dC[ch];
-                        }
-                        Tc = Tb;
-                        if (!clamped) {
-                            const float gpow = galpha * alpha;     // d alpha / d power = alpha
-                            g[5] = galpha * ex;                    // d alpha / d alpha0 = e^power
-                            g[2] = -0.5f * dx * dx * gpow;         // A
-                            g[4] = -0.5f * dy * dy * gpow;         // C
-                            g[3] = -dx * dy * gpow;                // B
-                            g[0] = gpow * (-g0.z * dx - g0.w * dy);   // u
-                            g[1] = gpow * (-g1.x * dy - g0.w * dx);   // v
-                        }
-                        any = true;
-                    }
-                }
-                if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) g[k] = warp_sumf(g[k]);
-                    if (lane < 9) {
-                        float v = g[0];
-#pragma unroll
-                        for (int k = 1; k < 9; ++k) v = lane == (uint32_t)k ? g[k] : v;
-                        atomicAdd(gsplat + (size_t)B.m[j] * kGS + lane, v);
-                    }
-                }
-            }
-            __syncthreads();
-        }
     }
 }
 
@@ -296,37 +319,57 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
 // ---------------------------------------------------------------------------
 namespace {
 
-// d Y_k / d(x, y, z) of the real SH basis (Cartesian polynomials), k < 16.
-__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float Y[16],
-                                              float dY[16][3])
+// Real SH basis (Cartesian form, degree kDeg <= 3) and its partial derivatives
+// in (x, y, z), treating the three as independent.
+template <int kDeg>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float Y[16], float dY[16][3])
 {
     using namespace proj;
-    for (int k = 0; k < 16; ++k) { Y[k] = 0.0f; dY[k][0] = dY[k][1] = dY[k][2] = 0.0f; }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        Y[k] = 0.0f;
+        dY[k][0] = dY[k][1] = dY[k][2] = 0.0f;
+    }
     Y[0] = kY00;
-    if (deg < 1) return;
+    if (kDeg < 1) return;
     Y[1] = -kY1 * y; dY[1][1] = -kY1;
-    Y[2] = kY1 * z; dY[2][2] = kY1;
+    Y[2] = kY1 * z;  dY[2][2] = kY1;
     Y[3] = -kY1 * x; dY[3][0] = -kY1;
-    if (deg < 2) return;
+    if (kDeg < 2) return;
     const float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = kY2a * x * y; dY[4][0] = kY2a * y; dY[4][1] = kY2a * x;
-    Y[5] = -kY2a * y * z; dY[5][1] = -kY2a * z; dY[5][2] = -kY2a * y;
-    Y[6] = kY2b * (2.0f * zz - xx - yy); dY[6][0] = -2.0f * kY2b * x; dY[6][1] = -2.0f * kY2b * y;
+    Y[4] = kY2a * x * y;                 dY[4][0] = kY2a * y;           dY[4][1] = kY2a * x;
+    Y[5] = -kY2a * y * z;                dY[5][1] = -kY2a * z;          dY[5][2] = -kY2a * y;
+    Y[6] = kY2b * (2.0f * zz - xx - yy); dY[6][0] = -2.0f * kY2b * x;   dY[6][1] = -2.0f * kY2b * y;
     dY[6][2] = 4.0f * kY2b * z;
-    Y[7] = -kY2a * x * z; dY[7][0] = -kY2a * z; dY[7][2] = -kY2a * x;
-    Y[8] = kY2c * (xx - yy); dY[8][0] = 2.0f * kY2c * x; dY[8][1] = -2.0f * kY2c * y;
-    if (deg < 3) return;
-    Y[9] = -kY3a * y * (3.0f * xx - yy); dY[9][0] = -6.0f * kY3a * x * y; dY[9][1] = -kY3a * (3.0f * xx - 3.0f * yy);
-    Y[10] = kY3b * x * y * z; dY[10][0] = kY3b * y * z; dY[10][1] = kY3b * x * z; dY[10][2] = kY3b * x * y;
-    Y[11] = -kY3c * y * (4.0f * zz - xx - yy); dY[11][0] = 2.0f * kY3c * x * y;
-    dY[11][1] = -kY3c * (4.0f * zz - xx - 3.0f * yy); dY[11][2] = -8.0f * kY3c * y * z;
-    Y[12] = kY3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy); dY[12][0] = -6.0f * kY3d * x * z;
-    dY[12][1] = -6.0f * kY3d * y * z; dY[12][2] = kY3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
-    Y[13] = -kY3c * x * (4.0f * zz - xx - yy); dY[13][0] = -kY3c * (4.0f * zz - 3.0f * xx - yy);
-    dY[13][1] = 2.0f * kY3c * x * y; dY[13][2] = -8.0f * kY3c * x * z;
-    Y[14] = kY3e * z * (xx - yy); dY[14][0] = 2.0f * kY3e * x * z; dY[14][1] = -2.0f * kY3e * y * z;
+    Y[7] = -kY2a * x * z;                dY[7][0] = -kY2a * z;          dY[7][2] = -kY2a * x;
+    Y[8] = kY2c * (xx - yy);             dY[8][0] = 2.0f * kY2c * x;    dY[8][1] = -2.0f * kY2c * y;
+    if (kDeg < 3) return;
+    Y[9] = -kY3a * y * (3.0f * xx - yy);
+    dY[9][0] = -6.0f * kY3a * x * y;
+    dY[9][1] = -kY3a * (3.0f * xx - 3.0f * yy);
+    Y[10] = kY3b * x * y * z;
+    dY[10][0] = kY3b * y * z;
+    dY[10][1] = kY3b * x * z;
+    dY[10][2] = kY3b * x * y;
+    Y[11] = -kY3c * y * (4.0f * zz - xx - yy);
+    dY[11][0] = 2.0f * kY3c * x * y;
+    dY[11][1] = -kY3c * (4.0f * zz - xx - 3.0f * yy);
+    dY[11][2] = -8.0f * kY3c * y * z;
+    Y[12] = kY3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    dY[12][0] = -6.0f * kY3d * x * z;
+    dY[12][1] = -6.0f * kY3d * y * z;
+    dY[12][2] = kY3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -kY3c * x * (4.0f * zz - xx - yy);
+    dY[13][0] = -kY3c * (4.0f * zz - 3.0f * xx - yy);
+    dY[13][1] = 2.0f * kY3c * x * y;
+    dY[13][2] = -8.0f * kY3c * x * z;
+    Y[14] = kY3e * z * (xx - yy);
+    dY[14][0] = 2.0f * kY3e * x * z;
+    dY[14][1] = -2.0f * kY3e * y * z;
     dY[14][2] = kY3e * (xx - yy);
-    Y[15] = -kY3a * x * (xx - 3.0f * yy); dY[15][0] = -kY3a * (3.0f * xx - 3.0f * yy); dY[15][1] = 6.0f * kY3a * x * y;
+    Y[15] = -kY3a * x * (xx - 3.0f * yy);
+    dY[15][0] = -kY3a * (3.0f * xx - 3.0f * yy);
+    dY[15][1] = 6.0f * kY3a * x * y;
 }
 
 }  // namespace
@@ -342,20 +385,56 @@ struct GradPtrs {
 // Chain rule for selected Gaussian m (node sel[m]): splat gradient -> mean,
 // log-scale, quaternion, logit, SH.  Each node appears once in the selection,
 // so plain stores (or read-modify-writes when accumulating) need no atomics.
-template <bool kAccumulate>
-__global__ void __launch_bounds__(128) project_bwd_kernel(DevTree t, DevCamera cam, ParamPtrs p,
+//
+// Each warp takes 32 consecutive selected Gaussians per iteration, one per
+// lane.  Their SH rows (3 K floats each, contiguous per node) are staged in
+// shared memory with coalesced asynchronous copies, and the SH gradient rows
+// leave the same way; the row stride 3 K + 1 is odd, so lane l reading row l, element k hits
+// bank (l (3 K + 1) + k) mod 32, a different bank for every lane.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(blendk::smem_addr(smem)), "l"(gmem)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+constexpr int kPbWarps = 2;   // warps per projection-backward block
+
+template <int kDeg, bool kAccumulate>
+__global__ void __launch_bounds__(kPbWarps * 32, 16 / kPbWarps) project_bwd_kernel(DevTree t, DevCamera cam, ParamPtrs p,
                                                           const uint32_t* __restrict__ sel,
                                                           const float* __restrict__ gsplat,
                                                           GradPtrs gr, const FrameState* st)
 {
+    constexpr int K = (kDeg + 1) * (kDeg + 1);
+    constexpr int K3 = 3 * K, RS = K3 + 1;
+    __shared__ float s_rows[kPbWarps][32 * RS];
+    __shared__ float s_olds[kAccumulate ? kPbWarps : 1][kAccumulate ? 32 * RS : 1];
     const uint32_t M = st->M;
     const size_t N = p.n;
     const float* W = cam.R;
-    const int deg = (int)t.sh_degree;
-    const int K = (deg + 1) * (deg + 1);
-    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
-        const uint32_t n = sel[m];
-        const float* gs = gsplat + (size_t)m * kGS;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* rows = s_rows[warp];
+    float* olds = s_olds[kAccumulate ? warp : 0];
+    float* row = rows + lane * RS;
+    for (uint32_t base = (blockIdx.x * kPbWarps + warp) * 32; base < M; base += gridDim.x * kPbWarps * 32) {
+        const uint32_t m = base + lane;
+        const bool act = m < M;
+        const uint32_t n = act ? sel[m] : sel[base];
+        // stage the warp's SH rows (and, accumulating, their current gradient
+        // rows) with asynchronous copies: element i * 32 + lane of the 32 x K3
+        // block, all in flight at once, no registers held
+#pragma unroll
+        for (int i = 0; i < K3; ++i) {
+            const uint32_t idx = (uint32_t)i * 32u + lane, r = idx / K3, k = idx - r * K3;
+            const uint32_t nr = __shfl_sync(0xffffffffu, n, r);
+            cp_async4(rows + r * RS + k, p.sh + (size_t)nr * K3 + k);
+            if (kAccumulate && base + r < M) cp_async4(olds + r * RS + k, gr.sh + (size_t)nr * K3 + k);
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        const float* gs = gsplat + (size_t)(act ? m : base) * kGS;
         const float gu = gs[0], gv = gs[1], gA = gs[2], gB = gs[3], gC = gs[4], ga0 = gs[5];
         const float gcol[3] = {gs[6], gs[7], gs[8]};
         const float mu[3] = {p.mu[n], p.mu[N + n], p.mu[2 * N + n]};
@@ -455,24 +534,34 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(DevTree t, DevCamera c
 #pragma unroll
         for (int k = 0; k < 3; ++k) d[k] *= idl;
         float Y[16], dY[16][3];
-        sh_basis_grad(deg, d[0], d[1], d[2], Y, dY);
-        const float* shp = p.sh + (size_t)n * K * 3;
-        float* gsh = gr.sh + (size_t)n * K * 3;
+        sh_basis_grad<kDeg>(d[0], d[1], d[2], Y, dY);
         float gd[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             float pre = 0.5f;
-            for (int k = 0; k < K; ++k) pre += Y[k] * shp[3 * k + ch];
+#pragma unroll
+            for (int k = 0; k < K; ++k) pre += Y[k] * row[3 * k + ch];
             const float g = pre > 0.0f ? gcol[ch] : 0.0f;
+#pragma unroll
             for (int k = 0; k < K; ++k) {
-                const float v = Y[k] * g;
-                if (kAccumulate) gsh[3 * k + ch] += v;
-                else gsh[3 * k + ch] = v;
-                const float cf = shp[3 * k + ch] * g;
-                gd[0] += cf * dY[k][0];
-                gd[1] += cf * dY[k][1];
-                gd[2] += cf * dY[k][2];
+                const float cg = row[3 * k + ch] * g;
+                gd[0] += cg * dY[k][0];
+                gd[1] += cg * dY[k][1];
+                gd[2] += cg * dY[k][2];
+                row[3 * k + ch] = Y[k] * g;      // the row now holds the SH gradient
             }
         }
+        __syncwarp();
+        // SH gradient rows out, coalesced
+#pragma unroll
+        for (int i = 0; i < K3; ++i) {
+            const uint32_t idx = (uint32_t)i * 32u + lane, r = idx / K3, k = idx - r * K3;
+            const uint32_t nr = __shfl_sync(0xffffffffu, n, r);
+            const float g = rows[r * RS + k] + (kAccumulate ? olds[r * RS + k] : 0.0f);
+            if (base + r < M) gr.sh[(size_t)nr * K3 + k] = g;
+        }
+        __syncwarp();
+        if (!act) continue;
         const float dd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
 #pragma unroll
         for (int k = 0; k < 3; ++k) gmu[k] += (gd[k] - d[k] * dd) * idl;
@@ -480,14 +569,25 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(DevTree t, DevCamera c
 #pragma unroll
         for (int k = 0; k < 4; ++k) gqn[k] = (gq[k] - qh[k] * dotq) / qn;
         if (kAccumulate) {
+            // all eleven loads before the first store (the arrays may alias as far
+            // as the compiler knows)
+            float o_mu[3], o_ls[3], o_q[4];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                gr.mu[k * N + n] += gmu[k];
-                gr.log_scale[k * N + n] += gls[k];
+                o_mu[k] = gr.mu[k * N + n];
+                o_ls[k] = gr.log_scale[k * N + n];
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) gr.quat[k * N + n] += gqn[k];
-            gr.logit[n] += glogit;
+            for (int k = 0; k < 4; ++k) o_q[k] = gr.quat[k * N + n];
+            const float o_l = gr.logit[n];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gr.mu[k * N + n] = o_mu[k] + gmu[k];
+                gr.log_scale[k * N + n] = o_ls[k] + gls[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gr.quat[k * N + n] = o_q[k] + gqn[k];
+            gr.logit[n] = o_l + glogit;
         } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -516,16 +616,34 @@ void launch_prep_params(const DevTree& t, const float* mu, const float* log_scal
 {
     ParamPtrs p{mu, log_scale, quat, logit, sh, t.n};
     prep_params_kernel<<<blocks, 256, 0, s>>>(t, p);
+    switch (t.sh_degree) {
+    case 0: prep_sh_kernel<0><<<blocks, 256, 0, s>>>(t, sh); break;
+    case 1: prep_sh_kernel<1><<<blocks, 256, 0, s>>>(t, sh); break;
+    case 2: prep_sh_kernel<2><<<blocks, 256, 0, s>>>(t, sh); break;
+    default: prep_sh_kernel<3><<<blocks, 256, 0, s>>>(t, sh); break;
+    }
+}
+
+template <int kDeg>
+static void launch_project_bwd(const DevTree& t, const DevCamera& cam, const ParamPtrs& p,
+                               const uint32_t* sel, const float* gsplat, const GradPtrs& gr,
+                               bool accumulate, int blocks, FrameState* st, cudaStream_t s)
+{
+    if (accumulate)
+        project_bwd_kernel<kDeg, true><<<blocks, kPbWarps * 32, 0, s>>>(t, cam, p, sel, gsplat, gr, st);
+    else
+        project_bwd_kernel<kDeg, false><<<blocks, kPbWarps * 32, 0, s>>>(t, cam, p, sel, gsplat, gr, st);
 }
 
 void launch_backward(const DevTree& t, const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
-                     const float* splat, const uint32_t* sel, const float* dL_drgb, float* gsplat,
-                     const float* const params[5], float* const grads[5], bool accumulate, int proj_blocks,
-                     FrameState* st, cudaStream_t s)
+                     const float* splat, const uint2* keep, const uint32_t* sel, const float* dL_drgb,
+                     float* gsplat, const float* const params[5], float* const grads[5], bool accumulate,
+                     int sms, FrameState* st, cudaStream_t s)
 {
     // gsplat rows of the selected Gaussians start at zero: the blend backward adds into them
-    zero_rows_kernel<<<proj_blocks, 128, 0, s>>>(reinterpret_cast<float4*>(gsplat), st);
-    blend_bwd_kernel<<<cam.tiles_x * cam.tiles_y, 256, 0, s>>>(cam, ranges, vals, splat, dL_drgb, gsplat, st);
+    zero_rows_kernel<<<sms * 8, 128, 0, s>>>(reinterpret_cast<float4*>(gsplat), st);
+    blend_bwd_kernel<<<cam.tiles_x * cam.tiles_y, 256, 0, s>>>(cam, ranges, vals, splat, keep, dL_drgb,
+                                                               gsplat, st);
     const ParamPtrs p{params[0], params[1], params[2], params[3], params[4], t.n};
     const GradPtrs gr{grads[0], grads[1], grads[2], grads[3], grads[4]};
     if (!accumulate) {
@@ -536,9 +654,13 @@ void launch_backward(const DevTree& t, const DevCamera& cam, const uint2* ranges
         cudaMemsetAsync(gr.quat, 0, sizeof(float) * 4 * t.n, s);
         cudaMemsetAsync(gr.logit, 0, sizeof(float) * t.n, s);
         cudaMemsetAsync(gr.sh, 0, sizeof(float) * K3 * t.n, s);
-        project_bwd_kernel<false><<<proj_blocks, 128, 0, s>>>(t, cam, p, sel, gsplat, gr, st);
-    } else {
-        project_bwd_kernel<true><<<proj_blocks, 128, 0, s>>>(t, cam, p, sel, gsplat, gr, st);
+    }
+    const int blocks = sms * (16 / kPbWarps);
+    switch (t.sh_degree) {
+    case 0: launch_project_bwd<0>(t, cam, p, sel, gsplat, gr, accumulate, blocks, st, s); break;
+    case 1: launch_project_bwd<1>(t, cam, p, sel, gsplat, gr, accumulate, blocks, st, s); break;
+    case 2: launch_project_bwd<2>(t, cam, p, sel, gsplat, gr, accumulate, blocks, st, s); break;
+    default: launch_project_bwd<3>(t, cam, p, sel, gsplat, gr, accumulate, blocks, st, s); break;
     }
 }
 

@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256) bblend_kernel(const DevCamera* __restrict
     __syncthreads();
     const unsigned long long o = __ldg(img_off + v);
     blendk::blend_tile<false>(s_cam, gtile - __ldg(tile_base + v), gtile, S, s_red, ranges, vals, splat,
-                              rgb + 3 * o, Tout ? Tout + o : nullptr, nullptr, nullptr, st);
+                              rgb + 3 * o, Tout ? Tout + o : nullptr, nullptr, nullptr, nullptr, st);
 }
 
 // ---------------------------------------------------------------------------

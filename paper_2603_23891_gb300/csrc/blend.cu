@@ -22,11 +22,12 @@ namespace fgs {
 
 using blendk::BlendSmem;
 
-template <bool kKpc, bool kCount = false>
+template <bool kKpc, bool kCount = false, bool kKeep = false>
 __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* __restrict__ ranges,
                                                     const uint32_t* __restrict__ vals,
                                                     const float* __restrict__ splat,
                                                     float* __restrict__ rgb, float* __restrict__ Tout,
+                                                    uint2* __restrict__ keep,
                                                     float* __restrict__ kpc_out,
                                                     float* __restrict__ G_out, FrameState* st)
 {
@@ -34,20 +35,25 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
     __shared__ double s_red[8];
     grid_dep_wait();
     grid_dep_trigger();
-    blendk::blend_tile<kKpc, kCount>(cam, blockIdx.x, blockIdx.x, S, s_red, ranges, vals, splat, rgb,
-                                     Tout, kpc_out, G_out, st);
+    blendk::blend_tile<kKpc, kCount, kKeep>(cam, blockIdx.x, blockIdx.x, S, s_red, ranges, vals, splat, rgb,
+                                     Tout, keep, kpc_out, G_out, st);
 }
 
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
-                  const float* splat, float* rgb, float* T, FrameState* st, bool count, cudaStream_t s)
+                  const float* splat, float* rgb, float* T, uint2* keep, FrameState* st, bool count,
+                  cudaStream_t s)
 {
     const int n_tiles = cam.tiles_x * cam.tiles_y;
+    float* const nf = nullptr;
     if (count)
-        launch_pdl(blend_kernel<false, true>, n_tiles, 256, 0, s, cam, ranges, vals, splat, rgb, T,
-                   (float*)nullptr, (float*)nullptr, st);
+        launch_pdl(blend_kernel<false, true>, n_tiles, 256, 0, s, cam, ranges, vals, splat, rgb, T, keep,
+                   nf, nf, st);
+    else if (keep)
+        launch_pdl(blend_kernel<false, false, true>, n_tiles, 256, 0, s, cam, ranges, vals, splat, rgb, T,
+                   keep, nf, nf, st);
     else
-        launch_pdl(blend_kernel<false>, n_tiles, 256, 0, s, cam, ranges, vals, splat, rgb, T,
-                   (float*)nullptr, (float*)nullptr, st);
+        launch_pdl(blend_kernel<false>, n_tiles, 256, 0, s, cam, ranges, vals, splat, rgb, T, keep, nf, nf,
+                   st);
 }
 
 void launch_blend_kpc(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
@@ -55,7 +61,7 @@ void launch_blend_kpc(const DevCamera& cam, const uint2* ranges, const uint32_t*
 {
     const int n_tiles = cam.tiles_x * cam.tiles_y;
     launch_pdl(blend_kernel<true>, n_tiles, 256, 0, s, cam, ranges, vals, splat, (float*)nullptr,
-               (float*)nullptr, kpc, G, st);
+               (float*)nullptr, (uint2*)nullptr, kpc, G, st);
 }
 
 __global__ void eval_exp_kernel(const float* __restrict__ x, float* __restrict__ y, uint64_t n)

@@ -152,14 +152,18 @@ __device__ __forceinline__ uint32_t warp_mask(const DevCamera& cam, int32_t tx0,
 
 // Blend one image tile (the CTA's).  `tile` is the tile in the camera's grid;
 // `gtile` indexes ranges and G_out (the same for one view; the batch's global
-// tile id).  rgb / Tout are the camera's own image planes.
-template <bool kKpc, bool kCount = false>
+// tile id).  rgb / Tout are the camera's own image planes.  With kKeep,
+// keep_out receives per pixel {final T bits, stop position}: the sorted-pair
+// index of the Gaussian the pixel stopped at, or the tile's end if it did not
+// stop; the differentiable form's backward walks each pixel from there.
+template <bool kKpc, bool kCount = false, bool kKeep = false>
 __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, uint32_t gtile,
                                            BlendSmem<kKpc>& S, double* s_red,
                                            const uint2* __restrict__ ranges,
                                            const uint32_t* __restrict__ vals,
                                            const float* __restrict__ splat, float* __restrict__ rgb,
-                                           float* __restrict__ Tout, float* __restrict__ kpc_out,
+                                           float* __restrict__ Tout, uint2* __restrict__ keep_out,
+                                           float* __restrict__ kpc_out,
                                            float* __restrict__ G_out, FrameState* st)
 {
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -238,6 +242,8 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
                     const float Tn = fm(T, fs(1.0f, alpha));
                     if (Tn < 0.0001f) {
                         done = true;            // stop before adding this Gaussian
+                        if (kKeep)
+                            keep_out[(size_t)y * cam.width + x] = make_uint2(__float_as_uint(T), s0 + j);
                     } else {
                         const float4 g2 = S.g2[j];
                         w = alpha * T;
@@ -285,6 +291,7 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
         rgb[hw + pix] = fmaf(T, cam.bg[1], Cacc.y);
         rgb[2 * hw + pix] = fmaf(T, cam.bg[2], Cacc.z);
         if (Tout) Tout[pix] = T;
+        if (kKeep && !done) keep_out[pix] = make_uint2(__float_as_uint(T), e);   // did not stop
     }
     if (kKpc) {
         // Eq. 6: G = mean KPC over the tile's pairs; fixed-order block reduction

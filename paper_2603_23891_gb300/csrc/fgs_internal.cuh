@@ -333,7 +333,8 @@ void launch_tile_ranges(const unsigned long long* keys, unsigned long long cap, 
                         const FrameState* st, int blocks, cudaStream_t s);
 // count: use the counting variant (fills FrameState::blend_* work counters)
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
-                  const float* splat, float* rgb, float* T, FrameState* st, bool count, cudaStream_t s);
+                  const float* splat, float* rgb, float* T, uint2* keep, FrameState* st, bool count,
+                  cudaStream_t s);
 void launch_blend_kpc(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
                       const float* splat, float* kpc, float* G, FrameState* st, cudaStream_t s);
 
@@ -351,7 +352,8 @@ void launch_batch_blend(const DevCamera* cams, int V, uint32_t total_tiles, cons
 void launch_prep_params(const DevTree& t, const float* mu, const float* log_scale, const float* quat,
                         const float* logit, const float* sh, int blocks, cudaStream_t s);
 void launch_backward(const DevTree& t, const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
-                     const float* splat, const uint32_t* sel, const float* dL_drgb, float* gsplat,
+                     const float* splat, const uint2* keep, const uint32_t* sel, const float* dL_drgb,
+                     float* gsplat,
                      const float* const params[5], float* const grads[5], bool accumulate, int proj_blocks,
                      FrameState* st, cudaStream_t s);
 void launch_levelwise_step(const DevTree& t, const DevCamera& cam, const uint32_t* child_start,

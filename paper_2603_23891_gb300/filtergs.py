@@ -31,6 +31,7 @@ FGS_RENDER_STAGE_EVENTS = 2
 FGS_RENDER_COUNT = 8
 FGS_N_STAGES = 6
 FGS_BATCH_GRAPH = 4
+FGS_RENDER_KEEP = 16
 STAGE_NAMES = ["filter_rl", "ancestor_compact", "project_keys", "sort", "tile_ranges", "blend"]
 SPLAT_FIELDS = ["u", "v", "A", "B", "C", "lthr", "a0", "depth", "r", "g", "b", "radius"]
 
@@ -447,7 +448,7 @@ class Renderer:
         levels = fgs_filter_levelwise(self.ctx, self.stream, out, n, M, 0)
         return out[: int(M[0])].copy(), levels
 
-    def render(self, rgb=None, T=None, stats=False, stage_events=False, count=False):
+    def render(self, rgb=None, T=None, stats=False, stage_events=False, count=False, keep=False):
         torch = _torch()
         H, W = self.cam.height, self.cam.width
         if rgb is None:
@@ -456,7 +457,7 @@ class Renderer:
             T = torch.empty((H, W), dtype=torch.float32, device=self.torch_device)
         st = fgs_stats()
         flags = (FGS_RENDER_STATS if stats else 0) | (FGS_RENDER_STAGE_EVENTS if stage_events else 0)
-        flags |= FGS_RENDER_COUNT if count else 0
+        flags |= (FGS_RENDER_COUNT if count else 0) | (FGS_RENDER_KEEP if keep else 0)
         fgs_render(self.ctx, self.stream, rgb, T, 1, flags, st)
         return rgb, T, st
 
@@ -617,7 +618,7 @@ def _make_render_function():
             params = {k: v.detach().contiguous() for k, v in
                       zip(GRAD_FIELDS, (mu, log_scale, quat, logit, sh))}
             renderer.update_params(params)
-            rgb, _, _ = renderer.render()
+            rgb, _, _ = renderer.render(keep=True)
             ctx.renderer = renderer
             ctx.params = params
             return rgb

@@ -5,7 +5,10 @@
 
 With --tau the frames use that shrink threshold and no calibration kernels run,
 so the launch sequence is exactly the per-frame path (12 kernels per frame).
-Without it the frames use the 3-sigma footprint.
+Without it the frames use the 3-sigma footprint.  With --backward the tree's
+attributes are first recomputed from its parameters (one prep_params launch)
+and every frame is followed by the differentiable form's backward for
+dL/drgb ~ N(0, 1) (accumulate mode: zero_rows, blend_bwd, project_bwd).
 """
 from __future__ import annotations
 
@@ -26,6 +29,7 @@ def main():
     ap.add_argument("--pose", type=int, default=0)
     ap.add_argument("--tau", type=float, default=None)
     ap.add_argument("--ln-tau", dest="ln_tau", type=float, default=None)
+    ap.add_argument("--backward", action="store_true")
     args = ap.parse_args()
 
     import torch
@@ -43,10 +47,22 @@ def main():
         r.shrink(args.tau, args.ln_tau)
     cam = cams[args.pose % len(cams)]
     r.set_camera(cam)
+    P = G = dL = None
+    if args.backward:
+        import numpy as np
+        P = {"mu": tree.mu, "log_scale": tree.log_scale, "quat": tree.quat,
+             "logit": tree.opacity_logit, "sh": tree.sh}
+        P = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda() for k, v in P.items()}
+        G = {k: torch.zeros_like(v) for k, v in P.items()}
+        dL = torch.randn((3, cam.height, cam.width), device="cuda",
+                         generator=torch.Generator(device="cuda").manual_seed(0))
+        r.update_params(P)
     t0 = time.time()
     st = None
     for _ in range(args.frames):
-        _, _, st = r.render(stats=True)
+        _, _, st = r.render(stats=True, keep=args.backward)
+        if args.backward:
+            r.backward(dL, P, G, accumulate=True)
     torch.cuda.synchronize()
     print(f"{args.frames} frames, M={st.n_selected} N_P={st.n_pairs} "
           f"launches/frame={st.n_launches} ({time.time() - t0:.3f}s)")

@@ -11,6 +11,7 @@ IMG_TOL = 2e-3          # max-abs per channel, FP32 accumulation (spec bou
 PSNR_MIN = 60.0
 EXACT_FIELDS = [0, 1, 2, 3, 4, 5, 6, 7, 11]   # u v A B C lthr a0 depth radius
 COLOUR_FIELDS = [8, 9, 10]
+GRAD_RTOL = 1e-3        # per parameter group: max-abs error / max-abs oracle gradient
 
 
 def psnr(a, b):
@@ -80,3 +81,81 @@ def orbit_cameras(tree, n, size, seed, dist=(8.0, 40.0), fov=(35.0, 80.0)):
         cams.append(synth.look_at_camera(pos, c + rng.normal(0, 1.0, 3), size[0], size[1],
                                          rng.uniform(*fov)))
     return cams
+
+
+# ---------------------------------------------------------------- differentiable form
+
+def dev_params(gp):
+    import torch
+    return {k: torch.from_numpy(np.ascontiguousarray(getattr(gp, k), np.float32)).cuda()
+            for k in oracle.GRAD_FIELDS}
+
+
+def gpu_grad(r, gp, cam, tau_R, dL, tile=(16, 16), bg=(0, 0, 0), shrink=None, warp_w=8):
+    """update_params -> render -> backward; host numpy results."""
+    import torch
+    r.set_params(tau_R=tau_R, tile=tile, bg=bg, blend_warp_w=warp_w)
+    r.set_camera(cam)
+    r.shrink(*shrink) if shrink else r.shrink(None)
+    P = dev_params(gp)
+    r.update_params(P)
+    rgb, T, st = r.render(stats=True, keep=True)
+    G = r.backward(torch.from_numpy(np.ascontiguousarray(dL, np.float32)).cuda(), P)
+    torch.cuda.synchronize()
+    keys, vals = r.pairs()
+    out = dict(rgb=rgb.cpu().numpy(), T=T.cpu().numpy(), keys=keys, vals=vals, splat=r.splats(),
+               M=int(st.n_selected), NP=int(st.n_pairs),
+               grads={k: v.cpu().numpy() for k, v in G.items()}, P=P)
+    out["sel"] = r.filter()
+    return out
+
+
+def oracle_params(tau_R, tile=(16, 16), bg=(0, 0, 0), shrink=None):
+    p = oracle.Params(tau_R=tau_R, tile_w=tile[0], tile_h=tile[1], bg=tuple(bg))
+    if shrink:
+        p.shrink, p.tau, p.ln_tau = True, shrink[0], shrink[1]
+    return p
+
+
+def assert_grad_parity(g, of, n_nodes):
+    sel = of.frame.sel
+    outside = np.ones(n_nodes, bool)
+    outside[sel] = False
+    worst = {}
+    for k in oracle.GRAD_FIELDS:
+        a = g["grads"][k].astype(np.float64)
+        o = of.grads[k]
+        scale = np.abs(o).max()
+        err = np.abs(a - o).max()
+        worst[k] = err / max(scale, 1e-30)
+        assert err <= GRAD_RTOL * scale + 1e-7, (k, err, scale)
+        node_axis = 0 if k == "sh" else -1
+        zero = np.take(a, np.nonzero(outside)[0], axis=node_axis)
+        assert not zero.any(), f"{k}: gradient outside the cut"
+    return worst
+
+
+def grad_parity_case(r, tree, cam, tau_R, seed, tile=(16, 16), bg=(0.2, 0.1, 0.4), shrink=None,
+                     warp_w=8, pix=None):
+    """The tree's own parameters through the GPU and the oracle; dL/drgb ~ N(0, 1)
+    (only at ``pix`` when given).  Whole frames: the frame bit for bit; with
+    ``pix``: selection and pairs bit for bit.  Then the gradients."""
+    gp = oracle.GaussParams.of_tree(tree)
+    rng = np.random.default_rng(seed)
+    dL = rng.normal(size=(3, cam.height, cam.width)).astype(np.float32)
+    if pix is not None:
+        mask = np.zeros(cam.height * cam.width, bool)
+        mask[pix] = True
+        dL = dL * mask.reshape(cam.height, cam.width)
+    r.load_tree(tree)
+    g = gpu_grad(r, gp, cam, tau_R, dL, tile, bg, shrink, warp_w)
+    p = oracle_params(tau_R, tile, bg, shrink)
+    of = oracle.grad_frame(tree, gp, cam, p, dL, pix=pix)
+    if pix is None:
+        of_fr = oracle.frame(oracle.tree_with_params(tree, gp), cam, p)
+        assert_frame_parity(g, of_fr)
+    else:
+        assert np.array_equal(g["sel"], of.frame.sel)
+        assert g["NP"] == len(of.frame.keys)
+        assert np.array_equal(g["keys"], of.frame.keys) and np.array_equal(g["vals"], of.frame.vals)
+    return g, of, assert_grad_parity(g, of, tree.n)

@@ -10,11 +10,9 @@ import pytest
 import oracle
 from paper_2603_23891_gb300 import synth
 
-from gpu_util import assert_frame_parity
+from gpu_util import dev_params, gpu_grad, grad_parity_case
 
 pytestmark = pytest.mark.gpu
-
-GRAD_RTOL = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -29,84 +27,11 @@ def renderer():
     r.close()
 
 
-def _dev_params(gp):
-    import torch
-    return {k: torch.from_numpy(np.ascontiguousarray(getattr(gp, k), np.float32)).cuda()
-            for k in oracle.GRAD_FIELDS}
-
-
-def gpu_grad(r, gp, cam, tau_R, dL, tile=(16, 16), bg=(0, 0, 0), shrink=None, warp_w=8):
-    """update_params -> render -> backward; host numpy results."""
-    import torch
-    r.set_params(tau_R=tau_R, tile=tile, bg=bg, blend_warp_w=warp_w)
-    r.set_camera(cam)
-    r.shrink(*shrink) if shrink else r.shrink(None)
-    P = _dev_params(gp)
-    r.update_params(P)
-    rgb, T, st = r.render(stats=True)
-    G = r.backward(torch.from_numpy(np.ascontiguousarray(dL, np.float32)).cuda(), P)
-    torch.cuda.synchronize()
-    keys, vals = r.pairs()
-    out = dict(rgb=rgb.cpu().numpy(), T=T.cpu().numpy(), keys=keys, vals=vals, splat=r.splats(),
-               M=int(st.n_selected), NP=int(st.n_pairs),
-               grads={k: v.cpu().numpy() for k, v in G.items()}, P=P)
-    out["sel"] = r.filter()
-    return out
-
-
-def oracle_params(tau_R, tile=(16, 16), bg=(0, 0, 0), shrink=None):
-    p = oracle.Params(tau_R=tau_R, tile_w=tile[0], tile_h=tile[1], bg=tuple(bg))
-    if shrink:
-        p.shrink, p.tau, p.ln_tau = True, shrink[0], shrink[1]
-    return p
-
-
-def assert_grad_parity(g, of, n_nodes):
-    sel = of.frame.sel
-    outside = np.ones(n_nodes, bool)
-    outside[sel] = False
-    worst = {}
-    for k in oracle.GRAD_FIELDS:
-        a = g["grads"][k].astype(np.float64)
-        o = of.grads[k]
-        scale = np.abs(o).max()
-        err = np.abs(a - o).max()
-        worst[k] = err / max(scale, 1e-30)
-        assert err <= GRAD_RTOL * scale + 1e-7, (k, err, scale)
-        node_axis = 0 if k == "sh" else -1
-        zero = np.take(a, np.nonzero(outside)[0], axis=node_axis)
-        assert not zero.any(), f"{k}: gradient outside the cut"
-    return worst
-
-
-def _check(r, tree, cam, tau_R, seed, tile=(16, 16), bg=(0.2, 0.1, 0.4), shrink=None, warp_w=8,
-           pix=None):
-    gp = oracle.GaussParams.of_tree(tree)
-    rng = np.random.default_rng(seed)
-    dL = rng.normal(size=(3, cam.height, cam.width)).astype(np.float32)
-    if pix is not None:
-        mask = np.zeros(cam.height * cam.width, bool)
-        mask[pix] = True
-        dL = dL * mask.reshape(cam.height, cam.width)
-    r.load_tree(tree)
-    g = gpu_grad(r, gp, cam, tau_R, dL, tile, bg, shrink, warp_w)
-    p = oracle_params(tau_R, tile, bg, shrink)
-    of = oracle.grad_frame(tree, gp, cam, p, dL, pix=pix)
-    if pix is None:
-        of_fr = oracle.frame(oracle.tree_with_params(tree, gp), cam, p)
-        assert_frame_parity(g, of_fr)
-    else:
-        assert np.array_equal(g["sel"], of.frame.sel)
-        assert g["NP"] == len(of.frame.keys)
-        assert np.array_equal(g["keys"], of.frame.keys) and np.array_equal(g["vals"], of.frame.vals)
-    return g, of, assert_grad_parity(g, of, tree.n)
-
-
 @pytest.mark.parametrize("seed,deg,warp_w", [(0, 3, 8), (1, 1, 4), (2, 0, 8), (3, 2, 4)])
 def test_grad_scene(renderer, seed, deg, warp_w):
     """64 Gaussians at 32x32 (several layers per pixel), SH degrees 0-3, both warp shapes."""
     tree, cam = synth.grad_scene(seed, sh_degree=deg)
-    _, of, worst = _check(renderer, tree, cam, 0.0, seed, warp_w=warp_w)
+    _, of, worst = grad_parity_case(renderer, tree, cam, 0.0, seed, warp_w=warp_w)
     assert len(of.ent) > 4 * cam.width * cam.height
     print(f"seed {seed}: worst relative gradient error {max(worst.values()):.2e}")
 
@@ -118,7 +43,7 @@ def test_multilevel_cut_ragged_and_shrink(renderer, tile):
                                    log_scale_mean=-0.8)
     cam = synth.look_at_camera([0.0, -14.0, 6.0], [0.0, 0.0, 0.0], 40, 24, 60.0)
     for shrink in (None, (0.02, float(np.float32(np.log(0.02))))):
-        g, of, _ = _check(renderer, tree, cam, 6.0, 5, tile=tile, shrink=shrink)
+        g, of, _ = grad_parity_case(renderer, tree, cam, 6.0, 5, tile=tile, shrink=shrink)
         assert (tree.is_leaf[of.frame.sel] == 0).any()
 
 
@@ -128,7 +53,7 @@ def test_random_trees_many_tiles(renderer):
         tree = synth.random_small_tree(seed, n_leaves=2000, branching=(2, 6), sh_degree=3,
                                        extent=12.0, log_scale_mean=-1.2)
         cam = synth.look_at_camera([0.0, -30.0, 14.0], [0.0, 0.0, 0.0], 200, 120, 60.0)
-        _check(renderer, tree, cam, tau_R, seed)
+        grad_parity_case(renderer, tree, cam, tau_R, seed)
 
 
 def test_empty_view_gradient_is_zero(renderer):
@@ -154,7 +79,7 @@ def test_accumulate_and_autograd(renderer):
     P = g["P"]
     # accumulate: the same frame's gradient added twice
     renderer.update_params(P)
-    renderer.render()
+    renderer.render(keep=True)
     dLt = torch.from_numpy(dL).cuda()
     acc = renderer.backward(dLt, P)
     renderer.backward(dLt, P, grads=acc, accumulate=True)
@@ -176,13 +101,17 @@ def test_backward_state_and_argument_errors(renderer):
     gp = oracle.GaussParams.of_tree(tree)
     renderer.load_tree(tree)
     renderer.set_camera(cam)
-    P = _dev_params(gp)
+    P = dev_params(gp)
     renderer.update_params(P)
     dL = torch.zeros((3, 32, 32), device="cuda")
     with pytest.raises(filtergs.FgsError) as e:          # no frame since the parameters changed
         renderer.backward(dL, P)
     assert e.value.code == filtergs.FGS_ERR_STATE
-    renderer.render()
+    renderer.render()                                    # rendered without KEEP: refused too
+    with pytest.raises(filtergs.FgsError) as e:
+        renderer.backward(dL, P)
+    assert e.value.code == filtergs.FGS_ERR_STATE
+    renderer.render(keep=True)
     host = {k: v.cpu() for k, v in P.items()}
     with pytest.raises(filtergs.FgsError) as e:          # host memory is refused before any launch
         filtergs.fgs_backward(renderer.ctx, renderer.stream, dL, host,
@@ -198,6 +127,6 @@ def test_blobs_1080p_sampled_pixels(renderer):
     tree = synth.blob_tree()
     cam = synth.blob_cameras()[2]
     pix = np.sort(np.random.default_rng(9).choice(cam.width * cam.height, 4096, replace=False))
-    g, of, worst = _check(renderer, tree, cam, 3.0, 21, shrink=(0.05, float(np.float32(np.log(0.05)))),
-                          pix=pix)
+    shrink = (0.05, float(np.float32(np.log(0.05))))
+    g, of, worst = grad_parity_case(renderer, tree, cam, 3.0, 21, shrink=shrink, pix=pix)
     print(f"blobs: M={g['M']} N_P={g['NP']} worst relative gradient error {max(worst.values()):.2e}")

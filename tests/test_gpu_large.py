@@ -12,7 +12,7 @@ import pytest
 import oracle
 from paper_2603_23891_gb300 import synth
 
-from gpu_util import IMG_TOL, assert_frame_parity, gpu_frame, oracle_frame, psnr
+from gpu_util import IMG_TOL, assert_frame_parity, gpu_frame, grad_parity_case, oracle_frame, psnr
 
 pytestmark = pytest.mark.gpu
 
@@ -96,3 +96,16 @@ def test_city_benchmark_configuration(renderer, city):
         assert np.abs(grgb - rgb).max() <= IMG_TOL
         assert np.array_equal(gT.view(np.uint32), T.view(np.uint32))
         print(f"pose {k}: M={g['M']} N_P={g['NP']} sampled max-abs {np.abs(grgb - rgb).max():.2e}")
+
+
+def test_city_gradient_sampled_pixels(renderer, city):
+    """Differentiable form on the 10M-leaf city tree at 1920x1080 (16x16 tiles, shrink at
+    tau = 0.0772): the gradient of a loss on 4096 sampled pixels for every node, against
+    the oracle's binary64 gradient; selection and pairs bit for bit."""
+    tree, cams = city
+    pix = np.sort(np.random.default_rng(5).choice(1920 * 1080, 4096, replace=False))
+    shrink = (0.0772, float(np.float32(math.log(0.0772))))
+    g, of, worst = grad_parity_case(renderer, tree, cams[21], 3.0, 8, bg=(0.0, 0.0, 0.0),
+                                    shrink=shrink, pix=pix)
+    print(f"city pose 21: M={g['M']} N_P={g['NP']} worst relative gradient error "
+          f"{max(worst.values()):.2e}")
