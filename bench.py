@@ -419,6 +419,23 @@ def run_ours(args):
     if args.batch and args.workload == "city":
         batched = run_batched(r, torch, filtergs, args)
 
+    # shrinking study (3 sigma, tau = 1/255, lambda_G sweep) on 8 of the poses
+    study = None
+    if args.study:
+        from paper_2603_23891_gb300 import shrink_study
+        r.set_params(tau_R=tau_R, tile=(16, 16), blend_warp_w=8, pair_capacity=args.pair_capacity)
+        st_poses = my_poses[:: max(1, len(my_poses) // 8)][:8]
+        full = shrink_study.run_study(r, cams, st_poses)
+        study = {"poses": full["poses"], "G_bar": full["G_bar"], "settings": [
+            {k: row[k] for k in ("setting", "tau", "N_P_mean", "N_P_vs_3sigma", "fps",
+                                 "psnr_vs_3sigma_db", "max_abs_vs_3sigma")}
+            | {"kpc_below_0.01": row["kpc"]["below_0.01"], "kpc_below_0.05": row["kpc"]["below_0.05"],
+               "redundant_0.05_vs_3sigma": row["redundant_0.05_vs_3sigma"]}
+            for row in full["settings"]],
+            "how": "per setting: mean over the poses; KPC (Eq. 5) of the emitted pairs under that "
+                   "footprint; image error against the 3-sigma GPU render of the same pose"}
+        r.shrink(tau, ln_tau)
+
     # last: it replaces the tree's attributes by the binary32 parameter map
     backward = None
     if args.backward:
@@ -497,6 +514,7 @@ def run_ours(args):
             "calibration_s": round(calib_s, 3),
             "batched": batched,
             "backward": backward,
+            "shrink_study": study,
             "wall_s_timed": round(wall, 4),
         }
     r.close()
@@ -600,6 +618,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--no-backward", dest="backward", action="store_false")
+    ap.add_argument("--no-study", dest="study", action="store_false")
     ap.add_argument("--batch-reps", type=int, default=5)
     ap.add_argument("--batch-sel-cap", type=int, default=96 << 20)
     ap.add_argument("--batch-pair-cap", type=int, default=256 << 20)

@@ -243,6 +243,14 @@ int fgs_get_splats(fgs_ctx* ctx, void* stream, float* out, uint32_t cap, uint32_
 int fgs_calibrate_view(fgs_ctx* ctx, void* stream, double* gbar_out, float* kpc_out,
                        uint64_t kpc_cap, float* G_out, int out_is_device);
 
+/* As fgs_calibrate_view, but under the context's current footprint mode
+ * (3-sigma, or shrunk to tau when shrinking is on): the KPC of every pair the
+ * shrunk frame emits, the per-tile GTC and the view average.  Serves the study
+ * of redundant pairs (§3.3: pairs whose KPC is near zero) before and after
+ * shrinking.  Same arguments, outputs and errors as fgs_calibrate_view. */
+int fgs_kpc_view(fgs_ctx* ctx, void* stream, double* gbar_out, float* kpc_out, uint64_t kpc_cap,
+                 float* G_out, int out_is_device);
+
 /* Scene calibration (§3.3, Eq. 8): pre-render n_views cameras (host array),
  * G = mean of their G_v, tau = lambda_G / G, ln_tau = ln lambda_G - ln G
  * (float64, rounded once).  gbar_views_out (host, n_views doubles) may be

@@ -887,15 +887,19 @@ int fgs_get_splats(fgs_ctx* c, void* stream, float* out, uint32_t cap, uint32_t*
     return FGS_OK;
 }
 
-int fgs_calibrate_view(fgs_ctx* c, void* stream, double* gbar_out, float* kpc_out, uint64_t kpc_cap,
-                       float* G_out, int out_is_device)
+namespace {
+
+// The current camera through the KPC blend (Eq. 5-7); force_3sigma selects the
+// calibration footprint, otherwise the context's shrink mode applies.
+int kpc_view(fgs_ctx* c, void* stream, bool force_3sigma, double* gbar_out, float* kpc_out,
+             uint64_t kpc_cap, float* G_out, int out_is_device)
 {
     int r = check_ready(c);
     if (r) return r;
     if (!gbar_out) return fail(c, FGS_ERR_ARG, "null gbar output");
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    const DevCamera dc = make_devcam(c, true);   // calibration uses the 3-sigma footprint
+    const DevCamera dc = make_devcam(c, force_3sigma);
     enqueue_front(c, dc, s, nullptr);
     FGS_CUDA(c, cudaMemsetAsync(c->kpc, 0, c->pair_cap * 4, s));
     launch_blend_kpc(dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, c->kpc, c->G,
@@ -927,6 +931,21 @@ int fgs_calibrate_view(fgs_ctx* c, void* stream, double* gbar_out, float* kpc_ou
         }
     *gbar_out = used ? sum / (double)used : NAN;
     return FGS_OK;
+}
+
+}  // namespace
+
+int fgs_calibrate_view(fgs_ctx* c, void* stream, double* gbar_out, float* kpc_out, uint64_t kpc_cap,
+                       float* G_out, int out_is_device)
+{
+    // calibration uses the 3-sigma footprint
+    return kpc_view(c, stream, true, gbar_out, kpc_out, kpc_cap, G_out, out_is_device);
+}
+
+int fgs_kpc_view(fgs_ctx* c, void* stream, double* gbar_out, float* kpc_out, uint64_t kpc_cap,
+                 float* G_out, int out_is_device)
+{
+    return kpc_view(c, stream, false, gbar_out, kpc_out, kpc_cap, G_out, out_is_device);
 }
 
 int fgs_calibrate_gtc(fgs_ctx* c, void* stream, const fgs_camera* views, int n_views, float lambda_G,

@@ -41,7 +41,7 @@ EXPORTED = ["fgs_version", "fgs_create", "fgs_destroy", "fgs_last_error", "fgs_s
             "fgs_calibrate_view", "fgs_calibrate_gtc", "fgs_sync", "fgs_validate_tree",
             "fgs_eval_exp", "fgs_compact_selection_noalloc", "fgs_filter_levelwise",
             "fgs_batch_setup", "fgs_batch_set_cameras", "fgs_batch_image_offsets", "fgs_render_batch",
-            "fgs_update_params", "fgs_backward"]
+            "fgs_update_params", "fgs_backward", "fgs_kpc_view"]
 
 FGS_BACKWARD_ACCUMULATE = 1
 GRAD_FIELDS = ("mu", "log_scale", "quat", "logit", "sh")
@@ -116,6 +116,7 @@ def lib():
         "fgs_get_pairs": ([vp, vp, vp, vp, u64, C.POINTER(u64), i32], i32),
         "fgs_get_splats": ([vp, vp, vp, u32, C.POINTER(u32), i32], i32),
         "fgs_calibrate_view": ([vp, vp, C.POINTER(C.c_double), vp, u64, vp, i32], i32),
+        "fgs_kpc_view": ([vp, vp, C.POINTER(C.c_double), vp, u64, vp, i32], i32),
         "fgs_calibrate_gtc": ([vp, vp, vp, i32, f32, vp, C.POINTER(f32), C.POINTER(f32)], i32),
         "fgs_sync": ([vp, vp], i32),
         "fgs_validate_tree": ([C.POINTER(fgs_tree), C.c_char_p, C.c_size_t], i32),
@@ -338,6 +339,14 @@ def fgs_calibrate_view(ctx, stream, kpc_out=None, kpc_cap: int = 0, G_out=None,
     return float(g.value)
 
 
+def fgs_kpc_view(ctx, stream, kpc_out=None, kpc_cap: int = 0, G_out=None,
+                 out_is_device: int = 0) -> float:
+    g = C.c_double()
+    _check(ctx, lib().fgs_kpc_view(ctx, stream, C.byref(g), _ptr(kpc_out), kpc_cap,
+                                   _ptr(G_out), out_is_device))
+    return float(g.value)
+
+
 def fgs_calibrate_gtc(ctx, stream, cams, lambda_G: float = 0.2):
     arr = (fgs_camera * len(cams))(*[c if isinstance(c, fgs_camera) else make_camera(c) for c in cams])
     gb = np.zeros(len(cams), np.float64)
@@ -501,6 +510,16 @@ class Renderer:
             kpc = np.zeros(max(cap, 1), np.float32)
         gbar = fgs_calibrate_view(self.ctx, self.stream, kpc, cap, G, 0)
         return gbar, G, (kpc[:cap] if want_kpc else None)
+
+    def kpc_view(self, n_pairs):
+        """KPC of every pair of the current camera under the current footprint
+        mode (host numpy), with the per-tile GTC and the view average."""
+        tiles = ((self.cam.width + self.params.tile_w - 1) // self.params.tile_w) * \
+                ((self.cam.height + self.params.tile_h - 1) // self.params.tile_h)
+        G = np.zeros(tiles, np.float32)
+        kpc = np.zeros(max(int(n_pairs), 1), np.float32)
+        gbar = fgs_kpc_view(self.ctx, self.stream, kpc, int(n_pairs), G, 0)
+        return gbar, G, kpc[: int(n_pairs)]
 
     def calibrate(self, cams, lambda_G=0.2):
         return fgs_calibrate_gtc(self.ctx, self.stream, cams, lambda_G)
