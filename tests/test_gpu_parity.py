@@ -10,7 +10,7 @@ import pytest
 import oracle
 from paper_2603_23891_gb300 import synth
 
-from gpu_util import assert_frame_parity, gpu_frame, oracle_frame, orbit_cameras
+from gpu_util import IMG_TOL, assert_frame_parity, gpu_frame, oracle_frame, orbit_cameras
 
 pytestmark = pytest.mark.gpu
 
@@ -280,3 +280,36 @@ def test_blend_counters_consistent(renderer, tiny):
     assert st1.n_pairs == st0.n_pairs
     assert 0 < st1.blend_hits <= st1.blend_evals <= 32 * st1.blend_entries
     assert st1.blend_entries <= 8 * st1.n_pairs
+
+
+def test_crowded_tiles_sorted_in_global_memory(renderer):
+    """Tiles holding more than 4096 pairs (the per-tile sort's shared-memory limit):
+    20k Gaussians seen at 64x48 on 16x16 tiles (12 tiles), sorted by the global-memory
+    bitonic network; pairs and image against the oracle."""
+    tree = synth.random_small_tree(21, n_leaves=20000, branching=(2, 6), sh_degree=0,
+                                   extent=6.0, log_scale_mean=-1.0)
+    cam = synth.look_at_camera([0.0, -16.0, 8.0], [0.0, 0.0, 0.0], 64, 48, 60.0)
+    renderer.load_tree(tree)
+    g = gpu_frame(renderer, tree, cam, -1.0)
+    o, _ = oracle_frame(tree, cam, -1.0)
+    tiles = (o.keys >> np.uint64(32)).astype(np.int64)
+    per_tile = np.bincount(tiles)
+    assert per_tile.max() > 4096, per_tile.max()
+    assert_frame_parity(g, o)
+
+
+def test_large_tile_grid_uses_radix_sort(renderer):
+    """A 4096x4096 image on 16x16 tiles (65,536 tiles: more than the tile-bucketing
+    prefix holds) takes the global radix sort; pairs bit for bit, sampled pixels."""
+    tree = synth.tiny_tree()
+    cam = synth.look_at_camera([0.0, -60.0, 30.0], [0.0, 0.0, 0.0], 4096, 4096, 60.0)
+    renderer.load_tree(tree)
+    g = gpu_frame(renderer, tree, cam, 3.0)
+    o, p = oracle_frame(tree, cam, 3.0, blend=False)
+    assert len(o.keys) > 100000
+    assert_frame_parity(g, o, check_image=False)
+    pix = np.sort(np.random.default_rng(3).choice(4096 * 4096, 20000, replace=False))
+    rgb, T = oracle.render_pixels(o.splat, o.keys, o.vals, cam, p, pix)
+    grgb = g["rgb"].reshape(3, -1)[:, pix].T.astype(np.float64)
+    assert np.abs(grgb - rgb).max() <= IMG_TOL
+    assert np.array_equal(g["T"].reshape(-1)[pix].view(np.uint32), T.view(np.uint32))
