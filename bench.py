@@ -216,61 +216,109 @@ def run_batched(r, torch, filtergs, args):
 
 # ----------------------------------------------------------------------------- ours
 
-def run_backward(r, torch, filtergs, tree, cams, poses, args):
-    """Differentiable form on the workload: parameters -> attributes, render,
-    then the hand-written backward for dL/drgb ~ N(0, 1).  Times the render and
-    the backward per pose (CUDA events, L2 flushed between), in overwrite mode
-    (every node's gradient written: zeros outside the cut) and in accumulate
-    mode (only the cut's gradients added)."""
-    dev = torch.device("cuda", torch.cuda.current_device())
+def _time_backward(r, torch, cams, poses, P, G, dL_of, keep, accumulate, flush):
+    """Per pose: render (keep or not), the loss gradient, the backward; CUDA
+    events around the render and around the backward.  Returns mean ms."""
+    stream = torch.cuda.current_stream()
+    for w in range(3):
+        r.set_camera(cams[poses[w % len(poses)]])
+        rgb, _, _ = r.render(keep=keep)
+        r.backward(dL_of(poses[w % len(poses)], rgb), P, G, accumulate=accumulate)
+    torch.cuda.synchronize()
+    fwd, bwd = [], []
+    for k in poses:
+        flush.zero_()
+        r.set_camera(cams[k])
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        rgb, _, _ = r.render(keep=keep)
+        e[1].record(stream)
+        dL = dL_of(k, rgb)
+        e[2].record(stream)
+        r.backward(dL, P, G, accumulate=accumulate)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        fwd.append(e[0].elapsed_time(e[1]))
+        bwd.append(e[2].elapsed_time(e[3]))
+    return round(float(np.mean(fwd)), 4), round(float(np.mean(bwd)), 4)
+
+
+def _tree_params(torch, tree, dev):
     P = {"mu": tree.mu, "log_scale": tree.log_scale, "quat": tree.quat,
          "logit": tree.opacity_logit, "sh": tree.sh}
-    P = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).to(dev) for k, v in P.items()}
-    G = {k: torch.empty_like(v) for k, v in P.items()}
-    W, H = cams[0].width, cams[0].height
-    dL = torch.randn((3, H, W), generator=torch.Generator(device=dev).manual_seed(0), device=dev)
-    rgb = torch.empty((3, H, W), dtype=torch.float32, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
+    return {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).to(dev) for k, v in P.items()}
+
+
+def run_backward(r, torch, filtergs, args):
+    """Differentiable form, its configuration: the 1M-leaf blob tree at
+    1920x1080 (3-sigma footprint), L2 loss against the image of the same tree
+    with every leaf attribute perturbed by N(0, 0.01) (seed 3, parents rebuilt).
+    Per pose: forward, dL/drgb = 2 (rgb - target), hand-written backward.  The
+    default backward recomputes each pixel's final transmittance by a walk over
+    its tile; with the forward's kept state (FGS_RENDER_KEEP) it reads it.
+    Accumulate mode (the cut's gradients added into the caller's buffers)."""
+    from paper_2603_23891_gb300 import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tree, target_tree, cams = synth.blob_tree(), synth.blob_target_tree(), synth.blob_cameras()
+    poses = list(range(len(cams)))
+    r.set_params(tau_R=3.0, tile=(16, 16), blend_warp_w=8, bg=(0.0, 0.0, 0.0),
+                 pair_capacity=args.pair_capacity)
+    r.shrink(None)
+    r.load_tree(target_tree)
+    targets = {}
+    for k in poses:
+        r.set_camera(cams[k])
+        rgb, _, _ = r.render()
+        targets[k] = rgb.clone()
+    r.load_tree(tree)
+    P = _tree_params(torch, tree, dev)
+    G = {k: torch.zeros_like(v) for k, v in P.items()}
     torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
     r.update_params(P)
-    t1.record(stream)
+    t1.record()
     torch.cuda.synchronize()
     prep_ms = t0.elapsed_time(t1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    loss = []
+
+    def dL_of(k, rgb):
+        d = rgb - targets[k]
+        if len(loss) < len(poses):
+            loss.append(float((d * d).sum()))
+        return 2.0 * d
+
+    out = {}
+    for name, keep in (("recompute", False), ("kept_state", True)):
+        f, b = _time_backward(r, torch, cams, poses, P, G, dL_of, keep, True, flush)
+        out[name] = {"forward_ms": f, "backward_ms": b}
+    K3 = (tree.sh_degree + 1) ** 2 * 3
+    return {"workload": "blobs-1M, 1920x1080, 8 poses, 3-sigma footprint, L2 loss against the "
+                        "tree with leaf attributes perturbed by N(0, 0.01)",
+            "nodes": tree.n, "params_per_node": 11 + K3, "ms_per_frame": out["recompute"]["backward_ms"],
+            "recompute": out["recompute"], "kept_state": out["kept_state"],
+            "prep_params_ms": round(prep_ms, 4), "loss_pose0": loss[0] if loss else None,
+            "how": "CUDA events around fgs_render and around fgs_backward per pose (L2 flushed "
+                   "before each pose), accumulate mode; the loss gradient is outside both"}
+
+
+def run_backward_city(r, torch, tree, cams, poses, args):
+    """The backward on the bench workload (city-10M, adaptive shrink), dL/drgb ~
+    N(0, 1), both transmittance modes, accumulate mode."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    P = _tree_params(torch, tree, dev)
+    G = {k: torch.zeros_like(v) for k, v in P.items()}
+    W, H = cams[0].width, cams[0].height
+    dL = torch.randn((3, H, W), generator=torch.Generator(device=dev).manual_seed(0), device=dev)
+    r.update_params(P)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     poses = poses[: min(16, len(poses))]
     out = {}
-    for mode, acc in (("overwrite", False), ("accumulate", True)):
-        for w in range(3):
-            r.set_camera(cams[poses[w % len(poses)]])
-            r.render(rgb, keep=True)
-            r.backward(dL, P, G, accumulate=acc)
-        torch.cuda.synchronize()
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in poses]
-        for i, k in enumerate(poses):
-            flush.zero_()
-            r.set_camera(cams[k])
-            ev[i][0].record(stream)
-            r.render(rgb, keep=True)
-            ev[i][1].record(stream)
-            r.backward(dL, P, G, accumulate=acc)
-            ev[i][2].record(stream)
-        torch.cuda.synchronize()
-        fwd = [e[0].elapsed_time(e[1]) for e in ev]
-        bwd = [e[1].elapsed_time(e[2]) for e in ev]
-        out[mode] = {"forward_ms": round(float(np.mean(fwd)), 4),
-                     "backward_ms": round(float(np.mean(bwd)), 4)}
-    n = tree.n
-    K3 = (tree.sh_degree + 1) ** 2 * 3
-    return {"poses": len(poses), "params_per_node": 11 + K3, "nodes": n,
-            "prep_params_ms": round(prep_ms, 4),
-            "overwrite": out["overwrite"], "accumulate": out["accumulate"],
-            "ms_per_frame": out["accumulate"]["backward_ms"],
-            "grad_zeroing_bytes": 4 * (11 + K3) * n,
-            "how": "CUDA events around fgs_render and fgs_backward per pose; dL/drgb ~ N(0,1); "
-                   "overwrite mode also writes zeros for every node outside the cut"}
+    for name, keep in (("recompute", False), ("kept_state", True)):
+        f, b = _time_backward(r, torch, cams, poses, P, G, lambda k, rgb: dL, keep, True, flush)
+        out[name] = {"forward_ms": f, "backward_ms": b}
+    return {"workload": "city-10M, 1920x1080, 16 poses, adaptive shrink, dL/drgb ~ N(0, 1)", **out}
 
 
 def run_ours(args):
@@ -436,12 +484,14 @@ def run_ours(args):
                    "footprint; image error against the 3-sigma GPU render of the same pose"}
         r.shrink(tau, ln_tau)
 
-    # last: it replaces the tree's attributes by the binary32 parameter map
+    # last: they replace the tree's attributes by the binary32 parameter map
     backward = None
     if args.backward:
         r.set_params(tau_R=tau_R, tile=(16, 16), blend_warp_w=8, pair_capacity=args.pair_capacity)
         r.shrink(tau, ln_tau)
-        backward = run_backward(r, torch, filtergs, tree, cams, my_poses, args)
+        backward_city = run_backward_city(r, torch, tree, cams, my_poses, args)
+        backward = run_backward(r, torch, filtergs, args)
+        backward["city"] = backward_city
 
     frames = K * world
     fps = frames / (total_ms / 1e3)

@@ -59,7 +59,8 @@ extern "C" {
 #define FGS_RENDER_STAGE_EVENTS 2u /* record per-stage CUDA events (see fgs_stage_times) */
 #define FGS_RENDER_COUNT 8u        /* count the blend's work (fgs_stats blend_*); implies STATS */
 #define FGS_RENDER_KEEP 16u        /* keep per-pixel final T and stop position (8 bytes a pixel,
-                                      context-owned) for fgs_backward; ignored with COUNT */
+                                      context-owned) so that fgs_backward need not recompute
+                                      them; ignored with COUNT */
 
 #define FGS_N_STAGES 6             /* filter-R&L, ancestor+compact, project+keys, sort, ranges, blend */
 
@@ -367,19 +368,20 @@ typedef struct fgs_gauss_grads {
 int fgs_update_params(fgs_ctx* ctx, void* stream, const fgs_gauss_params* p);
 
 /* Gradient of L = sum over pixels and channels of dL_drgb * rgb for the last
- * fgs_render of this context, which must have been made with FGS_RENDER_KEEP
- * (same camera, parameters as passed to the last fgs_update_params).  dL_drgb: DEVICE [3][H][W] (the layout of fgs_render's
+ * fgs_render of this context (same camera, parameters as passed to the last
+ * fgs_update_params).  dL_drgb: DEVICE [3][H][W] (the layout of fgs_render's
  * rgb_out).  p: the parameters of that render; g: gradient arrays of the same
  * shapes (device).  Without FGS_BACKWARD_ACCUMULATE every entry of g is
  * written (zero for nodes outside the cut); with it, the selected nodes'
- * gradients are added.  Two kernels: a per-tile blend backward that starts
- * from each pixel's kept final transmittance and stop position and walks the
- * tile back to front, recovering T before each Gaussian as T / (1 - alpha);
- * and a per-Gaussian chain rule through the conic, the EWA Jacobian,
- * Sigma(q, s), the sigmoid and the SH basis.  Asynchronous on `stream`.
- * Errors: FGS_ERR_STATE (no FGS_RENDER_KEEP frame since the last change of
- * tree, camera, parameters or settings), FGS_ERR_ARG, FGS_ERR_NOMEM,
- * FGS_ERR_CUDA. */
+ * gradients are added.  Two kernels: a per-tile blend backward that
+ * recomputes each pixel's final transmittance and stop position by a
+ * front-to-back walk over its tile (or reads them, if the render used
+ * FGS_RENDER_KEEP) and then walks the tile back to front, recovering T before
+ * each Gaussian as T / (1 - alpha); and a per-Gaussian chain rule through the
+ * conic, the EWA Jacobian, Sigma(q, s), the sigmoid and the SH basis.
+ * Asynchronous on `stream`.  Errors: FGS_ERR_STATE (no rendered frame since
+ * the last change of tree, camera, parameters or settings), FGS_ERR_ARG,
+ * FGS_ERR_NOMEM, FGS_ERR_CUDA. */
 int fgs_backward(fgs_ctx* ctx, void* stream, const float* dL_drgb, const fgs_gauss_params* p,
                  const fgs_gauss_grads* g, uint32_t flags);
 

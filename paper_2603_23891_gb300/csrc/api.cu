@@ -101,7 +101,8 @@ struct fgs_ctx {
     size_t gsplat_rows = 0;
     // last frame
     bool have_frame = false;
-    bool frame_kept = false;        // the last frame came from fgs_render with FGS_RENDER_KEEP
+    bool frame_rendered = false;    // the last frame came from fgs_render (not a calibration)
+    bool frame_kept = false;        // ... with FGS_RENDER_KEEP
     bool sorted_in_1 = false;
     // batched multi-view state
     struct Batch {
@@ -797,6 +798,7 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
     if (ev) cudaEventRecord(ev[6], s);
     FGS_CUDA(c, cudaGetLastError());
     c->have_frame = true;
+    c->frame_rendered = true;
     c->frame_kept = keep;
     if (!out_is_device) {
         FGS_CUDA(c, cudaMemcpyAsync(rgb_out, c->img, 3 * hw * 4, cudaMemcpyDeviceToHost, s));
@@ -906,6 +908,7 @@ int kpc_view(fgs_ctx* c, void* stream, bool force_3sigma, double* gbar_out, floa
                      c->st, s);
     FGS_CUDA(c, cudaGetLastError());
     c->have_frame = true;
+    c->frame_rendered = false;
     c->frame_kept = false;
     if ((r = read_state(c, s))) return r;
     if ((r = latched_status(c))) {
@@ -1031,8 +1034,7 @@ int fgs_backward(fgs_ctx* c, void* stream, const float* dL_drgb, const fgs_gauss
     int r = check_ready(c);
     if (r) return r;
     if (!p || !gr) return fail(c, FGS_ERR_ARG, "null parameter or gradient struct");
-    if (!c->have_frame || !c->frame_kept)
-        return fail(c, FGS_ERR_STATE, "no frame rendered with FGS_RENDER_KEEP to differentiate");
+    if (!c->have_frame || !c->frame_rendered) return fail(c, FGS_ERR_STATE, "no rendered frame to differentiate");
     DeviceGuard g(c->device);
     const void* ptrs[] = {dL_drgb, p->mu, p->log_scale, p->quat, p->logit, p->sh,
                           gr->mu, gr->log_scale, gr->quat, gr->logit, gr->sh};
@@ -1047,7 +1049,8 @@ int fgs_backward(fgs_ctx* c, void* stream, const float* dL_drgb, const fgs_gauss
     cudaStream_t s = (cudaStream_t)stream;
     const float* params[5] = {p->mu, p->log_scale, p->quat, p->logit, p->sh};
     float* grads[5] = {gr->mu, gr->log_scale, gr->quat, gr->logit, gr->sh};
-    launch_backward(c->tree, dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, c->keep, c->sel,
+    launch_backward(c->tree, dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat,
+                    c->frame_kept ? c->keep : nullptr, c->sel,
                     dL_drgb, c->gsplat, params, grads, (flags & FGS_BACKWARD_ACCUMULATE) != 0, c->sms, c->st,
                     s);
     FGS_CUDA(c, cudaGetLastError());

@@ -6,11 +6,12 @@
 // mean mu, log-scale s, quaternion q (any norm), opacity logit l, SH
 // coefficients; Sigma = R(q/|q|) diag(e^{2s}) R^T, alpha0 = sigmoid(l).
 //
-// The forward blend keeps, per pixel, its final transmittance and the sorted
-// position where it stopped (8 bytes).  blend_bwd_kernel walks each tile back
-// to front from there, recovering T before each Gaussian as T / (1 - alpha)
-// and accumulating the colour behind it; chunks past the last stop of the
-// tile are never loaded.  Gradients with respect to the splat record (u, v,
+// blend_bwd_kernel recomputes each pixel's final transmittance and stop
+// position by a front-to-back walk over its tile with the forward's exact
+// decisions (or, after a FGS_RENDER_KEEP forward, reads the 8 bytes per pixel
+// the forward kept), then walks the tile back to front, recovering T before
+// each Gaussian as T / (1 - alpha) and accumulating the colour behind it;
+// chunks past the last stop of the tile are never loaded.  Gradients with respect to the splat record (u, v,
 // conic A B C, alpha0, colour) are reduced per warp (a transposed reduction:
 // 12 shuffles for 9 values) and added per Gaussian; project_bwd_kernel then
 // applies the chain rule to the parameters.
@@ -183,6 +184,10 @@ __device__ __forceinline__ int lane_component(uint32_t lane)
     return (!(lane & 1) && pb < 3 && pa < 5 && comp < 9) ? comp : -1;
 }
 
+// kKept: the forward kept {final T, stop} per pixel (FGS_RENDER_KEEP).  Otherwise
+// a first front-to-back walk over the tile recomputes them with the forward's
+// exact decisions (nothing but the image is stored by the forward).
+template <bool kKept>
 __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uint2* __restrict__ ranges,
                                                         const uint32_t* __restrict__ vals,
                                                         const float* __restrict__ splat,
@@ -213,25 +218,79 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
     float dC[3] = {0.0f, 0.0f, 0.0f};
     if (inside) {
         const size_t hw = (size_t)cam.width * cam.height, pix = (size_t)y * cam.width + x;
-        const uint2 kp = keep[pix];
-        T = __uint_as_float(kp.x);
-        lim = kp.y;
+        if (kKept) {
+            const uint2 kp = keep[pix];
+            T = __uint_as_float(kp.x);
+            lim = kp.y;
+        }
         dC[0] = __ldg(dL_drgb + pix);
         dC[1] = __ldg(dL_drgb + hw + pix);
         dC[2] = __ldg(dL_drgb + 2 * hw + pix);
     }
-    const uint32_t wlim = __reduce_max_sync(0xffffffffu, lim);
-    if (lane == 0) B.lim[warp] = wlim;
     if (tid == 0) {
         blendk::mbar_init(&S.bar, 1);
         S.timed_out = 0;
     }
     __syncthreads();
+    uint32_t phase = 0;
+    if (!kKept) {
+        // recompute final T and the stop position: the forward walk without colour
+        bool done = !inside;
+        lim = inside ? rg.y : s;
+        for (uint32_t s0 = s; s0 < rg.y; s0 += blendk::kChunk) {
+            const uint32_t e0 = min(rg.y, s0 + blendk::kChunk);
+            const uint32_t cnt = e0 - s0;
+            const uint32_t off = blendk::stage_vals(S.vals, &S.bar, &S.timed_out, vals, s0, e0, phase, st);
+            if (S.timed_out) return;
+            if (tid < cnt) {
+                uint32_t m = S.vals[off + tid];
+                if (m >= M) m = 0;
+                const float4* g = reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride);
+                const float4 a = __ldg(g), b = __ldg(g + 1);
+                S.g0[tid] = a;
+                S.g1[tid] = b;
+                S.wmask[tid] = blendk::warp_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
+            }
+            __syncthreads();
+            uint32_t wcnt = 0;
+            for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
+                const uint32_t j = j0 + lane;
+                const bool mine = j < cnt && ((S.wmask[j] >> warp) & 1u);
+                const uint32_t bb = __ballot_sync(0xffffffffu, mine);
+                if (mine) S.wlist[warp][wcnt + __popc(bb & ((1u << lane) - 1u))] = (uint16_t)j;
+                wcnt += __popc(bb);
+            }
+            __syncwarp();
+            for (uint32_t i = 0; i < wcnt; ++i) {
+                if (__all_sync(0xffffffffu, done)) break;
+                const uint32_t j = S.wlist[warp][i];
+                if (done) continue;
+                const float4 g0 = S.g0[j];
+                const float4 g1 = S.g1[j];
+                const float dx = fs(g0.x, px), dy = fs(g0.y, py);
+                const float power = fs(fm(-0.5f, fa(fm(fm(g0.z, dx), dx), fm(fm(g1.x, dy), dy))),
+                                       fm(fm(g0.w, dx), dy));
+                if (power > 0.0f || power < g1.y) continue;
+                float alpha = fm(g1.z, exp_cw(power));
+                alpha = alpha < 0.99f ? alpha : 0.99f;
+                const float Tn = fm(T, fs(1.0f, alpha));
+                if (Tn < 0.0001f) {
+                    done = true;
+                    lim = s0 + j;
+                    continue;
+                }
+                T = Tn;
+            }
+            if (__syncthreads_count(done) == (int)blockDim.x) break;
+        }
+    }
+    const uint32_t wlim = __reduce_max_sync(0xffffffffu, lim);
+    if (lane == 0) B.lim[warp] = wlim;
+    __syncthreads();
     uint32_t e = B.lim[0];
 #pragma unroll
     for (int w = 1; w < 8; ++w) e = max(e, B.lim[w]);
     e = min(e, rg.y);                    // no pixel of the tile reaches past e
-    uint32_t phase = 0;
 
     float Bk[3] = {cam.bg[0] * T, cam.bg[1] * T, cam.bg[2] * T};   // colour behind, absolute
     float Tc = T;                                                    // transmittance after
@@ -642,8 +701,12 @@ void launch_backward(const DevTree& t, const DevCamera& cam, const uint2* ranges
 {
     // gsplat rows of the selected Gaussians start at zero: the blend backward adds into them
     zero_rows_kernel<<<sms * 8, 128, 0, s>>>(reinterpret_cast<float4*>(gsplat), st);
-    blend_bwd_kernel<<<cam.tiles_x * cam.tiles_y, 256, 0, s>>>(cam, ranges, vals, splat, keep, dL_drgb,
-                                                               gsplat, st);
+    if (keep)
+        blend_bwd_kernel<true><<<cam.tiles_x * cam.tiles_y, 256, 0, s>>>(cam, ranges, vals, splat, keep, dL_drgb,
+                                                                     gsplat, st);
+    else
+        blend_bwd_kernel<false><<<cam.tiles_x * cam.tiles_y, 256, 0, s>>>(cam, ranges, vals, splat, keep,
+                                                                      dL_drgb, gsplat, st);
     const ParamPtrs p{params[0], params[1], params[2], params[3], params[4], t.n};
     const GradPtrs gr{grads[0], grads[1], grads[2], grads[3], grads[4]};
     if (!accumulate) {

@@ -396,8 +396,7 @@ def tiny_camera() -> Camera:
                           256, 256, 60.0)
 
 
-def blob_tree(seed: int = 0, n_leaves: int = 1_000_000, n_blobs: int = 2000) -> Tree:
-    """1M leaves in a 500x500x50 m box drawn from 2,000 isotropic blobs, SH degree 3."""
+def _blob_leaves(seed: int, n_leaves: int, n_blobs: int):
     rng = np.random.default_rng(seed)
     lo = np.array([-250.0, -250.0, 0.0])
     hi = np.array([250.0, 250.0, 50.0])
@@ -415,7 +414,30 @@ def blob_tree(seed: int = 0, n_leaves: int = 1_000_000, n_blobs: int = 2000) -> 
     quat = _random_quats(rng, n_leaves)
     logit = rng.normal(0.0, 1.5, size=n_leaves)
     sh = _sh_leaves(rng, n_leaves, 3, 0.05)
+    return pts, logs, quat, logit, sh, rng
+
+
+def blob_tree(seed: int = 0, n_leaves: int = 1_000_000, n_blobs: int = 2000) -> Tree:
+    """1M leaves in a 500x500x50 m box drawn from 2,000 isotropic blobs, SH degree 3."""
+    pts, logs, quat, logit, sh, rng = _blob_leaves(seed, n_leaves, n_blobs)
     return build_tree(pts, logs, quat, logit, sh, 3, (2, 8), rng, name="blobs-1M")
+
+
+def blob_target_tree(seed: int = 0, perturb_seed: int = 3, sigma: float = 0.01,
+                     n_leaves: int = 1_000_000, n_blobs: int = 2000) -> Tree:
+    """The blob tree's leaves with every attribute (mean, log-scales, quaternion
+    components, opacity logit, SH coefficients) perturbed by N(0, sigma), seed
+    3, parents rebuilt by moment matching: the target of the differentiable
+    form's L2 loss."""
+    pts, logs, quat, logit, sh, rng = _blob_leaves(seed, n_leaves, n_blobs)
+    pr = np.random.default_rng(perturb_seed)
+    pts = pts + pr.normal(0.0, sigma, pts.shape)
+    logs = logs + pr.normal(0.0, sigma, logs.shape)
+    quat = quat + pr.normal(0.0, sigma, quat.shape)
+    quat /= np.linalg.norm(quat, axis=1, keepdims=True)
+    logit = logit + pr.normal(0.0, sigma, logit.shape)
+    sh = sh + pr.normal(0.0, sigma, sh.shape)
+    return build_tree(pts, logs, quat, logit, sh, 3, (2, 8), rng, name="blobs-1M-target")
 
 
 def blob_cameras(width=1920, height=1080) -> list:

@@ -10,7 +10,7 @@ import pytest
 import oracle
 from paper_2603_23891_gb300 import synth
 
-from gpu_util import dev_params, gpu_grad, grad_parity_case
+from gpu_util import GRAD_RTOL, dev_params, gpu_grad, grad_parity_case
 
 pytestmark = pytest.mark.gpu
 
@@ -107,7 +107,7 @@ def test_backward_state_and_argument_errors(renderer):
     with pytest.raises(filtergs.FgsError) as e:          # no frame since the parameters changed
         renderer.backward(dL, P)
     assert e.value.code == filtergs.FGS_ERR_STATE
-    renderer.render()                                    # rendered without KEEP: refused too
+    renderer.calibrate_view()                            # a calibration frame is not differentiable
     with pytest.raises(filtergs.FgsError) as e:
         renderer.backward(dL, P)
     assert e.value.code == filtergs.FGS_ERR_STATE
@@ -130,3 +130,66 @@ def test_blobs_1080p_sampled_pixels(renderer):
     shrink = (0.05, float(np.float32(np.log(0.05))))
     g, of, worst = grad_parity_case(renderer, tree, cam, 3.0, 21, shrink=shrink, pix=pix)
     print(f"blobs: M={g['M']} N_P={g['NP']} worst relative gradient error {max(worst.values()):.2e}")
+
+
+@pytest.mark.parametrize("seed", [0, 5])
+def test_recomputed_transmittance_equals_kept(renderer, seed):
+    """The default backward recomputes each pixel's final T and stop by a walk over its
+    tile; after a FGS_RENDER_KEEP forward it reads them.  Same gradients (up to the
+    order of the atomic additions), on a one-tile scene and a multi-tile random tree."""
+    import torch
+    if seed == 0:
+        tree, cam = synth.grad_scene(4, sh_degree=3)
+    else:
+        tree = synth.random_small_tree(seed, n_leaves=3000, branching=(2, 6), sh_degree=2,
+                                       extent=12.0, log_scale_mean=-1.0)
+        cam = synth.look_at_camera([0.0, -30.0, 14.0], [0.0, 0.0, 0.0], 160, 96, 60.0)
+    gp = oracle.GaussParams.of_tree(tree)
+    renderer.load_tree(tree)
+    renderer.set_params(tau_R=2.0, tile=(16, 16), bg=(0.2, 0.1, 0.4))
+    renderer.set_camera(cam)
+    renderer.shrink(None)
+    P = dev_params(gp)
+    renderer.update_params(P)
+    dL = torch.randn((3, cam.height, cam.width), device="cuda",
+                     generator=torch.Generator(device="cuda").manual_seed(seed))
+    renderer.render(keep=True)
+    kept = {k: v.cpu().numpy() for k, v in renderer.backward(dL, P).items()}
+    renderer.render()
+    rec = {k: v.cpu().numpy() for k, v in renderer.backward(dL, P).items()}
+    for k in oracle.GRAD_FIELDS:
+        scale = np.abs(kept[k]).max()
+        assert np.abs(rec[k] - kept[k]).max() <= 1e-5 * scale + 1e-9, k
+
+
+def test_blobs_l2_loss_against_perturbed_target(renderer):
+    """The differentiable configuration: the 1M-leaf blob tree at 1920x1080, L2 loss
+    against the image of the tree with every leaf attribute perturbed by N(0, 0.01);
+    gradient of the loss restricted to 4096 sampled pixels, every node against the
+    oracle (default backward: transmittance recomputed per tile)."""
+    import torch
+    tree, target_tree = synth.blob_tree(), synth.blob_target_tree()
+    cam = synth.blob_cameras()[0]
+    renderer.set_params(tau_R=3.0, tile=(16, 16), bg=(0.0, 0.0, 0.0))
+    renderer.set_camera(cam)
+    renderer.shrink(None)
+    renderer.load_tree(target_tree)
+    target, _, _ = renderer.render()
+    target = target.clone()
+    renderer.load_tree(tree)
+    gp = oracle.GaussParams.of_tree(tree)
+    P = dev_params(gp)
+    renderer.update_params(P)
+    rgb, _, _ = renderer.render()
+    pix = np.sort(np.random.default_rng(17).choice(cam.width * cam.height, 4096, replace=False))
+    mask = torch.zeros(cam.width * cam.height, device="cuda")
+    mask[torch.from_numpy(pix).cuda()] = 1.0
+    dL = 2.0 * (rgb - target) * mask.view(1, cam.height, cam.width)
+    G = {k: v.cpu().numpy() for k, v in renderer.backward(dL, P).items()}
+    torch.cuda.synchronize()
+    assert float((rgb - target).abs().max()) > 1e-3          # the target differs
+    of = oracle.grad_frame(tree, gp, cam, oracle.Params(tau_R=3.0), dL.cpu().numpy(), pix=pix)
+    for k in oracle.GRAD_FIELDS:
+        o = of.grads[k]
+        err = np.abs(G[k].astype(np.float64) - o).max()
+        assert err <= GRAD_RTOL * np.abs(o).max() + 1e-7, (k, err, np.abs(o).max())

@@ -96,9 +96,10 @@ def test_frozen_forward_equals_oracle_render():
     assert np.abs(fr.rgb.reshape(3, -1).T - gf.rgb).max() < 1e-6
 
 
-@pytest.mark.parametrize("seed,deg", [(0, 3), (1, 1)])
+@pytest.mark.parametrize("seed,deg", [(4, 3), (0, 3), (1, 1)])
 def test_gradient_matches_finite_differences(seed, deg):
-    """64 Gaussians at 32x32, every parameter group (SH sampled)."""
+    """64 Gaussians at 32x32, every parameter group (SH sampled); seed 4 is the
+    differentiable configuration's finite-difference scene."""
     tree, cam = synth.grad_scene(seed, sh_degree=deg)
     gp, p, dL, gf = _setup(tree, cam, seed=seed + 10)
     rel = _fd_check(gp, p, cam, gf, dL, n_per_group=256)
