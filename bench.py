@@ -216,6 +216,20 @@ def run_batched(r, torch, filtergs, args):
 
 # ----------------------------------------------------------------------------- ours
 
+def shard_poses(n_poses: int, rank: int, world: int) -> list:
+    """Views are independent: rank r renders poses r, r + world, r + 2 world, ...
+    (one pose at least).  No data crosses ranks."""
+    return [k for k in range(n_poses) if k % world == rank] or [rank % n_poses]
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The job's time for a per-rank time: the maximum over ranks."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _time_backward(r, torch, cams, poses, P, G, dL_of, keep, accumulate, flush):
     """Per pose: render (keep or not), the loss gradient, the backward; CUDA
     events around the render and around the backward.  Returns mean ms."""
@@ -339,7 +353,7 @@ def run_ours(args):
     log(f"[rank {rank}] workload {tree.name}: {tree.n} nodes, {tree.n_leaves} leaves, "
         f"depth {tree.depth} ({time.time() - t0:.1f}s)")
     P = len(cams)
-    my_poses = [k for k in range(P) if k % world == rank] or [rank % P]
+    my_poses = shard_poses(P, rank, world)
     W, H = cams[0].width, cams[0].height
 
     r = filtergs.Renderer(device=local, tau_R=tau_R, pair_capacity=args.pair_capacity)
@@ -413,9 +427,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     stage_ms = np.array([filtergs.fgs_stage_times(r.ctx, (slot0 + k) % 256) for k in range(K)])
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, "cuda")
 
     # end-to-end through the C ABI with pinned host buffers (camera in, image out)
     rgb_h = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
@@ -432,9 +444,7 @@ def run_ours(args):
         r.render_host(rgb_h.numpy(), T_h.numpy())
     e2e_s = time.perf_counter() - e0
     if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist, "cuda")
 
     # traversal-free filter vs the serial level-by-level baseline (Eq. 3 / Table 2),
     # same poses, wall time of each call on an idle stream
