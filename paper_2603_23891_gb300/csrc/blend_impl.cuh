@@ -226,33 +226,35 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
                 ++c_entries;
                 c_evals += __popc(__ballot_sync(0xffffffffu, !done));
             }
-            if (!done) {
-                const float4 g0 = S.g0[j];
-                const float4 g1 = S.g1[j];
-                const float dx = fs(g0.x, px);
-                const float dy = fs(g0.y, py);
-                const float p1 = fm(fm(g0.z, dx), dx);
-                const float p2 = fm(fm(g1.x, dy), dy);
-                const float p3 = fm(fm(g0.w, dx), dy);
-                const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
-                if (!(power > 0.0f || power < g1.y)) {
-                    if (kCount) ++c_hits;
-                    float alpha = fm(g1.z, exp_cw(power));
-                    alpha = alpha < 0.99f ? alpha : 0.99f;
-                    const float Tn = fm(T, fs(1.0f, alpha));
-                    if (Tn < 0.0001f) {
-                        done = true;            // stop before adding this Gaussian
-                        if (kKeep)
-                            keep_out[(size_t)y * cam.width + x] = make_uint2(__float_as_uint(T), s0 + j);
-                    } else {
-                        const float4 g2 = S.g2[j];
-                        w = alpha * T;
-                        Cacc.x = fmaf(g2.x, w, Cacc.x);
-                        Cacc.y = fmaf(g2.y, w, Cacc.y);
-                        Cacc.z = fmaf(g2.z, w, Cacc.z);
-                        T = Tn;
-                    }
-                }
+            // Branch-free evaluation: every lane computes power; if any lane of
+            // the warp can apply the Gaussian, all compute alpha and T' and the
+            // outcome is selected per lane.  Lanes that apply it take exactly
+            // the operations of the branching form, so decisions are unchanged.
+            const float4 g0 = S.g0[j];
+            const float4 g1 = S.g1[j];
+            const float dx = fs(g0.x, px);
+            const float dy = fs(g0.y, py);
+            const float p1 = fm(fm(g0.z, dx), dx);
+            const float p2 = fm(fm(g1.x, dy), dy);
+            const float p3 = fm(fm(g0.w, dx), dy);
+            const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
+            const bool hit = !done && !(power > 0.0f || power < g1.y);
+            if (__any_sync(0xffffffffu, hit)) {
+                if (kCount) c_hits += hit ? 1u : 0u;
+                float alpha = fm(g1.z, exp_cw(fminf(power, 0.0f)));
+                alpha = alpha < 0.99f ? alpha : 0.99f;
+                const float Tn = fm(T, fs(1.0f, alpha));
+                const bool stop = hit && Tn < 0.0001f;     // stop before adding this Gaussian
+                const bool apply = hit && !stop;
+                if (kKeep && stop)
+                    keep_out[(size_t)y * cam.width + x] = make_uint2(__float_as_uint(T), s0 + j);
+                const float4 g2 = S.g2[j];
+                w = apply ? alpha * T : 0.0f;
+                Cacc.x = fmaf(g2.x, w, Cacc.x);
+                Cacc.y = fmaf(g2.y, w, Cacc.y);
+                Cacc.z = fmaf(g2.z, w, Cacc.z);
+                T = apply ? Tn : T;
+                done = done || stop;
             }
             if (kKpc) {
                 // Eq. 5: sum of alpha * T over the warp's pixels for this pair
