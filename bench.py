@@ -465,12 +465,13 @@ def run_ours(args):
                 filt_lw.append((t2 - t1) * 1e3)
 
     # blend work counters (one counting frame per pose, outside the timed region)
-    cnt_evals, cnt_hits, cnt_entries = [], [], []
+    cnt_evals, cnt_hits, cnt_entries, cnt_active = [], [], [], []
     for k in my_poses:
         r.set_camera(cams[k])
         _, _, st = r.render(rgb, Tt, count=True)
         cnt_evals.append(st.blend_evals)
         cnt_hits.append(st.blend_hits)
+        cnt_active.append(st.blend_active)
         cnt_entries.append(st.blend_entries)
 
     batched = None
@@ -563,7 +564,8 @@ def run_ours(args):
             "gpu_launches": int(K * launches),
             "blend_work_per_frame": {"entries": round(float(np.mean(cnt_entries))),
                                      "evaluations": round(float(np.mean(cnt_evals))),
-                                     "alpha_applied": round(float(np.mean(cnt_hits)))},
+                                     "alpha_applied": round(float(np.mean(cnt_hits))),
+                                     "entries_with_alpha": round(float(np.mean(cnt_active)))},
             "filter_vs_levelwise": {
                 "parallel_ms": round(float(np.median(filt_par)), 4),
                 "levelwise_ms": round(float(np.median(filt_lw)), 4),

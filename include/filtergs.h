@@ -129,6 +129,7 @@ typedef struct fgs_stats {
     uint64_t blend_entries;   /* FGS_RENDER_COUNT: per-warp list entries the blend walked */
     uint64_t blend_evals;     /* FGS_RENDER_COUNT: pixel-Gaussian evaluations (pixels not stopped) */
     uint64_t blend_hits;      /* FGS_RENDER_COUNT: evaluations that reached alpha / T (exp taken) */
+    uint64_t blend_active;    /* FGS_RENDER_COUNT: warp-list entries where some pixel reached it */
 } fgs_stats;
 
 /* Library version (FGS_VERSION). */

@@ -817,6 +817,7 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
             st->blend_entries = c->st_host->blend_entries;
             st->blend_evals = c->st_host->blend_evals;
             st->blend_hits = c->st_host->blend_hits;
+            st->blend_active = c->st_host->blend_active;
         }
         if ((r = latched_status(c))) {
             clear_status(c, s);

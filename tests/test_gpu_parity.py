@@ -280,6 +280,9 @@ def test_blend_counters_consistent(renderer, tiny):
     assert st1.n_pairs == st0.n_pairs
     assert 0 < st1.blend_hits <= st1.blend_evals <= 32 * st1.blend_entries
     assert st1.blend_entries <= 8 * st1.n_pairs
+    # every entry where some pixel applies alpha has at least one such pixel
+    assert st1.blend_active <= st1.blend_hits <= 32 * st1.blend_active
+    assert st1.blend_active <= st1.blend_entries
 
 
 def test_crowded_tiles_sorted_in_global_memory(renderer):
