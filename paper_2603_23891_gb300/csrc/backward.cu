@@ -264,22 +264,21 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
             for (uint32_t i = 0; i < wcnt; ++i) {
                 if (__all_sync(0xffffffffu, done)) break;
                 const uint32_t j = S.wlist[warp][i];
-                if (done) continue;
+                // branch-free as in the forward: same operations for the lanes that apply it
                 const float4 g0 = S.g0[j];
                 const float4 g1 = S.g1[j];
                 const float dx = fs(g0.x, px), dy = fs(g0.y, py);
                 const float power = fs(fm(-0.5f, fa(fm(fm(g0.z, dx), dx), fm(fm(g1.x, dy), dy))),
                                        fm(fm(g0.w, dx), dy));
-                if (power > 0.0f || power < g1.y) continue;
-                float alpha = fm(g1.z, exp_cw(power));
+                const bool hit = !done && !(power > 0.0f || power < g1.y);
+                if (!__any_sync(0xffffffffu, hit)) continue;
+                float alpha = fm(g1.z, exp_cw(fminf(power, 0.0f)));
                 alpha = alpha < 0.99f ? alpha : 0.99f;
                 const float Tn = fm(T, fs(1.0f, alpha));
-                if (Tn < 0.0001f) {
-                    done = true;
-                    lim = s0 + j;
-                    continue;
-                }
-                T = Tn;
+                const bool stop = hit && Tn < 0.0001f;
+                lim = stop ? s0 + j : lim;
+                T = (hit && !stop) ? Tn : T;
+                done = done || stop;
             }
             if (__syncthreads_count(done) == (int)blockDim.x) break;
         }
@@ -325,49 +324,43 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
         __syncwarp();
         for (int i = (int)wcnt - 1; i >= 0; --i) {
             const uint32_t j = S.wlist[warp][i];
-            float g[9] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            bool any = false;
-            if (s0 + j < lim) {
-                const float4 g0 = S.g0[j];
-                const float4 g1 = S.g1[j];
-                const float dx = fs(g0.x, px), dy = fs(g0.y, py);
-                const float power = fs(fm(-0.5f, fa(fm(fm(g0.z, dx), dx), fm(fm(g1.x, dy), dy))),
-                                       fm(fm(g0.w, dx), dy));
-                if (!(power > 0.0f || power < g1.y)) {
-                    const float ex = exp_cw(power);
-                    const float raw = fm(g1.z, ex);
-                    const bool clamped = !(raw < 0.99f);
-                    const float alpha = clamped ? 0.99f : raw;
-                    const float4 g2 = S.g2[j];
-                    const float iom = __frcp_rn(1.0f - alpha);     // decides nothing
-                    const float Tb = Tc * iom;                      // transmittance before
-                    const float w = alpha * Tb;
-                    const float galpha = dC[0] * (g2.x * Tb - Bk[0] * iom) +
-                                         dC[1] * (g2.y * Tb - Bk[1] * iom) +
-                                         dC[2] * (g2.z * Tb - Bk[2] * iom);
-                    Bk[0] += g2.x * w;
-                    Bk[1] += g2.y * w;
-                    Bk[2] += g2.z * w;
-                    g[6] = w * dC[0];
-                    g[7] = w * dC[1];
-                    g[8] = w * dC[2];
-                    Tc = Tb;
-                    if (!clamped) {
-                        const float gpow = galpha * alpha;         // d alpha / d power = alpha
-                        g[5] = galpha * ex;                        // d alpha / d alpha0 = e^power
-                        g[2] = -0.5f * dx * dx * gpow;             // A
-                        g[3] = -dx * dy * gpow;                    // B
-                        g[4] = -0.5f * dy * dy * gpow;             // C
-                        g[0] = -gpow * (g0.z * dx + g0.w * dy);    // u
-                        g[1] = -gpow * (g1.x * dy + g0.w * dx);    // v
-                    }
-                    any = true;
-                }
-            }
-            if (__any_sync(0xffffffffu, any)) {
-                const float v = warp_reduce9(g, lane);
-                if (comp >= 0) atomicAdd(gsplat + (size_t)B.m[j] * kGS + comp, v);
-            }
+            // branch-free: every lane evaluates; the lanes whose pixel applied the
+            // Gaussian in the forward (same decisions) contribute, the others add 0
+            const float4 g0 = S.g0[j];
+            const float4 g1 = S.g1[j];
+            const float dx = fs(g0.x, px), dy = fs(g0.y, py);
+            const float power = fs(fm(-0.5f, fa(fm(fm(g0.z, dx), dx), fm(fm(g1.x, dy), dy))),
+                                   fm(fm(g0.w, dx), dy));
+            const bool hit = s0 + j < lim && !(power > 0.0f || power < g1.y);
+            if (!__any_sync(0xffffffffu, hit)) continue;
+            const float ex = exp_cw(fminf(power, 0.0f));
+            const float raw = fm(g1.z, ex);
+            const bool clamped = !(raw < 0.99f);
+            const float alpha = hit ? (clamped ? 0.99f : raw) : 0.0f;
+            const float4 g2 = S.g2[j];
+            const float iom = __frcp_rn(1.0f - alpha);              // decides nothing
+            const float Tb = Tc * iom;                               // transmittance before
+            const float w = alpha * Tb;
+            const float galpha = hit ? dC[0] * (g2.x * Tb - Bk[0] * iom) + dC[1] * (g2.y * Tb - Bk[1] * iom) +
+                                       dC[2] * (g2.z * Tb - Bk[2] * iom)
+                                     : 0.0f;
+            Bk[0] += g2.x * w;
+            Bk[1] += g2.y * w;
+            Bk[2] += g2.z * w;
+            Tc = Tb;
+            float g[9];
+            g[6] = w * dC[0];
+            g[7] = w * dC[1];
+            g[8] = w * dC[2];
+            const float gpow = clamped ? 0.0f : galpha * alpha;     // d alpha / d power = alpha
+            g[5] = clamped ? 0.0f : galpha * ex;                   // d alpha / d alpha0 = e^power
+            g[2] = -0.5f * dx * dx * gpow;                         // A
+            g[3] = -dx * dy * gpow;                                // B
+            g[4] = -0.5f * dy * dy * gpow;                         // C
+            g[0] = -gpow * (g0.z * dx + g0.w * dy);                // u
+            g[1] = -gpow * (g1.x * dy + g0.w * dx);                // v
+            const float v = warp_reduce9(g, lane);
+            if (comp >= 0) atomicAdd(gsplat + (size_t)B.m[j] * kGS + comp, v);
         }
         __syncthreads();
     }
