@@ -53,6 +53,13 @@ __global__ void __launch_bounds__(256) filter_pred_kernel(DevTree t, DevCamera c
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_chunks; i += stride) {
         const uint32_t n0 = i << 2;
+        if (i + stride < n_chunks) {
+            // next chunk's centres (and covariances) into L2 while this one computes
+            const float* nx = t.mu + ((size_t)(i + stride) << 2);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(nx));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + t.n_pad));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 2 * (size_t)t.n_pad));
+        }
         const float4 mx = __ldg(reinterpret_cast<const float4*>(t.mu) + i);
         const float4 my = __ldg(reinterpret_cast<const float4*>(t.mu + t.n_pad) + i);
         const float4 mz = __ldg(reinterpret_cast<const float4*>(t.mu + 2 * (size_t)t.n_pad) + i);

@@ -316,3 +316,29 @@ def test_large_tile_grid_uses_radix_sort(renderer):
     grgb = g["rgb"].reshape(3, -1)[:, pix].T.astype(np.float64)
     assert np.abs(grgb - rgb).max() <= IMG_TOL
     assert np.array_equal(g["T"].reshape(-1)[pix].view(np.uint32), T.view(np.uint32))
+
+
+def test_tiny_tree_thousand_random_cameras(renderer, tiny):
+    """The tiny LoD tree (4,096 leaves, LoD threshold 1 px) from 1,000 random 256x256
+    cameras (positions over and around the box, random targets and FOVs, some looking
+    away): selection, pair list and transmittance bit for bit, images within 2e-3 and
+    60 dB, for every camera."""
+    import time
+    tree, _ = tiny
+    renderer.load_tree(tree)
+    rng = np.random.default_rng(1)
+    t0 = time.time()
+    worst = 0.0
+    n_empty = 0
+    for k in range(1000):
+        pos = rng.uniform([-80.0, -80.0, 2.0], [80.0, 80.0, 90.0])
+        target = rng.uniform([-32.0, -32.0, -4.0], [32.0, 32.0, 4.0])
+        if k % 10 == 9:                                   # some cameras face away from the box
+            target = pos + (pos - target)
+        cam = synth.look_at_camera(pos, target, 256, 256, rng.uniform(30.0, 100.0))
+        g = gpu_frame(renderer, tree, cam, 1.0)
+        o, _ = oracle_frame(tree, cam, 1.0)
+        worst = max(worst, assert_frame_parity(g, o))
+        n_empty += len(o.sel) == 0
+    print(f"1000 cameras: worst max-abs {worst:.2e}, {n_empty} empty views, {time.time() - t0:.1f}s")
+    assert n_empty < 1000
