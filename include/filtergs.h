@@ -230,7 +230,9 @@ int fgs_get_pairs(fgs_ctx* ctx, void* stream, uint64_t* keys_out, uint32_t* vals
 /* Copy the projected splats of the last frame: float [M][12] rows of
  * u, v, conic A, B, C, ln-threshold, alpha_0, depth, r, g, b, footprint
  * radius (0 when the Gaussian is dropped by shrinking or has a singular
- * conic; conic 0 in the latter case), in selection order.
+ * conic; conic 0 in the latter case), in selection order.  r, g, b are
+ * evaluated only for Gaussians that emit at least one pair (0 otherwise:
+ * no pixel reads them).
  * *M_out = M.  Errors as fgs_get_pairs. */
 int fgs_get_splats(fgs_ctx* ctx, void* stream, float* out, uint32_t cap, uint32_t* M_out,
                    int out_is_device);

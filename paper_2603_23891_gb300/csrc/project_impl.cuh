@@ -139,12 +139,16 @@ __device__ __forceinline__ uint32_t project_one(const DevTree& t, const DevCamer
     }
     foot[m] = make_uint4((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16),
                          cnt, __float_as_uint(vz));
-    // ---- colour (FMA allowed: decides nothing)
-    float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
-    const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-    dx *= il; dy *= il; dz *= il;
-    float rgb[3];
-    sh_colour(t.sh + (size_t)n * t.sh_stride, (int)t.sh_degree, dx, dy, dz, rgb);
+    // ---- colour (FMA allowed: decides nothing), only for a Gaussian that emits
+    // pairs: no pixel ever reads the colour of one that does not (about 40% of
+    // the selection under shrinking), so its SH row is not fetched
+    float rgb[3] = {0.0f, 0.0f, 0.0f};
+    if (cnt) {
+        float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
+        const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= il; dy *= il; dz *= il;
+        sh_colour(t.sh + (size_t)n * t.sh_stride, (int)t.sh_degree, dx, dy, dz, rgb);
+    }
     float4* out = reinterpret_cast<float4*>(splat + (size_t)m * kSplatStride);
     out[0] = make_float4(u, v, A, B);
     out[1] = make_float4(C, lthr, a0, vz);
