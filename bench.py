@@ -131,8 +131,10 @@ def blend_alu_peak(sm_mhz, sms):
     return 128.0 * sms * sm_mhz * 1e6
 
 
-OPS_PER_EVAL = 11.0   # dx, dy, 3 x 2 products, sum, scale, subtract
-OPS_PER_HIT = 29.0    # exp (21), alpha and clamp (2), 1 - alpha and T (2), weight + 3 colour FMAs (4)
+# FP32 lane operations of Eq. 2 with the 3DGS rules, as the blend computes them
+OPS_PER_EVAL = 13.0   # dx, dy, 3 x 2 products, sum, scale, subtract, the two skip tests
+OPS_PER_HIT = 31.0    # exp (22: range test, reduction 6, degree-7 Horner 14, scaling), alpha,
+                      # clamp, 1 - alpha, T update, stop test, weight, 3 colour FMAs
 
 
 def _kernel_sources_sha(kernel):
@@ -534,8 +536,9 @@ def run_ours(args):
                       "peak": round(peak_tf, 3), "unit": "TFLOP/s", "frac": round(ach_tf / peak_tf, 4),
                       "traffic": profiled_traffic("blend_kernel"),
                       "peak_source": f"derived: 128 FP32 lanes x {sms} SMs x {clk_mhz:.0f} MHz",
-                      "ops": "FP32 lane operations: 11 per pixel-Gaussian evaluation (power and tests), "
-                             "29 more per evaluation that applies alpha (exp, alpha, T, colour)",
+                      "ops": "FP32 lane operations: 13 per pixel-Gaussian evaluation (offsets, power, "
+                             "the two skip tests), 31 more per evaluation that applies alpha (exp, alpha, "
+                             "clamp, T, stop test, colour)",
                       "hbm_view": {"achieved": stages[dom]["GB/s"], "peak": hbm_peak, "unit": "GB/s",
                                    "frac": stages[dom]["frac_hbm"]}}
         else:
