@@ -111,15 +111,16 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- roofline
 
-def algorithmic_bytes(tree, M, NP, width, height, sh_floats):
-    """Bytes the method must move per frame, per stage (documented in the design doc)."""
+def algorithmic_bytes(tree, M, NP, width, height, sh_floats, E):
+    """Bytes the method must move per frame, per stage (E: selected Gaussians that
+    emit pairs, the only ones whose SH colour is evaluated)."""
     N = tree.n
     n_int = N - tree.n_leaves
     D = tree.depth
     return {
         "filter_rl": 12.0 * N + 24.0 * n_int + N / 8.0 + N / 8.0,
         "ancestor_compact": N / 8.0 + 4.0 * D * M + 4.0 * M,
-        "project_keys": M * (4 + 12 + 24 + 8 + 4 * sh_floats + 48) + 12.0 * NP,
+        "project_keys": M * (4 + 12 + 24 + 8 + 48) + E * 4 * sh_floats + 12.0 * NP,
         "sort": NP * (8.0 + 6 * 24.0),
         "tile_ranges": 8.0 * NP,
         "blend": NP * (4.0 + 48.0) + 16.0 * width * height,
@@ -375,12 +376,13 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     # per-pose statistics (M, N_P), also checks device status
-    Ms, NPs = [], []
+    Ms, NPs, Es = [], [], []
     for k in my_poses:
         r.set_camera(cams[k])
         _, _, st = r.render(rgb, Tt, stats=True)
         Ms.append(st.n_selected)
         NPs.append(st.n_pairs)
+        Es.append(st.n_emitting)
         launches = st.n_launches
     # shrink-off pair counts for context
     r.shrink(None)
@@ -513,7 +515,8 @@ def run_ours(args):
         M_mean = float(np.mean(Ms))
         NP_mean = float(np.mean(NPs))
         sh_floats = (tree.sh_degree + 1) ** 2 * 3
-        ab = algorithmic_bytes(tree, M_mean, NP_mean, W, H, sh_floats)
+        E_mean = float(np.mean(Es))
+        ab = algorithmic_bytes(tree, M_mean, NP_mean, W, H, sh_floats, E_mean)
         st_mean = stage_ms.mean(axis=0)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -555,7 +558,8 @@ def run_ours(args):
             "config": {"workload": wname, "n_nodes": tree.n, "n_leaves": tree.n_leaves,
                        "depth": tree.depth, "resolution": f"{W}x{H}", "poses": P,
                        "tau_R": tau_R, "lambda_G": args.lambda_g, "tau": tau,
-                       "M_mean": round(M_mean, 1), "N_P_mean": round(NP_mean, 1),
+                       "M_mean": round(M_mean, 1), "emitting_mean": round(E_mean, 1),
+                       "N_P_mean": round(NP_mean, 1),
                        "N_P_mean_shrink_off": round(float(np.mean(NP_off)), 1),
                        "l2": "flushed between steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world} (views round-robin)"},

@@ -122,7 +122,7 @@ typedef struct fgs_params {
 
 typedef struct fgs_stats {
     uint32_t n_selected;      /* M: nodes in the LoD cut */
-    uint32_t reserved;
+    uint32_t n_emitting;      /* selected Gaussians with at least one pair (fgs_render) */
     uint64_t n_pairs;         /* N_P: Gaussian-tile pairs (may exceed capacity on error) */
     uint32_t n_launches;      /* kernels this call enqueued */
     int32_t device_status;    /* latched device status (FGS_OK if none) */

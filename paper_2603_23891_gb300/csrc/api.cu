@@ -818,6 +818,7 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
             st->blend_evals = c->st_host->blend_evals;
             st->blend_hits = c->st_host->blend_hits;
             st->blend_active = c->st_host->blend_active;
+            st->n_emitting = c->st_host->n_emitting;
         }
         if ((r = latched_status(c))) {
             clear_status(c, s);

@@ -82,6 +82,7 @@ struct FrameState {
     unsigned long long blend_evals;       // pixel-Gaussian evaluations (lanes not yet stopped)
     unsigned long long blend_hits;        // evaluations that reached the alpha / T update
     unsigned long long blend_active;      // warp-list entries where some lane reached it
+    uint32_t n_emitting;                  // selected Gaussians with at least one pair
 
 };
 

@@ -27,6 +27,7 @@ __global__ void frame_begin_kernel(FrameState* st, uint2* ranges, int n_tiles)
         st->blend_evals = 0;
         st->blend_hits = 0;
         st->blend_active = 0;
+        st->n_emitting = 0;
     }
     if (tid < 16) st->tickets[tid] = 0;
     for (int i = tid; i < kMaxSortPasses * 256; i += gridDim.x * blockDim.x)

@@ -30,6 +30,8 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(
         const uint32_t m = tile * kProjThreads + tid;
         uint32_t cnt = 0;
         if (m < M) cnt = proj::project_one(t, cam, __ldg(sel + m), m, splat, foot);
+        const uint32_t emitting = __popc(__ballot_sync(0xffffffffu, cnt > 0));
+        if (lane == 0 && emitting) atomicAdd(&st->n_emitting, emitting);
         const uint32_t wsum = warp_sum_u32(cnt);
         if (lane == 0) s_warp_tot[warp] = wsum;
         __syncthreads();

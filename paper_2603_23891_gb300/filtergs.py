@@ -82,7 +82,7 @@ class fgs_gauss_grads(C.Structure):
 
 
 class fgs_stats(C.Structure):
-    _fields_ = [("n_selected", C.c_uint32), ("reserved", C.c_uint32), ("n_pairs", C.c_uint64),
+    _fields_ = [("n_selected", C.c_uint32), ("n_emitting", C.c_uint32), ("n_pairs", C.c_uint64),
                 ("n_launches", C.c_uint32), ("device_status", C.c_int32),
                 ("blend_entries", C.c_uint64), ("blend_evals", C.c_uint64), ("blend_hits", C.c_uint64),
                 ("blend_active", C.c_uint64)]

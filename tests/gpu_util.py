@@ -33,7 +33,7 @@ def gpu_frame(r, tree_loaded, cam, tau_R, shrink=None, tile=(16, 16), bg=(0, 0, 
     keys, vals = r.pairs()
     spl = r.splats()
     out = dict(rgb=rgb.cpu().numpy(), T=T.cpu().numpy(), keys=keys, vals=vals, splat=spl,
-               M=int(st.n_selected), NP=int(st.n_pairs))
+               M=int(st.n_selected), NP=int(st.n_pairs), E=int(st.n_emitting))
     out["sel"] = r.filter()
     return out
 
@@ -49,6 +49,9 @@ def assert_frame_parity(g, o, check_image=True):
     assert np.array_equal(g["sel"], o.sel), f"selection differs ({len(g['sel'])} vs {len(o.sel)})"
     assert g["M"] == len(o.sel)
     assert g["NP"] == len(o.keys)
+    if "E" in g:
+        rect = o.rect
+        assert g["E"] == int(np.count_nonzero((rect[:, 1] > rect[:, 0]) & (rect[:, 3] > rect[:, 2])))
     assert g["splat"].shape == o.splat.shape
     if len(o.sel):
         ge = g["splat"][:, EXACT_FIELDS].view(np.uint32)
