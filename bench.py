@@ -6,16 +6,20 @@ blending) for one camera pose of the synthetic workload, inputs resident in HBM.
 
 Default workload: the 10M-leaf city tree (~12.5M nodes), 1920x1080, 64-pose
 flythrough, adaptive shrinking with tau calibrated over the 64 poses
-(lambda_G = 0.2).  Prints ONE JSON line on rank 0.
+(lambda_G = 0.2).  Prints ONE JSON line on rank 0.  Beside the headline the
+line carries the per-stage times and bandwidths, the blend's ALU roofline, the
+end-to-end rate through the C ABI with host buffers, the blend work counters,
+the traversal-free filter against the level-by-level baseline, the batched
+32-view form, the shrinking study and the differentiable form's backward.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload city|blobs|tiny]
-                  [--impl ours|reference] [--no-cpu-baseline]
+                  [--impl ours|reference] [--no-cpu-baseline] [--no-batch]
+                  [--no-study] [--no-backward]
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess

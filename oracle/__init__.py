@@ -27,7 +27,7 @@ import ctypes as C
 import math
 import os
 import subprocess
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 

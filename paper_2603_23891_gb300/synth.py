@@ -23,7 +23,7 @@ smaller id than its descendants; this mirrors the node indexing N_{i,j} of §3.2
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 import math
 
 import numpy as np
