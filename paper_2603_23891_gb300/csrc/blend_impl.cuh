@@ -219,52 +219,122 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
         }
         __syncwarp();
         uint32_t c_entries = 0, c_evals = 0, c_hits = 0, c_active = 0;
-        for (uint32_t i = 0; i < wcnt; ++i) {
-            if (!kKpc && __all_sync(0xffffffffu, done)) break;
-            const uint32_t j = S.wlist[warp][i];
-            float w = 0.0f;
-            if (kCount) {
-                ++c_entries;
-                c_evals += __popc(__ballot_sync(0xffffffffu, !done));
-            }
-            // Branch-free evaluation: every lane computes power; if any lane of
-            // the warp can apply the Gaussian, all compute alpha and T' and the
-            // outcome is selected per lane.  Lanes that apply it take exactly
-            // the operations of the branching form, so decisions are unchanged.
-            const float4 g0 = S.g0[j];
-            const float4 g1 = S.g1[j];
-            const float dx = fs(g0.x, px);
-            const float dy = fs(g0.y, py);
-            const float p1 = fm(fm(g0.z, dx), dx);
-            const float p2 = fm(fm(g1.x, dy), dy);
-            const float p3 = fm(fm(g0.w, dx), dy);
-            const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
-            const bool hit = !done && !(power > 0.0f || power < g1.y);
-            if (__any_sync(0xffffffffu, hit)) {
+        if (kKpc) {
+            // the KPC pass reduces alpha * T per entry across the warp: one entry at a time
+            for (uint32_t i = 0; i < wcnt; ++i) {
+                const uint32_t j = S.wlist[warp][i];
+                float w = 0.0f;
                 if (kCount) {
-                    c_hits += hit ? 1u : 0u;
-                    ++c_active;
+                    ++c_entries;
+                    c_evals += __popc(__ballot_sync(0xffffffffu, !done));
                 }
-                float alpha = fm(g1.z, exp_cw(fminf(power, 0.0f)));
-                alpha = alpha < 0.99f ? alpha : 0.99f;
-                const float Tn = fm(T, fs(1.0f, alpha));
-                const bool stop = hit && Tn < 0.0001f;     // stop before adding this Gaussian
-                const bool apply = hit && !stop;
-                if (kKeep && stop)
-                    keep_out[(size_t)y * cam.width + x] = make_uint2(__float_as_uint(T), s0 + j);
-                const float4 g2 = S.g2[j];
-                w = apply ? alpha * T : 0.0f;
-                Cacc.x = fmaf(g2.x, w, Cacc.x);
-                Cacc.y = fmaf(g2.y, w, Cacc.y);
-                Cacc.z = fmaf(g2.z, w, Cacc.z);
-                T = apply ? Tn : T;
-                done = done || stop;
+                // Branch-free evaluation: every lane computes power; if any lane of
+                // the warp can apply the Gaussian, all compute alpha and T' and the
+                // outcome is selected per lane.
+                const float4 g0 = S.g0[j];
+                const float4 g1 = S.g1[j];
+                const float dx = fs(g0.x, px);
+                const float dy = fs(g0.y, py);
+                const float p1 = fm(fm(g0.z, dx), dx);
+                const float p2 = fm(fm(g1.x, dy), dy);
+                const float p3 = fm(fm(g0.w, dx), dy);
+                const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
+                const bool hit = !done && !(power > 0.0f || power < g1.y);
+                if (__any_sync(0xffffffffu, hit)) {
+                    if (kCount) {
+                        c_hits += hit ? 1u : 0u;
+                        ++c_active;
+                    }
+                    float alpha = fm(g1.z, exp_cw(fminf(power, 0.0f)));
+                    alpha = alpha < 0.99f ? alpha : 0.99f;
+                    const float Tn = fm(T, fs(1.0f, alpha));
+                    const bool stop = hit && Tn < 0.0001f;     // stop before adding this Gaussian
+                    const bool apply = hit && !stop;
+                    if (kKeep && stop)
+                        keep_out[(size_t)y * cam.width + x] = make_uint2(__float_as_uint(T), s0 + j);
+                    const float4 g2 = S.g2[j];
+                    w = apply ? alpha * T : 0.0f;
+                    Cacc.x = fmaf(g2.x, w, Cacc.x);
+                    Cacc.y = fmaf(g2.y, w, Cacc.y);
+                    Cacc.z = fmaf(g2.z, w, Cacc.z);
+                    T = apply ? Tn : T;
+                    done = done || stop;
+                }
+                if (kKpc) {
+                    // Eq. 5: sum of alpha * T over the warp's pixels for this pair
+    #pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                    if (lane == 0) S.kpc_w[warp][j] = w;
+                }
             }
-            if (kKpc) {
-                // Eq. 5: sum of alpha * T over the warp's pixels for this pair
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-                if (lane == 0) S.kpc_w[warp][j] = w;
+        } else {
+            // Groups of 32 list entries.  Phase 1, in lockstep: every lane tests
+            // every entry of the group and keeps a bit per entry it applies.
+            // Phase 2: every lane applies its own entries in list order, the
+            // lanes of the warp working on different entries at once, so the
+            // alpha / T / colour work is spent only on pixels that apply.  A
+            // lane that stops drops its remaining bits.  Each lane performs
+            // exactly the operations of the one-entry-at-a-time walk, in the
+            // same order, so every decision is unchanged.
+            for (uint32_t i0 = 0; i0 < wcnt; i0 += 32) {
+                if (__all_sync(0xffffffffu, done)) break;
+                const uint32_t ng = min(32u, wcnt - i0);
+                const bool done0 = done;
+                uint32_t hits = 0;
+                for (uint32_t e = 0; e < ng; ++e) {
+                    const uint32_t j = S.wlist[warp][i0 + e];
+                    const float4 g0 = S.g0[j];
+                    const float4 g1 = S.g1[j];
+                    const float dx = fs(g0.x, px);
+                    const float dy = fs(g0.y, py);
+                    const float p1 = fm(fm(g0.z, dx), dx);
+                    const float p2 = fm(fm(g1.x, dy), dy);
+                    const float p3 = fm(fm(g0.w, dx), dy);
+                    const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
+                    hits |= (uint32_t)(!done && !(power > 0.0f || power < g1.y)) << e;
+                }
+                uint32_t proc = 0, n_eval = ng;
+                while (__any_sync(0xffffffffu, hits != 0u)) {
+                    if (hits) {
+                        const uint32_t e = __ffs(hits) - 1;
+                        hits &= hits - 1u;
+                        const uint32_t j = S.wlist[warp][i0 + e];
+                        const float4 g0 = S.g0[j];
+                        const float4 g1 = S.g1[j];
+                        const float dx = fs(g0.x, px);
+                        const float dy = fs(g0.y, py);
+                        const float p1 = fm(fm(g0.z, dx), dx);
+                        const float p2 = fm(fm(g1.x, dy), dy);
+                        const float p3 = fm(fm(g0.w, dx), dy);
+                        const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
+                        float alpha = fm(g1.z, exp_cw(power));
+                        alpha = alpha < 0.99f ? alpha : 0.99f;
+                        const float Tn = fm(T, fs(1.0f, alpha));
+                        if (kCount) {
+                            ++c_hits;
+                            proc |= 1u << e;
+                        }
+                        if (Tn < 0.0001f) {
+                            done = true;                    // stop before adding this Gaussian
+                            hits = 0;
+                            n_eval = e + 1;
+                            if (kKeep)
+                                keep_out[(size_t)y * cam.width + x] = make_uint2(__float_as_uint(T), s0 + j);
+                        } else {
+                            const float4 g2 = S.g2[j];
+                            const float w = alpha * T;
+                            Cacc.x = fmaf(g2.x, w, Cacc.x);
+                            Cacc.y = fmaf(g2.y, w, Cacc.y);
+                            Cacc.z = fmaf(g2.z, w, Cacc.z);
+                            T = Tn;
+                        }
+                    }
+                }
+                if (kCount) {
+                    c_entries += ng;
+                    c_evals += warp_sum_u32(done0 ? 0u : n_eval);
+                    c_active += __popc(__reduce_or_sync(0xffffffffu, proc));
+                }
             }
         }
         if (kCount) {
