@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(256) bblend_kernel(const DevCamera* __restrict
                                                      FrameState* st)
 {
     __shared__ __align__(128) blendk::BlendSmem<false> S;
+    __shared__ __align__(16) blendk::GroupSmem<true> Gs;
     __shared__ double s_red[8];
     __shared__ DevCamera s_cam;
     const uint32_t gtile = blockIdx.x;
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(256) bblend_kernel(const DevCamera* __restrict
         reinterpret_cast<uint32_t*>(&s_cam)[i] = reinterpret_cast<const uint32_t*>(cams + v)[i];
     __syncthreads();
     const unsigned long long o = __ldg(img_off + v);
-    blendk::blend_tile<false>(s_cam, gtile - __ldg(tile_base + v), gtile, S, s_red, ranges, vals, splat,
+    blendk::blend_tile<false>(s_cam, gtile - __ldg(tile_base + v), gtile, S, Gs, s_red, ranges, vals, splat,
                               rgb + 3 * o, Tout ? Tout + o : nullptr, nullptr, nullptr, nullptr, st);
 }
 

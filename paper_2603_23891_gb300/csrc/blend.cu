@@ -32,10 +32,11 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
                                                     float* __restrict__ G_out, FrameState* st)
 {
     __shared__ __align__(128) BlendSmem<kKpc> S;
+    __shared__ __align__(16) blendk::GroupSmem<!kKpc> Gs;
     __shared__ double s_red[8];
     grid_dep_wait();
     grid_dep_trigger();
-    blendk::blend_tile<kKpc, kCount, kKeep>(cam, blockIdx.x, blockIdx.x, S, s_red, ranges, vals, splat, rgb,
+    blendk::blend_tile<kKpc, kCount, kKeep>(cam, blockIdx.x, blockIdx.x, S, Gs, s_red, ranges, vals, splat, rgb,
                                      Tout, keep, kpc_out, G_out, st);
 }
 

@@ -72,6 +72,15 @@ struct BlendSmem {
     int timed_out;
 };
 
+// Per-warp scratch of the group walk (see blend_tile): each lane's binary32
+// power for every entry of the group, and the entries' alpha0 and colour.
+constexpr int kGroup = 16;
+template <bool kUsed>
+struct GroupSmem {
+    float pw[kUsed ? 8 : 1][kUsed ? kGroup : 1][32];
+    float4 grp[kUsed ? 8 : 1][kUsed ? kGroup : 1];   // alpha0, r, g, b
+};
+
 // Bring chunk [s0, e0) of the sorted values into shared memory with one TMA bulk
 // copy of the 16-byte aligned superset [s0 & ~3, (e0 + 3) & ~3).  Returns the
 // offset of s0 inside the staged copy.  Called by all threads; thread 0 issues
@@ -159,7 +168,7 @@ __device__ __forceinline__ uint32_t warp_mask(const DevCamera& cam, int32_t tx0,
 // stop; the differentiable form's backward walks each pixel from there.
 template <bool kKpc, bool kCount = false, bool kKeep = false>
 __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, uint32_t gtile,
-                                           BlendSmem<kKpc>& S, double* s_red,
+                                           BlendSmem<kKpc>& S, GroupSmem<!kKpc>& Gs, double* s_red,
                                            const uint2* __restrict__ ranges,
                                            const uint32_t* __restrict__ vals,
                                            const float* __restrict__ splat, float* __restrict__ rgb,
@@ -268,17 +277,20 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
                 }
             }
         } else {
-            // Groups of 32 list entries.  Phase 1, in lockstep: every lane tests
-            // every entry of the group and keeps a bit per entry it applies.
-            // Phase 2: every lane applies its own entries in list order, the
-            // lanes of the warp working on different entries at once, so the
-            // alpha / T / colour work is spent only on pixels that apply.  A
-            // lane that stops drops its remaining bits.  Each lane performs
-            // exactly the operations of the one-entry-at-a-time walk, in the
-            // same order, so every decision is unchanged.
-            for (uint32_t i0 = 0; i0 < wcnt; i0 += 32) {
+            // Groups of kGroup list entries.  Phase 1, in lockstep: every lane
+            // tests every entry of the group, keeps a bit per entry it applies
+            // and parks its binary32 power in shared memory.  Phase 2: every
+            // lane applies its own entries in list order, the lanes of the warp
+            // working on different entries at once, so the alpha / T / colour
+            // work is spent only on pixels that apply.  A lane that stops drops
+            // its remaining bits.  Each lane performs exactly the operations of
+            // the one-entry-at-a-time walk, in the same order, so every
+            // decision is unchanged.
+            float (*pw)[32] = Gs.pw[warp];
+            float4* grp = Gs.grp[warp];
+            for (uint32_t i0 = 0; i0 < wcnt; i0 += kGroup) {
                 if (__all_sync(0xffffffffu, done)) break;
-                const uint32_t ng = min(32u, wcnt - i0);
+                const uint32_t ng = min((uint32_t)kGroup, wcnt - i0);
                 const bool done0 = done;
                 uint32_t hits = 0;
                 for (uint32_t e = 0; e < ng; ++e) {
@@ -291,23 +303,22 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
                     const float p2 = fm(fm(g1.x, dy), dy);
                     const float p3 = fm(fm(g0.w, dx), dy);
                     const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
+                    pw[e][lane] = power;
                     hits |= (uint32_t)(!done && !(power > 0.0f || power < g1.y)) << e;
                 }
+                if (lane < ng) {
+                    const uint32_t j = S.wlist[warp][i0 + lane];
+                    const float4 c = S.g2[j];
+                    grp[lane] = make_float4(S.g1[j].z, c.x, c.y, c.z);
+                }
+                __syncwarp();
                 uint32_t proc = 0, n_eval = ng;
                 while (__any_sync(0xffffffffu, hits != 0u)) {
                     if (hits) {
                         const uint32_t e = __ffs(hits) - 1;
                         hits &= hits - 1u;
-                        const uint32_t j = S.wlist[warp][i0 + e];
-                        const float4 g0 = S.g0[j];
-                        const float4 g1 = S.g1[j];
-                        const float dx = fs(g0.x, px);
-                        const float dy = fs(g0.y, py);
-                        const float p1 = fm(fm(g0.z, dx), dx);
-                        const float p2 = fm(fm(g1.x, dy), dy);
-                        const float p3 = fm(fm(g0.w, dx), dy);
-                        const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
-                        float alpha = fm(g1.z, exp_cw(power));
+                        const float4 q = grp[e];
+                        float alpha = fm(q.x, exp_cw(pw[e][lane]));
                         alpha = alpha < 0.99f ? alpha : 0.99f;
                         const float Tn = fm(T, fs(1.0f, alpha));
                         if (kCount) {
@@ -319,17 +330,18 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
                             hits = 0;
                             n_eval = e + 1;
                             if (kKeep)
-                                keep_out[(size_t)y * cam.width + x] = make_uint2(__float_as_uint(T), s0 + j);
+                                keep_out[(size_t)y * cam.width + x] =
+                                    make_uint2(__float_as_uint(T), s0 + S.wlist[warp][i0 + e]);
                         } else {
-                            const float4 g2 = S.g2[j];
                             const float w = alpha * T;
-                            Cacc.x = fmaf(g2.x, w, Cacc.x);
-                            Cacc.y = fmaf(g2.y, w, Cacc.y);
-                            Cacc.z = fmaf(g2.z, w, Cacc.z);
+                            Cacc.x = fmaf(q.y, w, Cacc.x);
+                            Cacc.y = fmaf(q.z, w, Cacc.y);
+                            Cacc.z = fmaf(q.w, w, Cacc.z);
                             T = Tn;
                         }
                     }
                 }
+                __syncwarp();
                 if (kCount) {
                     c_entries += ng;
                     c_evals += warp_sum_u32(done0 ? 0u : n_eval);
