@@ -138,8 +138,10 @@ __global__ void __launch_bounds__(256) prep_sh_kernel(DevTree t, const float* __
 // ---------------------------------------------------------------------------
 // blend backward
 // ---------------------------------------------------------------------------
+template <bool kWalk>
 struct BwdSmem {
     blendk::BlendSmem<false> S;
+    blendk::GroupSmem<kWalk> G;     // the re-walk's scratch (not needed with kept state)
     uint32_t m[256];
     uint32_t lim[8];
 };
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
                                                         const float* __restrict__ dL_drgb,
                                                         float* __restrict__ gsplat, FrameState* st)
 {
-    __shared__ __align__(128) BwdSmem B;
+    __shared__ __align__(128) BwdSmem<!kKept> B;
     blendk::BlendSmem<false>& S = B.S;
     const uint32_t tile = blockIdx.x;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -261,24 +263,43 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
                 wcnt += __popc(bb);
             }
             __syncwarp();
-            for (uint32_t i = 0; i < wcnt; ++i) {
+            // the forward's group walk: lockstep tests, then each lane applies its
+            // own hits in order (same operations and order as the forward)
+            float (*pw)[32] = B.G.pw[warp];
+            float4* grp = B.G.grp[warp];
+            for (uint32_t i0 = 0; i0 < wcnt; i0 += blendk::kGroup) {
                 if (__all_sync(0xffffffffu, done)) break;
-                const uint32_t j = S.wlist[warp][i];
-                // branch-free as in the forward: same operations for the lanes that apply it
-                const float4 g0 = S.g0[j];
-                const float4 g1 = S.g1[j];
-                const float dx = fs(g0.x, px), dy = fs(g0.y, py);
-                const float power = fs(fm(-0.5f, fa(fm(fm(g0.z, dx), dx), fm(fm(g1.x, dy), dy))),
-                                       fm(fm(g0.w, dx), dy));
-                const bool hit = !done && !(power > 0.0f || power < g1.y);
-                if (!__any_sync(0xffffffffu, hit)) continue;
-                float alpha = fm(g1.z, exp_cw(fminf(power, 0.0f)));
-                alpha = alpha < 0.99f ? alpha : 0.99f;
-                const float Tn = fm(T, fs(1.0f, alpha));
-                const bool stop = hit && Tn < 0.0001f;
-                lim = stop ? s0 + j : lim;
-                T = (hit && !stop) ? Tn : T;
-                done = done || stop;
+                const uint32_t ng = min((uint32_t)blendk::kGroup, wcnt - i0);
+                uint32_t hits = 0;
+                for (uint32_t e = 0; e < ng; ++e) {
+                    const uint32_t j = S.wlist[warp][i0 + e];
+                    const float4 g0 = S.g0[j];
+                    const float4 g1 = S.g1[j];
+                    const float dx = fs(g0.x, px), dy = fs(g0.y, py);
+                    const float power = fs(fm(-0.5f, fa(fm(fm(g0.z, dx), dx), fm(fm(g1.x, dy), dy))),
+                                           fm(fm(g0.w, dx), dy));
+                    pw[e][lane] = power;
+                    hits |= (uint32_t)(!done && !(power > 0.0f || power < g1.y)) << e;
+                }
+                if (lane < ng) grp[lane].x = S.g1[S.wlist[warp][i0 + lane]].z;
+                __syncwarp();
+                while (__any_sync(0xffffffffu, hits != 0u)) {
+                    if (hits) {
+                        const uint32_t e = __ffs(hits) - 1;
+                        hits &= hits - 1u;
+                        float alpha = fm(grp[e].x, exp_cw(pw[e][lane]));
+                        alpha = alpha < 0.99f ? alpha : 0.99f;
+                        const float Tn = fm(T, fs(1.0f, alpha));
+                        if (Tn < 0.0001f) {
+                            done = true;
+                            hits = 0;
+                            lim = s0 + S.wlist[warp][i0 + e];
+                        } else {
+                            T = Tn;
+                        }
+                    }
+                }
+                __syncwarp();
             }
             if (__syncthreads_count(done) == (int)blockDim.x) break;
         }

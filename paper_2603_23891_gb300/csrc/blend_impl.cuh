@@ -74,7 +74,7 @@ struct BlendSmem {
 
 // Per-warp scratch of the group walk (see blend_tile): each lane's binary32
 // power for every entry of the group, and the entries' alpha0 and colour.
-constexpr int kGroup = 16;
+constexpr int kGroup = 32;
 template <bool kUsed>
 struct GroupSmem {
     float pw[kUsed ? 8 : 1][kUsed ? kGroup : 1][32];
