@@ -568,6 +568,7 @@ int fgs_load_tree(fgs_ctx* c, const fgs_tree* t)
     const size_t o_sh = off; off = align_up(off + sz_sh, 256);
     const size_t o_leaf = off; off = align_up(off + sz_leaf, 256);
     const size_t o_ap = off; off = align_up(off + sz_ap, 256);
+    const size_t o_attr = off; off = align_up(off + n_pad * 48, 256);
     const size_t total = off;
 
     free_ptr(c->tree_mem);
@@ -598,6 +599,22 @@ int fgs_load_tree(fgs_ctx* c, const fgs_tree* t)
     if (D > 0) {
         FGS_CUDA(c, cudaMemcpy2D(base + o_ap, n_pad * 4, t->ap, N * 4, N * 4, D, cudaMemcpyHostToDevice));
     }
+    {
+        // node-major copy of the attributes the projection gathers per selected node
+        std::vector<float> attr((size_t)N * 12, 0.0f);
+        for (uint64_t n = 0; n < N; ++n) {
+            float* a = attr.data() + n * 12;
+            a[0] = t->mu[n];
+            a[1] = t->mu[N + n];
+            a[2] = t->mu[2 * N + n];
+            a[3] = t->opacity[n];
+            for (int q = 0; q < 4; ++q) a[4 + q] = t->cov[q * N + n];
+            a[8] = t->cov[4 * N + n];
+            a[9] = t->cov[5 * N + n];
+            a[10] = t->ln_opacity[n];
+        }
+        FGS_CUDA(c, cudaMemcpy(base + o_attr, attr.data(), attr.size() * 4, cudaMemcpyHostToDevice));
+    }
     DevTree& dt = c->tree;
     dt.n = (uint32_t)N;
     dt.n_pad = (uint32_t)n_pad;
@@ -611,6 +628,7 @@ int fgs_load_tree(fgs_ctx* c, const fgs_tree* t)
     dt.sh = (const float*)(base + o_sh);
     dt.leaf_bits = (const uint32_t*)(base + o_leaf);
     dt.ap = (const uint32_t*)(base + o_ap);
+    dt.attr = (const float4*)(base + o_attr);
     int r = ensure_nodes(c, n_pad);
     if (r) return r;
     // children lists (CSR, ascending ids) for the level-wise baseline

@@ -114,8 +114,13 @@ __global__ void __launch_bounds__(256) prep_params_kernel(DevTree t, ParamPtrs p
 #pragma unroll
         for (int k = 0; k < 6; ++k) cov[k * np + n] = c6[k];
         const float den = fa(1.0f, exp_cw(-clamp_logit(p.logit[n])));
-        op[n] = fd(1.0f, den);
-        lop[n] = -ln_cw(den);
+        const float a0 = fd(1.0f, den), la0 = -ln_cw(den);
+        op[n] = a0;
+        lop[n] = la0;
+        float4* attr = const_cast<float4*>(t.attr) + 3 * (size_t)n;
+        attr[0] = make_float4(p.mu[n], p.mu[N + n], p.mu[2 * N + n], a0);
+        attr[1] = make_float4(c6[0], c6[1], c6[2], c6[3]);
+        attr[2] = make_float4(c6[4], c6[5], la0, 0.0f);
     }
 }
 

@@ -67,6 +67,9 @@ struct DevTree {
     const float* sh;           // [n_pad][sh_stride]
     const uint32_t* leaf_bits; // [n_pad/32]
     const uint32_t* ap;        // [depth][n_pad]
+    // the projection's gather copy, node-major: {mu.x, mu.y, mu.z, alpha0},
+    // {xx, xy, xz, yy}, {yz, zz, ln alpha0, 0}
+    const float4* attr;        // [n_pad][3]
 };
 
 // Per-frame device state (one per context).

@@ -96,13 +96,13 @@ __device__ __forceinline__ uint32_t project_one(const DevTree& t, const DevCamer
     const float ftx = (float)cam.tiles_x, fty = (float)cam.tiles_y;
     uint32_t cnt = 0;
     // ---- decision-exact binary32: frustum, EWA covariance, footprint
-    const size_t np = t.n_pad;
-    const float mx = __ldg(t.mu + n), my = __ldg(t.mu + np + n), mz = __ldg(t.mu + 2 * np + n);
-    float s6[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) s6[q] = __ldg(t.cov + q * np + n);
-    const float a0 = __ldg(t.opacity + n);
-    const float ln_a0 = __ldg(t.ln_opacity + n);
+    const float4 q0 = __ldg(t.attr + 3 * (size_t)n);
+    const float4 q1 = __ldg(t.attr + 3 * (size_t)n + 1);
+    const float4 q2 = __ldg(t.attr + 3 * (size_t)n + 2);
+    const float mx = q0.x, my = q0.y, mz = q0.z;
+    const float s6[6] = {q1.x, q1.y, q1.z, q1.w, q2.x, q2.y};
+    const float a0 = q0.w;
+    const float ln_a0 = q2.z;
     float vx, vy, vz, txtz = 0.0f, tytz = 0.0f;
     camera_space(cam, mx, my, mz, vx, vy, vz);
     const bool inf = frustum_test(cam, vx, vy, vz, txtz, tytz);
