@@ -170,7 +170,9 @@ int fgs_load_tree(fgs_ctx* ctx, const fgs_tree* tree);
 
 /* Set the camera used by the next frame calls (copied; host struct).  Grows
  * the tile buffers if the image has more tiles.  Errors: FGS_ERR_ARG for
- * non-finite values, width/height outside 1..16384, tan_half <= 0. */
+ * non-finite values, width/height outside 1..16384, tan_half <= 0, or more
+ * than 65,536 tiles with the current tile shape (the (tile | depth) keys hold
+ * 16 tile bits: 6 digit passes). */
 int fgs_set_camera(fgs_ctx* ctx, const fgs_camera* cam);
 
 /* Footprint mode for the next frames (§3.3): FGS_SHRINK_OFF (3 sigma) or

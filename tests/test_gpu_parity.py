@@ -342,3 +342,20 @@ def test_tiny_tree_thousand_random_cameras(renderer, tiny):
         n_empty += len(o.sel) == 0
     print(f"1000 cameras: worst max-abs {worst:.2e}, {n_empty} empty views, {time.time() - t0:.1f}s")
     assert n_empty < 1000
+
+
+def test_tile_grid_limit_rejected(renderer):
+    """More than 65,536 tiles (16384 x 8192 on 16x16 tiles) is refused on the host
+    before any launch; the context stays usable."""
+    from paper_2603_23891_gb300 import filtergs
+    tree = synth.tiny_tree()
+    renderer.load_tree(tree)
+    renderer.set_params(tau_R=3.0, tile=(16, 16))
+    big = synth.look_at_camera([0.0, -60.0, 30.0], [0.0, 0.0, 0.0], 16384, 8192, 70.0)
+    with pytest.raises(filtergs.FgsError) as e:
+        renderer.set_camera(big)
+    assert e.value.code == filtergs.FGS_ERR_ARG
+    cam = synth.tiny_camera()
+    g = gpu_frame(renderer, tree, cam, 3.0)
+    o, _ = oracle_frame(tree, cam, 3.0)
+    assert_frame_parity(g, o)
