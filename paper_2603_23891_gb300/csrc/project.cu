@@ -20,16 +20,26 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(
     uint4* __restrict__ foot, uint32_t* __restrict__ tile_total, FrameState* st)
 {
     __shared__ uint32_t s_warp_tot[kProjThreads / 32];
+    __shared__ uint32_t s_dhist[4][256];      // depth digits, weighted by pair count
     grid_dep_wait();
     grid_dep_trigger();
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t M = st->M;
     const uint32_t n_tiles = (M + kProjThreads - 1) / kProjThreads;
+    for (int i = tid; i < 4 * 256; i += kProjThreads) (&s_dhist[0][0])[i] = 0;
+    __syncthreads();
 
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint32_t m = tile * kProjThreads + tid;
         uint32_t cnt = 0;
         if (m < M) cnt = proj::project_one(t, cam, __ldg(sel + m), m, splat, foot);
+        if (cnt) {
+            // every pair of a Gaussian carries its depth: the four depth digits of
+            // the (tile | depth) keys are counted here, once per Gaussian
+            const uint32_t d = foot[m].w;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) atomicAdd(&s_dhist[p][(d >> (8 * p)) & 0xFFu], cnt);
+        }
         const uint32_t emitting = __popc(__ballot_sync(0xffffffffu, cnt > 0));
         if (lane == 0 && emitting) atomicAdd(&st->n_emitting, emitting);
         const uint32_t wsum = warp_sum_u32(cnt);
@@ -42,6 +52,10 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(
             tile_total[tile] = tot;
         }
         __syncthreads();
+    }
+    for (int i = tid; i < 4 * 256; i += kProjThreads) {
+        const uint32_t c = (&s_dhist[0][0])[i];
+        if (c) atomicAdd(&st->hist[0][0] + i, c);
     }
 }
 
@@ -133,7 +147,7 @@ __global__ void __launch_bounds__(kProjThreads) emit_kernel(
                         const unsigned long long key = (tl << 32) | o_d;
                         keys[idx] = key;
                         vals[idx] = o_m;
-                        for (int p = 0; p < passes; ++p)
+                        for (int p = 4; p < passes; ++p)     // tile digits (depth: projection)
                             atomicAdd(&s_hist[p][(uint32_t)(key >> (8 * p)) & 0xFFu], 1u);
                     }
                 }
@@ -145,7 +159,7 @@ __global__ void __launch_bounds__(kProjThreads) emit_kernel(
     }
     if (!any) return;
     __syncthreads();
-    for (int i = tid; i < passes * 256; i += kProjThreads) {
+    for (int i = 4 * 256 + tid; i < passes * 256; i += kProjThreads) {
         const uint32_t c = (&s_hist[0][0])[i];
         if (c) atomicAdd(&st->hist[0][0] + i, c);
     }
