@@ -3,8 +3,9 @@
 //
 // Two passes.  project_kernel: one thread per selected Gaussian computes the
 // splat record (centre, conic, log-domain skip threshold, opacity, depth,
-// colour, footprint radius), its tile rectangle and pair count, and each tile
-// of 256 Gaussians its pair total.  emit_kernel: exclusive prefixes of those
+// colour, footprint radius), its tile rectangle and pair count, each tile of
+// 256 Gaussians its pair total, and the histograms of the four depth digits of
+// the sort keys (weighted by pair count).  emit_kernel: exclusive prefixes of those
 // totals give every Gaussian its first pair slot, so pairs are emitted in
 // selection order (the tie-break of the stable (tile | depth) sort).
 #include "project_impl.cuh"
@@ -63,8 +64,9 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(
 // Gaussian tiles; its first slot is the sum of all earlier tile totals (a block
 // reduction, no waiting on other blocks).  Within a tile a block scan orders
 // the Gaussians, and each warp writes its pairs with consecutive lanes on
-// consecutive slots.  The radix digit histograms of all sort passes are
-// accumulated here, per block in shared memory.
+// consecutive slots.  The radix digit histograms of the tile digits are
+// accumulated here, per block in shared memory (the depth digits, equal for
+// all pairs of a Gaussian, were counted by the projection).
 __global__ void __launch_bounds__(kProjThreads) emit_kernel(
     DevCamera cam, const uint4* __restrict__ foot, const uint32_t* __restrict__ tile_total,
     unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals, unsigned long long cap,
