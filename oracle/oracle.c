@@ -27,28 +27,33 @@
 /* ------------------------------------------------------------------ */
 
 /* e^x for binary32.  Argument reduction after Cody & Waite (Software Manual
- * for the Elementary Functions, 1980): k = nearest integer to x / ln 2, and
- * r = x - k ln 2 with ln 2 split into a short leading part (exact products for
- * |k| < 2^15) plus a correction.  e^r, |r| <= ln2/2, is the Taylor polynomial
- * of degree 7 by Horner's rule (truncation < 6e-9 relative), and the result is
- * scaled by 2^k built from its exponent bits.  Fixed order, no fused ops, so
- * any IEEE binary32 machine returns the same bits. */
+ * for the Elementary Functions, 1980): k = the integer nearest to x / ln 2,
+ * taken from the binary32 sum x log2(e) + 1.5 * 2^23 formed with one rounding
+ * (a fused multiply-add), and r = x - k ln 2 with ln 2 split into a short
+ * leading part (exact products for |k| < 2^15) plus a correction.  e^r,
+ * |r| <= ln2/2, is the Taylor polynomial of degree 7 by Horner's rule with
+ * fused multiply-adds (truncation < 6e-9 relative), scaled by 2^k built from
+ * its exponent bits.  Every step is an IEEE 754 binary32 operation (fmaf is
+ * IEEE fusedMultiplyAdd) in a fixed order, so any conforming machine returns
+ * the same bits. */
 float oracle_expf(float x)
 {
     if (x < -87.0f) return 0.0f;
     if (x > 88.0f) return INFINITY;
-    float kf = rintf(x * 1.44269504088896341f);
-    float r = (x - kf * 0.693359375f) - kf * -2.12194440e-4f;
-    float p = 1.98412698412698413e-4f;     /* 1/7! */
-    p = p * r + 1.38888888888888889e-3f;   /* 1/6! */
-    p = p * r + 8.33333333333333333e-3f;   /* 1/5! */
-    p = p * r + 4.16666666666666667e-2f;   /* 1/4! */
-    p = p * r + 1.66666666666666667e-1f;   /* 1/3! */
-    p = p * r + 0.5f;                      /* 1/2! */
-    p = p * r + 1.0f;
-    p = p * r + 1.0f;
-    int32_t k = (int32_t)kf;
-    uint32_t bits = (uint32_t)(k + 127) << 23;
+    const float t = fmaf(x, 1.44269504088896341f, 12582912.0f);
+    const float kf = t - 12582912.0f;
+    float r = fmaf(kf, -0.693359375f, x);
+    r = fmaf(kf, 2.12194440e-4f, r);
+    float p = 1.98412698412698413e-4f;            /* 1/7! */
+    p = fmaf(p, r, 1.38888888888888889e-3f);      /* 1/6! */
+    p = fmaf(p, r, 8.33333333333333333e-3f);      /* 1/5! */
+    p = fmaf(p, r, 4.16666666666666667e-2f);      /* 1/4! */
+    p = fmaf(p, r, 1.66666666666666667e-1f);      /* 1/3! */
+    p = fmaf(p, r, 0.5f);                         /* 1/2! */
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    const int32_t k = (int32_t)kf;
+    const uint32_t bits = (uint32_t)(k + 127) << 23;
     float two_k;
     memcpy(&two_k, &bits, sizeof two_k);
     return p * two_k;
@@ -403,6 +408,18 @@ int64_t oracle_count_pairs_bruteforce(const ocam* c, const oparams* p, const flo
 /* Eq. 2 blending and Eq. 5 KPC                                        */
 /* ------------------------------------------------------------------ */
 
+/* power = -1/2 (A dx^2 + 2 B dx dy + C dy^2) for the conic (A, B, C) of splat
+ * record s, evaluated as (A' dx + B' dy) dx + (C' dy) dy with the per-Gaussian
+ * coefficients A' = -A/2, B' = -B, C' = -C/2: one product for B' dy, two for
+ * (C' dy) dy, then two fused multiply-adds, in that order. */
+static float oracle_power(const float* s, float dx, float dy)
+{
+    const float Ah = -0.5f * s[ORACLE_SPLAT_A];
+    const float Bn = -s[ORACLE_SPLAT_B];
+    const float Ch = -0.5f * s[ORACLE_SPLAT_C];
+    return fmaf(fmaf(Ah, dx, Bn * dy), dx, (Ch * dy) * dy);
+}
+
 /* Blend one pixel front to back over the pairs [b, e) of its tile.
  * 3DGS conventions: power = -1/2 d^T conic d; skip power > 0; skip alpha below
  * 1/255 (tested as power < -ln 255 - ln alpha0); alpha = min(0.99, alpha0 e^power);
@@ -417,10 +434,7 @@ static void blend_pixel(const float* splat, const uint32_t* vals, int64_t b, int
         const float* s = splat + (int64_t)vals[q] * ORACLE_SPLAT_STRIDE;
         const float dx = s[ORACLE_SPLAT_U] - px;
         const float dy = s[ORACLE_SPLAT_V] - py;
-        const float p1 = (s[ORACLE_SPLAT_A] * dx) * dx;
-        const float p2 = (s[ORACLE_SPLAT_C] * dy) * dy;
-        const float p3 = (s[ORACLE_SPLAT_B] * dx) * dy;
-        const float power = -0.5f * (p1 + p2) - p3;
+        const float power = oracle_power(s, dx, dy);
         if (power > 0.0f) continue;
         if (power < s[ORACLE_SPLAT_LTHR]) continue;
         float alpha = s[ORACLE_SPLAT_A0] * oracle_expf(power);
