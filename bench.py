@@ -137,8 +137,9 @@ def blend_alu_peak(sm_mhz, sms):
 
 
 # FP32 lane operations of Eq. 2 with the 3DGS rules, as the blend computes them
-OPS_PER_EVAL = 13.0   # dx, dy, 3 x 2 products, sum, scale, subtract, the two skip tests
-OPS_PER_HIT = 31.0    # exp (22: range test, reduction 6, degree-7 Horner 14, scaling), alpha,
+OPS_PER_EVAL = 9.0    # dx, dy, B'dy, C'dy, (C'dy)dy, two FMAs, the two skip tests
+OPS_PER_HIT = 24.0    # exp (15: k by one FMA and a subtraction, reduction 2 FMAs, degree-7
+                      # Horner 7 FMAs, 2^k 2 integer ops, scaling, range select), alpha,
                       # clamp, 1 - alpha, T update, stop test, weight, 3 colour FMAs
 
 
@@ -543,8 +544,8 @@ def run_ours(args):
                       "peak": round(peak_tf, 3), "unit": "TFLOP/s", "frac": round(ach_tf / peak_tf, 4),
                       "traffic": profiled_traffic("blend_kernel"),
                       "peak_source": f"derived: 128 FP32 lanes x {sms} SMs x {clk_mhz:.0f} MHz",
-                      "ops": "FP32 lane operations: 13 per pixel-Gaussian evaluation (offsets, power, "
-                             "the two skip tests), 31 more per evaluation that applies alpha (exp, alpha, "
+                      "ops": "FP32 lane operations: 9 per pixel-Gaussian evaluation (offsets, power, "
+                             "the two skip tests), 24 more per evaluation that applies alpha (exp, alpha, "
                              "clamp, T, stop test, colour)",
                       "hbm_view": {"achieved": stages[dom]["GB/s"], "peak": hbm_peak, "unit": "GB/s",
                                    "frac": stages[dom]["frac_hbm"]}}

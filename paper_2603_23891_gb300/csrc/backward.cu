@@ -254,8 +254,7 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
                 if (m >= M) m = 0;
                 const float4* g = reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride);
                 const float4 a = __ldg(g), b = __ldg(g + 1);
-                S.g0[tid] = a;
-                S.g1[tid] = b;
+                blendk::put_coeffs(S.g0[tid], S.g1[tid], a, b);
                 S.wmask[tid] = blendk::warp_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
             }
             __syncthreads();
@@ -267,6 +266,7 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
                 if (mine) S.wlist[warp][wcnt + __popc(bb & ((1u << lane) - 1u))] = (uint16_t)j;
                 wcnt += __popc(bb);
             }
+            if (wcnt + lane < ((wcnt + 3u) & ~3u)) S.wlist[warp][wcnt + lane] = 0;
             __syncwarp();
             // the forward's group walk: lockstep tests, then each lane applies its
             // own hits in order (same operations and order as the forward)
@@ -275,24 +275,15 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
             for (uint32_t i0 = 0; i0 < wcnt; i0 += blendk::kGroup) {
                 if (__all_sync(0xffffffffu, done)) break;
                 const uint32_t ng = min((uint32_t)blendk::kGroup, wcnt - i0);
-                uint32_t hits = 0;
-                for (uint32_t e = 0; e < ng; ++e) {
-                    const uint32_t j = S.wlist[warp][i0 + e];
-                    const float4 g0 = S.g0[j];
-                    const float4 g1 = S.g1[j];
-                    const float dx = fs(g0.x, px), dy = fs(g0.y, py);
-                    const float power = fs(fm(-0.5f, fa(fm(fm(g0.z, dx), dx), fm(fm(g1.x, dy), dy))),
-                                           fm(fm(g0.w, dx), dy));
-                    pw[e][lane] = power;
-                    hits |= (uint32_t)(!done && !(power > 0.0f || power < g1.y)) << e;
-                }
+                uint32_t hits = blendk::group_tests(S.g0, S.g1, &S.wlist[warp][i0], ng, px, py, pw, lane);
+                if (done) hits = 0;
                 if (lane < ng) grp[lane].x = S.g1[S.wlist[warp][i0 + lane]].z;
                 __syncwarp();
                 while (__any_sync(0xffffffffu, hits != 0u)) {
                     if (hits) {
                         const uint32_t e = __ffs(hits) - 1;
                         hits &= hits - 1u;
-                        float alpha = fm(grp[e].x, exp_cw(pw[e][lane]));
+                        float alpha = fm(grp[e].x, exp_nonpos(pw[e][lane]));
                         alpha = alpha < 0.99f ? alpha : 0.99f;
                         const float Tn = fm(T, fs(1.0f, alpha));
                         if (Tn < 0.0001f) {
@@ -331,8 +322,7 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
             if (m >= M) m = 0;
             const float4* g = reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride);
             const float4 a = __ldg(g), b = __ldg(g + 1);
-            S.g0[tid] = a;
-            S.g1[tid] = b;
+            blendk::put_coeffs(S.g0[tid], S.g1[tid], a, b);
             S.g2[tid] = __ldg(g + 2);
             S.wmask[tid] = blendk::warp_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
             B.m[tid] = m;
@@ -355,11 +345,10 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
             const float4 g0 = S.g0[j];
             const float4 g1 = S.g1[j];
             const float dx = fs(g0.x, px), dy = fs(g0.y, py);
-            const float power = fs(fm(-0.5f, fa(fm(fm(g0.z, dx), dx), fm(fm(g1.x, dy), dy))),
-                                   fm(fm(g0.w, dx), dy));
+            const float power = blendk::power_of(g0.z, g0.w, g1.x, dx, dy);
             const bool hit = s0 + j < lim && !(power > 0.0f || power < g1.y);
             if (!__any_sync(0xffffffffu, hit)) continue;
-            const float ex = exp_cw(fminf(power, 0.0f));
+            const float ex = exp_nonpos(fminf(power, 0.0f));
             const float raw = fm(g1.z, ex);
             const bool clamped = !(raw < 0.99f);
             const float alpha = hit ? (clamped ? 0.99f : raw) : 0.0f;
@@ -383,8 +372,9 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
             g[2] = -0.5f * dx * dx * gpow;                         // A
             g[3] = -dx * dy * gpow;                                // B
             g[4] = -0.5f * dy * dy * gpow;                         // C
-            g[0] = -gpow * (g0.z * dx + g0.w * dy);                // u
-            g[1] = -gpow * (g1.x * dy + g0.w * dx);                // v
+            // d power / du = -(A dx + B dy) = 2 A' dx + B' dy, likewise for v
+            g[0] = gpow * (2.0f * g0.z * dx + g0.w * dy);          // u
+            g[1] = gpow * (2.0f * g1.x * dy + g0.w * dx);          // v
             const float v = warp_reduce9(g, lane);
             if (comp >= 0) atomicAdd(gsplat + (size_t)B.m[j] * kGS + comp, v);
         }

@@ -62,11 +62,11 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 template <bool kKpc>
 struct BlendSmem {
     uint32_t vals[kValsSlots];
-    float4 g0[kChunk];          // u, v, A, B
-    float4 g1[kChunk];          // C, lthr, alpha0, depth
+    float4 g0[kChunk];          // u, v, A', B'  (power coefficients, see power_of)
+    float4 g1[kChunk];          // C', lthr, alpha0, depth
     float4 g2[kChunk];          // r, g, b, radius
     uint32_t wmask[kChunk];     // bit w: warp w's pixels can reach the skip threshold
-    uint16_t wlist[8][kChunk];  // per-warp list of chunk entries, in order
+    alignas(16) uint16_t wlist[8][kChunk];  // per-warp list of chunk entries, in order
     float kpc_w[kKpc ? 8 : 1][kKpc ? kChunk : 1];   // per-warp partial KPC (Eq. 5)
     uint64_t bar;
     int timed_out;
@@ -80,6 +80,52 @@ struct GroupSmem {
     float pw[kUsed ? 8 : 1][kUsed ? kGroup : 1][32];
     float4 grp[kUsed ? 8 : 1][kUsed ? kGroup : 1];   // alpha0, r, g, b
 };
+
+// The Gaussian's exponent at offset (dx, dy) = (u - px, v - py):
+// -1/2 (A dx^2 + 2 B dx dy + C dy^2) = (A' dx + B' dy) dx + (C' dy) dy with the
+// per-Gaussian coefficients A' = -A/2, B' = -B, C' = -C/2, evaluated with two
+// fused multiply-adds in this order (the reading both sides share).
+__device__ __forceinline__ float power_of(float Ah, float Bn, float Ch, float dx, float dy)
+{
+    return ff(ff(Ah, dx, fm(Bn, dy)), dx, fm(fm(Ch, dy), dy));
+}
+
+// Shared-memory copy of a splat record's first two float4 (u, v, A, B),
+// (C, lthr, alpha0, depth) with the conic replaced by the power coefficients.
+__device__ __forceinline__ void put_coeffs(float4& d0, float4& d1, float4 a, float4 b)
+{
+    d0 = make_float4(a.x, a.y, fm(-0.5f, a.z), -a.w);
+    d1 = make_float4(fm(-0.5f, b.x), b.y, b.z, b.w);
+}
+
+// Phase 1 of the group walk: this lane's binary32 power for each of the ng
+// (<= kGroup) entries of the warp list wl (chunk slots), parked in pw[e][lane],
+// and the bit mask of the entries whose power passes both skip tests.  The list
+// is read four entries at a time; it must be padded with valid slots to a
+// multiple of 4 (the padding's bits are cleared).
+__device__ __forceinline__ uint32_t group_tests(const float4* __restrict__ g0s,
+                                                const float4* __restrict__ g1s, const uint16_t* wl,
+                                                uint32_t ng, float px, float py, float (*pw)[32],
+                                                uint32_t lane)
+{
+    const uint2* wl4 = reinterpret_cast<const uint2*>(wl);
+    uint32_t hits = 0;
+    for (uint32_t e = 0; e < ng; e += 4) {
+        const uint2 jj = wl4[e >> 2];
+        const uint32_t jx[4] = {jj.x & 0xffffu, jj.x >> 16, jj.y & 0xffffu, jj.y >> 16};
+        uint32_t nib = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 a = g0s[jx[k]];
+            const float4 b = g1s[jx[k]];
+            const float power = power_of(a.z, a.w, b.x, fs(a.x, px), fs(a.y, py));
+            pw[e + k][lane] = power;
+            nib |= (uint32_t)!(power > 0.0f || power < b.y) << k;
+        }
+        hits |= nib << e;
+    }
+    return ng >= 32u ? hits : hits & ((1u << ng) - 1u);
+}
 
 // Bring chunk [s0, e0) of the sorted values into shared memory with one TMA bulk
 // copy of the 16-byte aligned superset [s0 & ~3, (e0 + 3) & ~3).  Returns the
@@ -211,13 +257,13 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
             if (m >= M) m = 0;      // only after a failed sort (status already latched)
             const float4* g = reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride);
             const float4 a = __ldg(g), b = __ldg(g + 1);
-            S.g0[tid] = a;
-            S.g1[tid] = b;
+            put_coeffs(S.g0[tid], S.g1[tid], a, b);
             S.g2[tid] = __ldg(g + 2);
             S.wmask[tid] = warp_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
         }
         __syncthreads();
-        // this warp's ordered list of the chunk entries that can reach its pixels
+        // this warp's ordered list of the chunk entries that can reach its pixels,
+        // padded with slot 0 to a multiple of 4 (group_tests reads 4 at a time)
         uint32_t wcnt = 0;
         for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
             const uint32_t j = j0 + lane;
@@ -226,6 +272,7 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
             if (mine) S.wlist[warp][wcnt + __popc(b & ((1u << lane) - 1u))] = (uint16_t)j;
             wcnt += __popc(b);
         }
+        if (wcnt + lane < ((wcnt + 3u) & ~3u)) S.wlist[warp][wcnt + lane] = 0;
         __syncwarp();
         uint32_t c_entries = 0, c_evals = 0, c_hits = 0, c_active = 0;
         if (kKpc) {
@@ -242,19 +289,14 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
                 // outcome is selected per lane.
                 const float4 g0 = S.g0[j];
                 const float4 g1 = S.g1[j];
-                const float dx = fs(g0.x, px);
-                const float dy = fs(g0.y, py);
-                const float p1 = fm(fm(g0.z, dx), dx);
-                const float p2 = fm(fm(g1.x, dy), dy);
-                const float p3 = fm(fm(g0.w, dx), dy);
-                const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
+                const float power = power_of(g0.z, g0.w, g1.x, fs(g0.x, px), fs(g0.y, py));
                 const bool hit = !done && !(power > 0.0f || power < g1.y);
                 if (__any_sync(0xffffffffu, hit)) {
                     if (kCount) {
                         c_hits += hit ? 1u : 0u;
                         ++c_active;
                     }
-                    float alpha = fm(g1.z, exp_cw(fminf(power, 0.0f)));
+                    float alpha = fm(g1.z, exp_nonpos(fminf(power, 0.0f)));
                     alpha = alpha < 0.99f ? alpha : 0.99f;
                     const float Tn = fm(T, fs(1.0f, alpha));
                     const bool stop = hit && Tn < 0.0001f;     // stop before adding this Gaussian
@@ -292,20 +334,8 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
                 if (__all_sync(0xffffffffu, done)) break;
                 const uint32_t ng = min((uint32_t)kGroup, wcnt - i0);
                 const bool done0 = done;
-                uint32_t hits = 0;
-                for (uint32_t e = 0; e < ng; ++e) {
-                    const uint32_t j = S.wlist[warp][i0 + e];
-                    const float4 g0 = S.g0[j];
-                    const float4 g1 = S.g1[j];
-                    const float dx = fs(g0.x, px);
-                    const float dy = fs(g0.y, py);
-                    const float p1 = fm(fm(g0.z, dx), dx);
-                    const float p2 = fm(fm(g1.x, dy), dy);
-                    const float p3 = fm(fm(g0.w, dx), dy);
-                    const float power = fs(fm(-0.5f, fa(p1, p2)), p3);
-                    pw[e][lane] = power;
-                    hits |= (uint32_t)(!done && !(power > 0.0f || power < g1.y)) << e;
-                }
+                uint32_t hits = group_tests(S.g0, S.g1, &S.wlist[warp][i0], ng, px, py, pw, lane);
+                if (done) hits = 0;
                 if (lane < ng) {
                     const uint32_t j = S.wlist[warp][i0 + lane];
                     const float4 c = S.g2[j];
@@ -318,7 +348,7 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
                         const uint32_t e = __ffs(hits) - 1;
                         hits &= hits - 1u;
                         const float4 q = grp[e];
-                        float alpha = fm(q.x, exp_cw(pw[e][lane]));
+                        float alpha = fm(q.x, exp_nonpos(pw[e][lane]));
                         alpha = alpha < 0.99f ? alpha : 0.99f;
                         const float Tn = fm(T, fs(1.0f, alpha));
                         if (kCount) {

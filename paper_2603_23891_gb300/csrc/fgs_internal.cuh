@@ -101,25 +101,41 @@ __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); 
 __device__ __forceinline__ float fd(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
 
-// e^x in binary32: Cody & Waite argument reduction (x = k ln2 + r with ln 2
-// split into a short leading part and a correction), the degree-7 Taylor
-// polynomial of e^r by Horner's rule, scaled by 2^k from exponent bits.
-// Explicitly rounded operations, so the bits do not depend on the compiler.
+__device__ __forceinline__ float ff(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// e^x in binary32, x <= 0 or NaN: Cody & Waite argument reduction (x = k ln2 + r,
+// k the integer nearest x log2(e), taken from the binary32 sum x log2(e) +
+// 1.5 * 2^23 formed with one rounding; ln 2 split into a short leading part and
+// a correction), the degree-7 Taylor polynomial of e^r by Horner's rule with
+// fused multiply-adds, scaled by 2^k from exponent bits (k = the low bits of
+// that sum).  Explicitly rounded operations, so the bits do not depend on the
+// compiler; for x <= 0 the same as exp_cw below.
+__device__ __forceinline__ float exp_nonpos(float x)
+{
+    const float t = ff(x, 1.44269504088896341f, 12582912.0f);
+    const float kf = fs(t, 12582912.0f);
+    float r = ff(kf, -0.693359375f, x);
+    r = ff(kf, 2.12194440e-4f, r);
+    float p = 1.98412698412698413e-4f;
+    p = ff(p, r, 1.38888888888888889e-3f);
+    p = ff(p, r, 8.33333333333333333e-3f);
+    p = ff(p, r, 4.16666666666666667e-2f);
+    p = ff(p, r, 1.66666666666666667e-1f);
+    p = ff(p, r, 0.5f);
+    p = ff(p, r, 1.0f);
+    p = ff(p, r, 1.0f);
+    // (k + 127) << 23 with k = bits(t) - bits(1.5 * 2^23); only the low 9 bits of
+    // bits(t) survive the shift, and k + 127 lies in [1, 254] for x >= -87
+    const float two_k = __uint_as_float((__float_as_uint(t) + (uint32_t)(127 - 0x4B400000)) << 23);
+    const float y = fm(p, two_k);
+    return x < -87.0f ? 0.0f : y;
+}
+
+// e^x in binary32 for any x: 0 below -87, infinity above 88.
 __device__ __forceinline__ float exp_cw(float x)
 {
-    if (x < -87.0f) return 0.0f;
-    const float kf = rintf(fm(x, 1.44269504088896341f));
-    const float r = fs(fs(x, fm(kf, 0.693359375f)), fm(kf, -2.12194440e-4f));
-    float p = 1.98412698412698413e-4f;
-    p = fa(fm(p, r), 1.38888888888888889e-3f);
-    p = fa(fm(p, r), 8.33333333333333333e-3f);
-    p = fa(fm(p, r), 4.16666666666666667e-2f);
-    p = fa(fm(p, r), 1.66666666666666667e-1f);
-    p = fa(fm(p, r), 0.5f);
-    p = fa(fm(p, r), 1.0f);
-    p = fa(fm(p, r), 1.0f);
-    const int k = (int)kf;
-    return fm(p, __int_as_float((k + 127) << 23));
+    if (x > 88.0f) return __int_as_float(0x7f800000);
+    return exp_nonpos(x);
 }
 
 // Screen-space view of one node: camera-space centre, frustum test and the
