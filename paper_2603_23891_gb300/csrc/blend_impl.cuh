@@ -170,15 +170,24 @@ __device__ __forceinline__ void warp_origin(const DevCamera& cam, int32_t tx0, i
 // Which warps of the tile may hold a pixel whose binary32 power reaches the
 // Gaussian's skip threshold lthr.  Exactly, power >= lthr is the ellipse
 // d^T Q d <= s with Q = [[A, B], [B, C]] and s = -2 lthr, whose bounding box has
-// half-widths sqrt(s C / det Q) and sqrt(s A / det Q).  The rounding error of the
-// binary32 power is below 1e-6 * cond(Q) * |lthr|; the box is enlarged by 5% in s
-// plus one pixel, which covers it for cond(Q) < 1e4 (cond(Q) <= tr^2 / det).
-// Beyond that, or for a singular Q, every warp keeps the Gaussian.  A warp left
-// out of the mask would have skipped the Gaussian at every one of its pixels.
-// Warp column c spans pixel centres tx0 + ww c + [0.5, ww - 0.5], row r spans
-// ty0 + wh r + [0.5, wh - 0.5]; the mask is the block of columns x rows the box
-// meets.  (An exact ellipse-rectangle test per warp removed only 4% of the
-// entries and cost more than it saved.)
+// half-widths sqrt(s C / det Q) and sqrt(s A / det Q).  Margins, for
+// cond(Q) < 1e4 (cond(Q) <= tr^2 / det; beyond that, or for a singular Q, every
+// warp keeps the Gaussian):
+//  * the binary32 power (offsets rounded, three products, two fused
+//    multiply-adds) is within 11 * 2^-24 * cond(Q) < 0.7% of the exact form at
+//    the exact offsets, so a pixel passing the test lies in the ellipse of
+//    s' = 1.05 s + 1e-4;
+//  * det Q computed in binary32 loses at most 2^-24 cond(Q) / 2 < 3e-4
+//    relative, so the computed half-widths are within 2e-4 relative of the
+//    exact ones for s' (the 5% in s leaves 2% of the half-width spare);
+//  * the box is further widened by 0.1% and 0.01 px for the roundings of
+//    u - tx0, v - ty0 and of the bounds below.
+// A warp left out of the mask would have skipped the Gaussian at every one of
+// its pixels.  Warp column c spans pixel centres tx0 + ww c + [0.5, ww - 0.5],
+// row r spans ty0 + wh r + [0.5, wh - 0.5]; the mask is the block of columns x
+// rows the box meets.  (A one-pixel margin here listed 28% more entries for the
+// few-pixel Gaussians of far LoD levels; an exact ellipse-rectangle test per
+// warp removed only 4% more and cost more than it saved.)
 __device__ __forceinline__ uint32_t warp_mask(const DevCamera& cam, int32_t tx0, int32_t ty0, float u,
                                               float v, float A, float B, float C, float lthr)
 {
@@ -187,8 +196,8 @@ __device__ __forceinline__ uint32_t warp_mask(const DevCamera& cam, int32_t tx0,
     const float tr = A + C;
     if (!(det > 0.0f) || tr * tr > 1e4f * det) return 0xFFu;
     const float sq = fmaf(-2.1f, lthr, 1e-4f);  // 1.05 * (-2 lthr) + 1e-4
-    const float ex = sqrtf(sq * C / det) + 1.0f;
-    const float ey = sqrtf(sq * A / det) + 1.0f;
+    const float ex = fmaf(sqrtf(sq * C / det), 1.001f, 0.01f);
+    const float ey = fmaf(sqrtf(sq * A / det), 1.001f, 0.01f);
     const int32_t sh = cam.tile_shift_x - cam.warp_shift;   // log2(warps per tile row)
     const int32_t ncol = 1 << sh, nrow = 8 >> sh;
     const float ww = (float)(1 << cam.warp_shift), wh = (float)(32 >> cam.warp_shift);
