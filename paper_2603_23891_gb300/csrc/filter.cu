@@ -204,8 +204,12 @@ __global__ void __launch_bounds__(256) compact_kernel(const uint32_t* __restrict
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n_tiles = (n_words + kCompactWords - 1) / kCompactWords;
     const uint32_t tag = st->epoch * 16u + 0u;
+    // block b takes tile b first, later tiles come from the ticket counter in
+    // order (the grid is at most the resident capacity: every look-back wait ends)
+    bool first = true;
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(&st->tickets[kTicketCompact], 1u);
+        if (tid == 0) s_tile = first ? blockIdx.x : gridDim.x + atomicAdd(&st->tickets[kTicketCompact], 1u);
+        first = false;
         __syncthreads();
         const uint32_t tile = s_tile;
         if (tile >= n_tiles) break;

@@ -73,8 +73,15 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(
         S.goff[tid] = block_excl_scan_256(h, S.scan_tmp, total);
     }
 
+    // Block b takes tile b first, then tickets hand out tiles gridDim.x, ... in
+    // order (one atomic round trip fewer on the critical path).  The grid is
+    // the resident capacity, so every earlier tile's block runs and each
+    // look-back wait ends.
+    bool first = true;
     for (;;) {
-        if (tid == 0) S.tile = atomicAdd(&st->tickets[kTicketSortBase + pass], 1u);
+        if (tid == 0)
+            S.tile = first ? blockIdx.x : gridDim.x + atomicAdd(&st->tickets[kTicketSortBase + pass], 1u);
+        first = false;
 #pragma unroll
         for (int w = 0; w < kSortThreads / 32; ++w) S.whist[w][tid] = 0;
         __syncthreads();
