@@ -295,9 +295,7 @@ __global__ void __launch_bounds__(256) bblend_kernel(const DevCamera* __restrict
                                                      float* __restrict__ rgb, float* __restrict__ Tout,
                                                      FrameState* st)
 {
-    __shared__ __align__(128) blendk::BlendSmem<false> S;
-    __shared__ __align__(16) blendk::GroupSmem<true> Gs;
-    __shared__ double s_red[8];
+    __shared__ __align__(128) blendk::HalfSmem H;
     __shared__ DevCamera s_cam;
     const uint32_t gtile = blockIdx.x;
     int lo = 0, hi = V;                            // largest v with tile_base[v] <= gtile
@@ -311,8 +309,8 @@ __global__ void __launch_bounds__(256) bblend_kernel(const DevCamera* __restrict
         reinterpret_cast<uint32_t*>(&s_cam)[i] = reinterpret_cast<const uint32_t*>(cams + v)[i];
     __syncthreads();
     const unsigned long long o = __ldg(img_off + v);
-    blendk::blend_tile<false>(s_cam, gtile - __ldg(tile_base + v), gtile, S, Gs, s_red, ranges, vals, splat,
-                              rgb + 3 * o, Tout ? Tout + o : nullptr, nullptr, nullptr, nullptr, st);
+    blendk::blend_tile_half(s_cam, gtile - __ldg(tile_base + v), gtile, H, ranges, vals, splat, rgb + 3 * o,
+                            Tout ? Tout + o : nullptr, nullptr, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -2,20 +2,22 @@
 // pass of the scene-adaptive shrinking (Eq. 5-7), sm_103a.
 //
 // One CTA per image tile, one thread per pixel (tile_w * tile_h = 256); each
-// warp covers an 8 x 4 pixel block.  The tile's slice of the sorted value list
-// is brought into shared memory in chunks of 256 by a TMA bulk copy
+// warp covers an 8 x 4 (or 4 x 8) pixel block.  The tile's slice of the sorted
+// value list is brought into shared memory in chunks of 256 by a TMA bulk copy
 // (cp.async.bulk, completion on an mbarrier; the copy starts at the 16-byte
 // boundary at or below the slice and the index is offset accordingly).  Each
 // thread then gathers one splat record into shared memory and computes which
-// warps' pixels the Gaussian can reach; every warp compacts the chunk to its own
-// ordered list and walks it front to back.
+// pixel blocks the Gaussian can reach.  The forward culls per 4 x 4 half-block
+// (each warp's two halves walk their own ordered lists in lockstep, testing in
+// groups of 32 entries and then applying each lane's hits); the KPC pass culls
+// per warp and walks one entry at a time, reducing alpha * T across the warp.
 //
 // Blend decisions are exact: power, the log-domain skip test, alpha, the
 // opacity clamp and the transmittance update use explicitly rounded binary32
 // operations and a deterministic exp, so which Gaussians a pixel applies, and
-// where it stops, do not depend on the compiler.  The per-warp culling only
-// drops Gaussians that every pixel of the warp would skip.  Colour
-// accumulation may use FMA (it decides nothing).
+// where it stops, do not depend on the compiler.  The culling only drops
+// Gaussians that every pixel of the block would skip.  Colour accumulation may
+// use FMA (it decides nothing).
 #include "blend_impl.cuh"
 
 namespace fgs {
@@ -31,13 +33,19 @@ __global__ void __launch_bounds__(256) blend_kernel(DevCamera cam, const uint2* 
                                                     float* __restrict__ kpc_out,
                                                     float* __restrict__ G_out, FrameState* st)
 {
-    __shared__ __align__(128) BlendSmem<kKpc> S;
-    __shared__ __align__(16) blendk::GroupSmem<!kKpc> Gs;
-    __shared__ double s_red[8];
-    grid_dep_wait();
-    grid_dep_trigger();
-    blendk::blend_tile<kKpc, kCount, kKeep>(cam, blockIdx.x, blockIdx.x, S, Gs, s_red, ranges, vals, splat, rgb,
-                                     Tout, keep, kpc_out, G_out, st);
+    if constexpr (kKpc) {
+        __shared__ __align__(128) BlendSmem<true> S;
+        __shared__ double s_red[8];
+        grid_dep_wait();
+        grid_dep_trigger();
+        blendk::blend_tile_kpc(cam, blockIdx.x, S, s_red, ranges, vals, splat, kpc_out, G_out, st);
+    } else {
+        __shared__ __align__(128) blendk::HalfSmem H;
+        grid_dep_wait();
+        grid_dep_trigger();
+        blendk::blend_tile_half<kCount, kKeep>(cam, blockIdx.x, blockIdx.x, H, ranges, vals, splat, rgb,
+                                               Tout, keep, st);
+    }
 }
 
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,

@@ -215,21 +215,18 @@ __device__ __forceinline__ uint32_t warp_mask(const DevCamera& cam, int32_t tx0,
 }
 
 
-// Blend one image tile (the CTA's).  `tile` is the tile in the camera's grid;
-// `gtile` indexes ranges and G_out (the same for one view; the batch's global
-// tile id).  rgb / Tout are the camera's own image planes.  With kKeep,
-// keep_out receives per pixel {final T bits, stop position}: the sorted-pair
-// index of the Gaussian the pixel stopped at, or the tile's end if it did not
-// stop; the differentiable form's backward walks each pixel from there.
-template <bool kKpc, bool kCount = false, bool kKeep = false>
-__device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, uint32_t gtile,
-                                           BlendSmem<kKpc>& S, GroupSmem<!kKpc>& Gs, double* s_red,
-                                           const uint2* __restrict__ ranges,
-                                           const uint32_t* __restrict__ vals,
-                                           const float* __restrict__ splat, float* __restrict__ rgb,
-                                           float* __restrict__ Tout, uint2* __restrict__ keep_out,
-                                           float* __restrict__ kpc_out,
-                                           float* __restrict__ G_out, FrameState* st)
+// The KPC pre-render of one tile (the CTA's; Eq. 5-6): the forward walk with
+// per-warp lists, one entry at a time, every lane computing power and (when any
+// lane of the warp can apply the Gaussian) alpha and T', selected per lane; the
+// applied alpha * T is reduced across the warp per entry and over the warps per
+// pair.  Writes kpc_out[pair] and the tile's mean KPC G_out[tile] (NaN for a
+// tile without pairs).  No image is written.
+__device__ __forceinline__ void blend_tile_kpc(const DevCamera& cam, uint32_t tile, BlendSmem<true>& S,
+                                               double* s_red, const uint2* __restrict__ ranges,
+                                               const uint32_t* __restrict__ vals,
+                                               const float* __restrict__ splat,
+                                               float* __restrict__ kpc_out, float* __restrict__ G_out,
+                                               FrameState* st)
 {
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t tx0 = (int32_t)(tile % (uint32_t)cam.tiles_x) * cam.tile_w;
@@ -240,7 +237,7 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
     const int32_t y = wy0 + (int32_t)(lane >> cam.warp_shift);
     const bool inside = x < cam.width && y < cam.height;
     const float px = fa((float)x, 0.5f), py = fa((float)y, 0.5f);
-    const uint2 rg = ranges[gtile];
+    const uint2 rg = ranges[tile];
     const uint32_t M = st->M;
     const uint32_t s = rg.x, e = rg.y;
 
@@ -251,7 +248,6 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
     __syncthreads();
 
     float T = 1.0f;
-    float3 Cacc = make_float3(0.0f, 0.0f, 0.0f);
     bool done = !inside;
     uint32_t phase = 0;
     double kpc_acc = 0.0;      // this thread's share of the tile's KPC sum (fixed order)
@@ -267,12 +263,10 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
             const float4* g = reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride);
             const float4 a = __ldg(g), b = __ldg(g + 1);
             put_coeffs(S.g0[tid], S.g1[tid], a, b);
-            S.g2[tid] = __ldg(g + 2);
             S.wmask[tid] = warp_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
         }
         __syncthreads();
-        // this warp's ordered list of the chunk entries that can reach its pixels,
-        // padded with slot 0 to a multiple of 4 (group_tests reads 4 at a time)
+        // this warp's ordered list of the chunk entries that can reach its pixels
         uint32_t wcnt = 0;
         for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
             const uint32_t j = j0 + lane;
@@ -281,111 +275,262 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
             if (mine) S.wlist[warp][wcnt + __popc(b & ((1u << lane) - 1u))] = (uint16_t)j;
             wcnt += __popc(b);
         }
-        if (wcnt + lane < ((wcnt + 3u) & ~3u)) S.wlist[warp][wcnt + lane] = 0;
         __syncwarp();
+        for (uint32_t i = 0; i < wcnt; ++i) {
+            const uint32_t j = S.wlist[warp][i];
+            float w = 0.0f;
+            const float4 g0 = S.g0[j];
+            const float4 g1 = S.g1[j];
+            const float power = power_of(g0.z, g0.w, g1.x, fs(g0.x, px), fs(g0.y, py));
+            const bool hit = !done && !(power > 0.0f || power < g1.y);
+            if (__any_sync(0xffffffffu, hit)) {
+                float alpha = fm(g1.z, exp_nonpos(fminf(power, 0.0f)));
+                alpha = alpha < 0.99f ? alpha : 0.99f;
+                const float Tn = fm(T, fs(1.0f, alpha));
+                const bool stop = hit && Tn < 0.0001f;     // stop before adding this Gaussian
+                const bool apply = hit && !stop;
+                w = apply ? alpha * T : 0.0f;
+                T = apply ? Tn : T;
+                done = done || stop;
+            }
+            // Eq. 5: sum of alpha * T over the warp's pixels for this pair
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            if (lane == 0) S.kpc_w[warp][j] = w;
+        }
+        __syncthreads();
+        if (tid < cnt) {
+            const uint32_t msk = S.wmask[tid];
+            float k = 0.0f;
+#pragma unroll
+            for (int w8 = 0; w8 < 8; ++w8)
+                if ((msk >> w8) & 1u) k += S.kpc_w[w8][tid];
+            kpc_out[s0 + tid] = k;
+            kpc_acc += (double)k;
+        }
+        __syncthreads();
+    }
+    // Eq. 6: G = mean KPC over the tile's pairs; fixed-order block reduction
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kpc_acc += __shfl_xor_sync(0xffffffffu, kpc_acc, o);
+    if (lane == 0) s_red[warp] = kpc_acc;
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t n = e - s;
+        double sum = 0.0;
+        for (int w8 = 0; w8 < 8; ++w8) sum += s_red[w8];
+        G_out[tile] = n > 0 ? (float)(sum / (double)n) : __int_as_float(0x7fc00000);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Half-warp culling: the forward's walk over 4x4-pixel half-blocks
+// ---------------------------------------------------------------------------
+// Each warp's 32 pixels are two 4x4 half-blocks (lanes 0-15 and 16-31), side by
+// side for 8x4 warps, stacked for 4x8 warps; a tile holds 16 of them.  Every
+// half-block has its own ordered list of the chunk's Gaussians whose threshold
+// box meets it, so a Gaussian a few pixels across is tested by the 16 lanes of
+// each half it can reach instead of by all 32 lanes of each warp (about 25%
+// fewer lockstep steps on far LoD levels).  Both halves of a warp walk their
+// own lists in lockstep.
+constexpr int kHalfBlocks = 16;
+
+struct HalfSmem {
+    uint32_t vals[kValsSlots];
+    float4 g0[kChunk];                          // u, v, A', B'
+    float4 g1[kChunk];                          // C', lthr, alpha0, depth
+    uint16_t hmask[kChunk];                     // bit b: half-block b may hold a pixel reaching lthr
+    alignas(16) uint8_t hl[kHalfBlocks][kChunk];   // per half-block ordered list of chunk slots
+    float pw[8][kGroup][32];                    // each lane's power per group entry
+    float4 grp[8][2][kGroup];                   // alpha0, r, g, b per half and group entry
+    uint64_t bar;
+    int timed_out;
+};
+
+// Half-blocks of the tile (grid of tile_w / 4 x tile_h / 4, row-major bits) that
+// the Gaussian's threshold box meets; the box and its margins are warp_mask's.
+__device__ __forceinline__ uint32_t half_mask(const DevCamera& cam, int32_t tx0, int32_t ty0, float u,
+                                              float v, float A, float B, float C, float lthr)
+{
+    if (!(lthr <= 0.0f)) return 0u;
+    const float det = A * C - B * B;
+    const float tr = A + C;
+    if (!(det > 0.0f) || tr * tr > 1e4f * det) return 0xFFFFu;
+    const float sq = fmaf(-2.1f, lthr, 1e-4f);
+    const float ex = fmaf(sqrtf(sq * C / det), 1.001f, 0.01f);
+    const float ey = fmaf(sqrtf(sq * A / det), 1.001f, 0.01f);
+    const int32_t sh = cam.tile_shift_x - 2;                 // log2(half-block columns)
+    const int32_t ncol = 1 << sh, nrow = kHalfBlocks >> sh;
+    const float ux = u - (float)tx0, vy = v - (float)ty0;
+    const int32_t c_lo = max(0, (int32_t)ceilf((ux - ex - 3.5f) * 0.25f));
+    const int32_t c_hi = min(ncol - 1, (int32_t)floorf((ux + ex - 0.5f) * 0.25f));
+    const int32_t r_lo = max(0, (int32_t)ceilf((vy - ey - 3.5f) * 0.25f));
+    const int32_t r_hi = min(nrow - 1, (int32_t)floorf((vy + ey - 0.5f) * 0.25f));
+    if (c_lo > c_hi || r_lo > r_hi) return 0u;
+    const uint32_t cols = ((2u << c_hi) - 1u) & ~((1u << c_lo) - 1u);
+    uint32_t mask = 0;
+    for (int32_t r = r_lo; r <= r_hi; ++r) mask |= cols << (r << sh);
+    return mask;
+}
+
+// group_tests over a list of 8-bit chunk slots: the warp-uniform bound ngw
+// covers both halves' groups; bits past this half's own ng are cleared.  Any
+// 8-bit slot indexes the chunk arrays, so entries read past a list's end are
+// harmless and masked.
+__device__ __forceinline__ uint32_t half_group_tests(const float4* __restrict__ g0s,
+                                                     const float4* __restrict__ g1s, const uint8_t* wl,
+                                                     uint32_t ngw, uint32_t ng, float px, float py,
+                                                     float (*pw)[32], uint32_t lane)
+{
+    const uint32_t* wl4 = reinterpret_cast<const uint32_t*>(wl);
+    uint32_t hits = 0;
+    for (uint32_t e = 0; e < ngw; e += 4) {
+        const uint32_t jj = wl4[e >> 2];
+        const uint32_t jx[4] = {jj & 0xffu, (jj >> 8) & 0xffu, (jj >> 16) & 0xffu, jj >> 24};
+        uint32_t nib = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 a = g0s[jx[k]];
+            const float4 b = g1s[jx[k]];
+            const float power = power_of(a.z, a.w, b.x, fs(a.x, px), fs(a.y, py));
+            pw[e + k][lane] = power;
+            nib |= (uint32_t)!(power > 0.0f || power < b.y) << k;
+        }
+        hits |= nib << e;
+    }
+    return ng >= 32u ? hits : hits & ((1u << ng) - 1u);
+}
+
+// Blend one image tile with half-block lists (the forward without KPC).
+// Arguments as blend_tile.
+template <bool kCount = false, bool kKeep = false>
+__device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t tile, uint32_t gtile,
+                                                HalfSmem& H, const uint2* __restrict__ ranges,
+                                                const uint32_t* __restrict__ vals,
+                                                const float* __restrict__ splat, float* __restrict__ rgb,
+                                                float* __restrict__ Tout, uint2* __restrict__ keep_out,
+                                                FrameState* st)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t tx0 = (int32_t)(tile % (uint32_t)cam.tiles_x) * cam.tile_w;
+    const int32_t ty0 = (int32_t)(tile / (uint32_t)cam.tiles_x) * cam.tile_h;
+    int32_t wx0, wy0;
+    warp_origin(cam, tx0, ty0, warp, wx0, wy0);
+    const uint32_t half = lane >> 4, q = lane & 15u;
+    const bool wide = cam.warp_shift == 3;       // 8x4 warps: halves side by side
+    const int32_t x = wx0 + (int32_t)(q & 3u) + (wide ? 4 * (int32_t)half : 0);
+    const int32_t y = wy0 + (int32_t)(q >> 2) + (wide ? 0 : 4 * (int32_t)half);
+    const uint32_t hb = ((uint32_t)(y - ty0) >> 2 << (cam.tile_shift_x - 2)) | ((uint32_t)(x - tx0) >> 2);
+    const uint32_t hb0 = __shfl_sync(0xffffffffu, hb, 0), hb1 = __shfl_sync(0xffffffffu, hb, 16);
+    const bool inside = x < cam.width && y < cam.height;
+    const float px = fa((float)x, 0.5f), py = fa((float)y, 0.5f);
+    const uint2 rg = ranges[gtile];
+    const uint32_t M = st->M;
+    const uint32_t s = rg.x, e = rg.y;
+    const uint32_t lt = (1u << lane) - 1u;
+
+    if (tid == 0) {
+        mbar_init(&H.bar, 1);
+        H.timed_out = 0;
+    }
+    __syncthreads();
+
+    float T = 1.0f;
+    float3 Cacc = make_float3(0.0f, 0.0f, 0.0f);
+    bool done = !inside;
+    uint32_t phase = 0;
+    for (uint32_t s0 = s; s0 < e; s0 += kChunk) {
+        const uint32_t e0 = min(e, s0 + kChunk);
+        const uint32_t cnt = e0 - s0;
+        const uint32_t off = stage_vals(H.vals, &H.bar, &H.timed_out, vals, s0, e0, phase, st);
+        if (H.timed_out) break;
+        if (tid < cnt) {
+            uint32_t m = H.vals[off + tid];
+            if (m >= M) m = 0;      // only after a failed sort (status already latched)
+            const float4* g = reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride);
+            const float4 a = __ldg(g), b = __ldg(g + 1);
+            put_coeffs(H.g0[tid], H.g1[tid], a, b);
+            H.hmask[tid] = (uint16_t)half_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
+        }
+        __syncthreads();
+        // the ordered lists of this warp's two half-blocks
+        uint32_t n0 = 0, n1 = 0;
+        for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            const uint32_t hm = j < cnt ? (uint32_t)H.hmask[j] : 0u;
+            const uint32_t b0 = __ballot_sync(0xffffffffu, (hm >> hb0) & 1u);
+            const uint32_t b1 = __ballot_sync(0xffffffffu, (hm >> hb1) & 1u);
+            if ((hm >> hb0) & 1u) H.hl[hb0][n0 + __popc(b0 & lt)] = (uint8_t)j;
+            if ((hm >> hb1) & 1u) H.hl[hb1][n1 + __popc(b1 & lt)] = (uint8_t)j;
+            n0 += __popc(b0);
+            n1 += __popc(b1);
+        }
+        __syncwarp();
+        const uint8_t* myl = H.hl[hb];
         uint32_t c_entries = 0, c_evals = 0, c_hits = 0, c_active = 0;
-        if (kKpc) {
-            // the KPC pass reduces alpha * T per entry across the warp: one entry at a time
-            for (uint32_t i = 0; i < wcnt; ++i) {
-                const uint32_t j = S.wlist[warp][i];
-                float w = 0.0f;
-                if (kCount) {
-                    ++c_entries;
-                    c_evals += __popc(__ballot_sync(0xffffffffu, !done));
-                }
-                // Branch-free evaluation: every lane computes power; if any lane of
-                // the warp can apply the Gaussian, all compute alpha and T' and the
-                // outcome is selected per lane.
-                const float4 g0 = S.g0[j];
-                const float4 g1 = S.g1[j];
-                const float power = power_of(g0.z, g0.w, g1.x, fs(g0.x, px), fs(g0.y, py));
-                const bool hit = !done && !(power > 0.0f || power < g1.y);
-                if (__any_sync(0xffffffffu, hit)) {
-                    if (kCount) {
-                        c_hits += hit ? 1u : 0u;
-                        ++c_active;
-                    }
-                    float alpha = fm(g1.z, exp_nonpos(fminf(power, 0.0f)));
+        float (*pw)[32] = H.pw[warp];
+        const uint32_t nmax = max(n0, n1);
+        for (uint32_t i0 = 0; i0 < nmax; i0 += kGroup) {
+            if (__all_sync(0xffffffffu, done)) break;
+            const uint32_t ngw = min((uint32_t)kGroup, nmax - i0);
+            const uint32_t g0n = n0 > i0 ? min((uint32_t)kGroup, n0 - i0) : 0u;
+            const uint32_t g1n = n1 > i0 ? min((uint32_t)kGroup, n1 - i0) : 0u;
+            const uint32_t ng = half ? g1n : g0n;
+            // colours of the group's entries, fetched now and stored after the tests
+            uint32_t ja = 0, jb = 0;
+            float4 ca = make_float4(0.f, 0.f, 0.f, 0.f), cb = ca;
+            if (lane < g0n) {
+                ja = H.hl[hb0][i0 + lane];
+                uint32_t m = H.vals[off + ja];
+                if (m >= M) m = 0;
+                ca = __ldg(reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride) + 2);
+            }
+            if (lane < g1n) {
+                jb = H.hl[hb1][i0 + lane];
+                uint32_t m = H.vals[off + jb];
+                if (m >= M) m = 0;
+                cb = __ldg(reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride) + 2);
+            }
+            const bool done0 = done;
+            uint32_t hits = half_group_tests(H.g0, H.g1, myl + i0, ngw, ng, px, py, pw, lane);
+            if (done) hits = 0;
+            if (lane < g0n) H.grp[warp][0][lane] = make_float4(H.g1[ja].z, ca.x, ca.y, ca.z);
+            if (lane < g1n) H.grp[warp][1][lane] = make_float4(H.g1[jb].z, cb.x, cb.y, cb.z);
+            __syncwarp();
+            const float4* grp = H.grp[warp][half];
+            uint32_t proc = 0, n_eval = ng;
+            while (__any_sync(0xffffffffu, hits != 0u)) {
+                if (hits) {
+                    const uint32_t e = __ffs(hits) - 1;
+                    hits &= hits - 1u;
+                    const float4 qv = grp[e];
+                    float alpha = fm(qv.x, exp_nonpos(pw[e][lane]));
                     alpha = alpha < 0.99f ? alpha : 0.99f;
                     const float Tn = fm(T, fs(1.0f, alpha));
-                    const bool stop = hit && Tn < 0.0001f;     // stop before adding this Gaussian
-                    const bool apply = hit && !stop;
-                    if (kKeep && stop)
-                        keep_out[(size_t)y * cam.width + x] = make_uint2(__float_as_uint(T), s0 + j);
-                    const float4 g2 = S.g2[j];
-                    w = apply ? alpha * T : 0.0f;
-                    Cacc.x = fmaf(g2.x, w, Cacc.x);
-                    Cacc.y = fmaf(g2.y, w, Cacc.y);
-                    Cacc.z = fmaf(g2.z, w, Cacc.z);
-                    T = apply ? Tn : T;
-                    done = done || stop;
-                }
-                if (kKpc) {
-                    // Eq. 5: sum of alpha * T over the warp's pixels for this pair
-    #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-                    if (lane == 0) S.kpc_w[warp][j] = w;
-                }
-            }
-        } else {
-            // Groups of kGroup list entries.  Phase 1, in lockstep: every lane
-            // tests every entry of the group, keeps a bit per entry it applies
-            // and parks its binary32 power in shared memory.  Phase 2: every
-            // lane applies its own entries in list order, the lanes of the warp
-            // working on different entries at once, so the alpha / T / colour
-            // work is spent only on pixels that apply.  A lane that stops drops
-            // its remaining bits.  Each lane performs exactly the operations of
-            // the one-entry-at-a-time walk, in the same order, so every
-            // decision is unchanged.
-            float (*pw)[32] = Gs.pw[warp];
-            float4* grp = Gs.grp[warp];
-            for (uint32_t i0 = 0; i0 < wcnt; i0 += kGroup) {
-                if (__all_sync(0xffffffffu, done)) break;
-                const uint32_t ng = min((uint32_t)kGroup, wcnt - i0);
-                const bool done0 = done;
-                uint32_t hits = group_tests(S.g0, S.g1, &S.wlist[warp][i0], ng, px, py, pw, lane);
-                if (done) hits = 0;
-                if (lane < ng) {
-                    const uint32_t j = S.wlist[warp][i0 + lane];
-                    const float4 c = S.g2[j];
-                    grp[lane] = make_float4(S.g1[j].z, c.x, c.y, c.z);
-                }
-                __syncwarp();
-                uint32_t proc = 0, n_eval = ng;
-                while (__any_sync(0xffffffffu, hits != 0u)) {
-                    if (hits) {
-                        const uint32_t e = __ffs(hits) - 1;
-                        hits &= hits - 1u;
-                        const float4 q = grp[e];
-                        float alpha = fm(q.x, exp_nonpos(pw[e][lane]));
-                        alpha = alpha < 0.99f ? alpha : 0.99f;
-                        const float Tn = fm(T, fs(1.0f, alpha));
-                        if (kCount) {
-                            ++c_hits;
-                            proc |= 1u << e;
-                        }
-                        if (Tn < 0.0001f) {
-                            done = true;                    // stop before adding this Gaussian
-                            hits = 0;
-                            n_eval = e + 1;
-                            if (kKeep)
-                                keep_out[(size_t)y * cam.width + x] =
-                                    make_uint2(__float_as_uint(T), s0 + S.wlist[warp][i0 + e]);
-                        } else {
-                            const float w = alpha * T;
-                            Cacc.x = fmaf(q.y, w, Cacc.x);
-                            Cacc.y = fmaf(q.z, w, Cacc.y);
-                            Cacc.z = fmaf(q.w, w, Cacc.z);
-                            T = Tn;
-                        }
+                    if (kCount) {
+                        ++c_hits;
+                        proc |= 1u << e;
+                    }
+                    if (Tn < 0.0001f) {
+                        done = true;                    // stop before adding this Gaussian
+                        hits = 0;
+                        n_eval = e + 1;
+                        if (kKeep)
+                            keep_out[(size_t)y * cam.width + x] = make_uint2(__float_as_uint(T), s0 + myl[i0 + e]);
+                    } else {
+                        const float w = alpha * T;
+                        Cacc.x = fmaf(qv.y, w, Cacc.x);
+                        Cacc.y = fmaf(qv.z, w, Cacc.y);
+                        Cacc.z = fmaf(qv.w, w, Cacc.z);
+                        T = Tn;
                     }
                 }
-                __syncwarp();
-                if (kCount) {
-                    c_entries += ng;
-                    c_evals += warp_sum_u32(done0 ? 0u : n_eval);
-                    c_active += __popc(__reduce_or_sync(0xffffffffu, proc));
-                }
+            }
+            __syncwarp();
+            if (kCount) {
+                c_entries += ngw;
+                c_evals += warp_sum_u32(done0 ? 0u : n_eval);
+                c_active += __popc(__reduce_or_sync(0xffffffffu, proc));
             }
         }
         if (kCount) {
@@ -397,20 +542,8 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
                 atomicAdd(&st->blend_active, (unsigned long long)c_active);
             }
         }
-        if (kKpc) {
-            __syncthreads();
-            if (tid < cnt) {
-                const uint32_t msk = S.wmask[tid];
-                float k = 0.0f;
-#pragma unroll
-                for (int w8 = 0; w8 < 8; ++w8)
-                    if ((msk >> w8) & 1u) k += S.kpc_w[w8][tid];
-                kpc_out[s0 + tid] = k;
-                kpc_acc += (double)k;
-            }
-        }
         const int n_done = __syncthreads_count(done);
-        if (!kKpc && n_done == (int)blockDim.x) break;
+        if (n_done == (int)blockDim.x) break;
     }
     if (inside && rgb) {
         const size_t hw = (size_t)cam.width * cam.height;
@@ -420,19 +553,6 @@ __device__ __forceinline__ void blend_tile(const DevCamera& cam, uint32_t tile, 
         rgb[2 * hw + pix] = fmaf(T, cam.bg[2], Cacc.z);
         if (Tout) Tout[pix] = T;
         if (kKeep && !done) keep_out[pix] = make_uint2(__float_as_uint(T), e);   // did not stop
-    }
-    if (kKpc) {
-        // Eq. 6: G = mean KPC over the tile's pairs; fixed-order block reduction
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) kpc_acc += __shfl_xor_sync(0xffffffffu, kpc_acc, o);
-        if (lane == 0) s_red[warp] = kpc_acc;
-        __syncthreads();
-        if (tid == 0) {
-            const uint32_t n = e - s;
-            double sum = 0.0;
-            for (int w8 = 0; w8 < 8; ++w8) sum += s_red[w8];
-            G_out[gtile] = n > 0 ? (float)(sum / (double)n) : __int_as_float(0x7fc00000);
-        }
     }
 }
 
