@@ -126,10 +126,11 @@ typedef struct fgs_stats {
     uint64_t n_pairs;         /* N_P: Gaussian-tile pairs (may exceed capacity on error) */
     uint32_t n_launches;      /* kernels this call enqueued */
     int32_t device_status;    /* latched device status (FGS_OK if none) */
-    uint64_t blend_entries;   /* FGS_RENDER_COUNT: per-warp list entries the blend walked */
+    uint64_t blend_entries;   /* FGS_RENDER_COUNT: lockstep warp steps of the blend's list walk
+                                 (a step tests one list entry in each half of a warp) */
     uint64_t blend_evals;     /* FGS_RENDER_COUNT: pixel-Gaussian evaluations (pixels not stopped) */
     uint64_t blend_hits;      /* FGS_RENDER_COUNT: evaluations that reached alpha / T (exp taken) */
-    uint64_t blend_active;    /* FGS_RENDER_COUNT: warp-list entries where some pixel reached it */
+    uint64_t blend_active;    /* FGS_RENDER_COUNT: lockstep steps where some pixel reached it */
 } fgs_stats;
 
 /* Library version (FGS_VERSION). */

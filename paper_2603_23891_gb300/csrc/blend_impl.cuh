@@ -72,8 +72,9 @@ struct BlendSmem {
     int timed_out;
 };
 
-// Per-warp scratch of the group walk (see blend_tile): each lane's binary32
-// power for every entry of the group, and the entries' alpha0 and colour.
+// Per-warp scratch of the backward's group walk over per-warp lists: each
+// lane's binary32 power for every entry of the group, and the entries' alpha0
+// and colour.  (The forward's half-block walk keeps the same in HalfSmem.)
 constexpr int kGroup = 32;
 template <bool kUsed>
 struct GroupSmem {
@@ -402,7 +403,13 @@ __device__ __forceinline__ uint32_t half_group_tests(const float4* __restrict__ 
 }
 
 // Blend one image tile with half-block lists (the forward without KPC).
-// Arguments as blend_tile.
+// `tile` is the tile in the camera's grid; `gtile` indexes ranges (the same
+// for one view; the batch's global tile id).  rgb / Tout are the camera's own
+// image planes.  With kKeep, keep_out receives per pixel {final T bits, stop
+// position}: the sorted-pair index of the Gaussian the pixel stopped at, or the
+// tile's end if it did not stop; the differentiable form's backward walks each
+// pixel from there.  kCount adds the work counters of FrameState (lockstep
+// warp steps, evaluations, alpha applications, steps with an application).
 template <bool kCount = false, bool kKeep = false>
 __device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t tile, uint32_t gtile,
                                                 HalfSmem& H, const uint2* __restrict__ ranges,

@@ -81,10 +81,10 @@ struct FrameState {
     int32_t status;            // latched error (0 = ok)
     uint32_t status_info;
     uint32_t hist[kMaxSortPasses][256];   // radix digit histograms
-    unsigned long long blend_entries;     // warp-list entries walked (counting frames only)
+    unsigned long long blend_entries;     // lockstep warp steps of the list walk (counting frames only)
     unsigned long long blend_evals;       // pixel-Gaussian evaluations (lanes not yet stopped)
     unsigned long long blend_hits;        // evaluations that reached the alpha / T update
-    unsigned long long blend_active;      // warp-list entries where some lane reached it
+    unsigned long long blend_active;      // lockstep steps where some lane reached it
     uint32_t n_emitting;                  // selected Gaussians with at least one pair
 
 };

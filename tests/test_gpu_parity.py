@@ -289,7 +289,7 @@ def test_levelwise_baseline_selects_same_set(renderer, seed):
 
 def test_blend_counters_consistent(renderer, tiny):
     """The counting blend variant renders the same image and reports consistent work:
-    alpha-applying evaluations <= evaluations <= 32 x warp-list entries."""
+    alpha-applying evaluations <= evaluations <= 32 x lockstep warp steps."""
     import torch
     tree, cam = tiny
     renderer.load_tree(tree)
