@@ -267,9 +267,24 @@ int fgs_calibrate_gtc(fgs_ctx* ctx, void* stream, const fgs_camera* views, int n
                       float lambda_G, double* gbar_views_out, float* tau_out, float* ln_tau_out);
 
 /* Diagnostic: evaluate the blend's binary32 exp (Cody-Waite reduction,
- * degree-7 Taylor polynomial) on n device floats x -> y (device pointers) on
- * `stream`.  Asynchronous.  Errors: FGS_ERR_ARG, FGS_ERR_CUDA. */
+ * degree-7 Taylor polynomial, fused multiply-adds in a fixed order) on n device
+ * floats x -> y (device pointers) on `stream`.  Asynchronous.  Errors:
+ * FGS_ERR_ARG, FGS_ERR_CUDA. */
 int fgs_eval_exp(const float* x, float* y, uint64_t n, void* stream);
+
+/* Diagnostic of the failure detection (no counterpart in the paper): launches
+ * one warp that waits, through the decoupled look-back wait the compaction
+ * uses, on a predecessor entry that nothing publishes (a tag no frame uses).
+ * The wait gives up after 4096 empty rounds (milliseconds; the render's waits
+ * allow 2^24) and latches the device status FGS_ERR_TIMEOUT, as a wait that
+ * runs out in a frame does; the kernel then returns.  The call clears any
+ * earlier status, synchronises `stream`, reads the status, clears it again and
+ * returns it: FGS_ERR_TIMEOUT (with *site_out = 0x7F0, the probe's site code)
+ * is the expected result; FGS_OK would mean the wait ended without its bound.
+ * The context stays usable.  Needs a loaded tree (its look-back buffer); do not
+ * overlap it with a render of the same context on another stream.  Errors:
+ * FGS_ERR_ARG, FGS_ERR_STATE, FGS_ERR_CUDA. */
+int fgs_probe_wait_timeout(fgs_ctx* ctx, void* stream, uint32_t* site_out);
 
 /* Allocation-free compaction of selection bits (no counterpart in the paper:
  * a service for callers that cannot allocate device memory, e.g. a host

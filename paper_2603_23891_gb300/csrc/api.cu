@@ -1005,6 +1005,24 @@ int fgs_eval_exp(const float* x, float* y, uint64_t n, void* stream)
     return cudaGetLastError() == cudaSuccess ? FGS_OK : FGS_ERR_CUDA;
 }
 
+int fgs_probe_wait_timeout(fgs_ctx* c, void* stream, uint32_t* site_out)
+{
+    if (!c) return FGS_ERR_ARG;
+    if (!c->has_tree) return fail(c, FGS_ERR_STATE, "no tree loaded");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int r;
+    if ((r = clear_status(c, s))) return r;
+    launch_wait_probe(c->lb_compact, c->st, s);
+    FGS_CUDA(c, cudaGetLastError());
+    if ((r = read_state(c, s))) return r;
+    if (site_out) *site_out = c->st_host->status_info;
+    r = latched_status(c);
+    if (r) clear_status(c, s);
+    FGS_CUDA(c, cudaStreamSynchronize(s));
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // differentiable form
 // ---------------------------------------------------------------------------

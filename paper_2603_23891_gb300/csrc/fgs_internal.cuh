@@ -259,8 +259,9 @@ __device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v)
 // per-tile values published in lb[] (one 64-bit entry per tile).  Lane l reads
 // predecessor (base - l), so each round trip inspects 32 tiles; entries are
 // consumed nearest-first up to the first inclusive one.  Tiles below 0 count
-// as an inclusive zero.  Bounded: after kSpinLimit empty rounds the status is
+// as an inclusive zero.  Bounded: after kLimit empty rounds the status is
 // latched and the partial prefix returned.  All lanes return the same value.
+template <uint64_t kLimit = kSpinLimit>
 __device__ __forceinline__ uint32_t warp_lookback(const unsigned long long* lb, uint32_t tile,
                                                   uint32_t tag, FrameState* st, uint32_t site)
 {
@@ -288,7 +289,7 @@ __device__ __forceinline__ uint32_t warp_lookback(const unsigned long long* lb, 
         prefix += warp_sum_u32(lane < take ? val : 0u);
         if (inc) break;
         if (take == 0) {
-            if (++spins > kSpinLimit) {
+            if (++spins > kLimit) {
                 set_status(st, kErrTimeout, site);
                 break;
             }
@@ -338,6 +339,12 @@ void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits,
 void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, int blocks,
                        cudaStream_t s);
 // Writes at most cap ids; more survivors latch FGS_ERR_CAPACITY and M = cap.
+// Failure-detection probe: one warp waits through warp_lookback on an entry of
+// lb that nothing publishes (a tag no frame uses), gives up after kProbeSpins
+// empty rounds and latches kErrTimeout with site kProbeSite.
+constexpr uint64_t kProbeSpins = 4096;
+constexpr uint32_t kProbeSite = 0x7F0u;
+void launch_wait_probe(const unsigned long long* lb, FrameState* st, cudaStream_t s);
 void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel, uint32_t cap,
                     unsigned long long* lookback, FrameState* st, int blocks, cudaStream_t s);
 void launch_project_emit(const DevTree& t, const DevCamera& cam, const uint32_t* sel,

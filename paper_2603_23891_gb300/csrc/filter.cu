@@ -277,6 +277,19 @@ __global__ void __launch_bounds__(256) compact_kernel(const uint32_t* __restrict
     }
 }
 
+// One warp looks back from tile 1 at tile 0 with a tag whose low four bits
+// (15) no frame uses (frames tag epoch * 16 + 0, 2..9), so entry 0 never reads as
+// ready and the wait ends by its bound.
+__global__ void wait_probe_kernel(const unsigned long long* lb, FrameState* st)
+{
+    (void)warp_lookback<kProbeSpins>(lb, 1u, 0x3FFFFFFFu, st, kProbeSite);
+}
+
+void launch_wait_probe(const unsigned long long* lb, FrameState* st, cudaStream_t s)
+{
+    wait_probe_kernel<<<1, 32, 0, s>>>(lb, st);
+}
+
 void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel, uint32_t cap,
                     unsigned long long* lookback, FrameState* st, int blocks, cudaStream_t s)
 {

@@ -41,7 +41,7 @@ EXPORTED = ["fgs_version", "fgs_create", "fgs_destroy", "fgs_last_error", "fgs_s
             "fgs_calibrate_view", "fgs_calibrate_gtc", "fgs_sync", "fgs_validate_tree",
             "fgs_eval_exp", "fgs_compact_selection_noalloc", "fgs_filter_levelwise",
             "fgs_batch_setup", "fgs_batch_set_cameras", "fgs_batch_image_offsets", "fgs_render_batch",
-            "fgs_update_params", "fgs_backward", "fgs_kpc_view"]
+            "fgs_update_params", "fgs_backward", "fgs_kpc_view", "fgs_probe_wait_timeout"]
 
 FGS_BACKWARD_ACCUMULATE = 1
 GRAD_FIELDS = ("mu", "log_scale", "quat", "logit", "sh")
@@ -122,6 +122,7 @@ def lib():
         "fgs_sync": ([vp, vp], i32),
         "fgs_validate_tree": ([C.POINTER(fgs_tree), C.c_char_p, C.c_size_t], i32),
         "fgs_eval_exp": ([vp, vp, u64, vp], i32),
+        "fgs_probe_wait_timeout": ([vp, vp, C.POINTER(u32)], i32),
         "fgs_compact_selection_noalloc": ([vp, u64, vp, vp, vp], i32),
         "fgs_filter_levelwise": ([vp, vp, vp, u32, vp, i32, vp], i32),
         "fgs_batch_setup": ([vp, vp, i32, vp, u64, u64], i32),
@@ -361,6 +362,14 @@ def fgs_sync(ctx, stream):
     return _check(ctx, lib().fgs_sync(ctx, stream))
 
 
+def fgs_probe_wait_timeout(ctx, stream):
+    """Run the bounded-wait probe; returns (status code, site).  The expected
+    result is (FGS_ERR_TIMEOUT, 0x7F0); no exception is raised for it."""
+    site = C.c_uint32(0)
+    code = lib().fgs_probe_wait_timeout(ctx, stream, C.byref(site))
+    return code, site.value
+
+
 def _gauss_struct(cls, arrays):
     return cls(*[_ptr(arrays[k]).value for k in GRAD_FIELDS])
 
@@ -530,6 +539,10 @@ class Renderer:
 
     def sync(self):
         fgs_sync(self.ctx, self.stream)
+
+    def probe_wait_timeout(self):
+        """Failure-detection probe (fgs_probe_wait_timeout): (status, site)."""
+        return fgs_probe_wait_timeout(self.ctx, self.stream)
 
     # ---- batched multi-view form
     def batch_setup(self, cams, tile_shapes=None, sel_capacity=0, pair_capacity=0):

@@ -287,6 +287,24 @@ def test_levelwise_baseline_selects_same_set(renderer, seed):
             assert 1 <= levels <= tree.depth + 1
 
 
+def test_bounded_wait_times_out_and_context_stays_usable(renderer, tiny):
+    """Failure detection without a GPU fault: a look-back wait on an entry that nothing
+    publishes gives up after its bound, the host reads FGS_ERR_TIMEOUT with the probe's
+    site code, and the next frames render bit-exactly as before."""
+    from paper_2603_23891_gb300 import filtergs
+    tree, cam = tiny
+    renderer.load_tree(tree)
+    before = gpu_frame(renderer, tree, cam, 1.0)
+    for _ in range(2):
+        code, site = renderer.probe_wait_timeout()
+        assert code == filtergs.FGS_ERR_TIMEOUT and site == 0x7F0
+    renderer.sync()                                 # the status was cleared by the probe
+    after = gpu_frame(renderer, tree, cam, 1.0)
+    o, _ = oracle_frame(tree, cam, 1.0)
+    assert_frame_parity(after, o)
+    assert np.array_equal(after["rgb"], before["rgb"]) and np.array_equal(after["T"], before["T"])
+
+
 def test_blend_counters_consistent(renderer, tiny):
     """The counting blend variant renders the same image and reports consistent work:
     alpha-applying evaluations <= evaluations <= 32 x lockstep warp steps."""
