@@ -1,0 +1,43 @@
+"""bench.py host logic on CPU: the clock / throttle sampler reads the sampling
+tool's CSV from a pipe and summarises it (a fake tool stands in for nvidia-smi)."""
+import sys
+import time
+
+import bench
+
+FAKE = ("import sys, time\n"
+        "rows = ['0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active',\n"
+        "        '0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active',\n"
+        "        '0, 2070, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active']\n"
+        "for r in rows:\n"
+        "    print(r, flush=True)\n"
+        "    time.sleep(0.05)\n"
+        "time.sleep(30)\n")
+
+
+def test_clock_sampler_reads_the_pipe_and_reports_reasons():
+    s = bench.ClockSampler(0, cmd=[sys.executable, "-c", FAKE])
+    s.start()
+    t0 = time.time()
+    while len(s.lines) < 3 and time.time() - t0 < 20:
+        time.sleep(0.05)
+    out = s.stop()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_of_throttled_and_malformed_lines():
+    lines = ["0, 1400, 2070, 1400, 0x8, Active, Not Active, Active, Not Active",
+             "garbage", "0, N/A, 2070, 1, 0, Not Active, Not Active, Not Active, Not Active",
+             "0, 1500, 2070, 1400, 0x8, Not Active, Active, Not Active, Not Active"]
+    out = bench.ClockSampler.summarise(lines)
+    assert out["samples"] == 2 and out["sm_mhz"] == 1450.0
+    assert out["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_sampler_without_the_tool():
+    s = bench.ClockSampler(0, cmd=["/nonexistent/sampler-tool"])
+    s.start()
+    out = s.stop()
+    assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
