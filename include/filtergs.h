@@ -294,9 +294,10 @@ int fgs_probe_wait_timeout(fgs_ctx* ctx, void* stream, uint32_t* site_out);
  * index 32 w + b) in ascending order to ids_out, and their number to
  * count_out[0] (0xFFFFFFFF if a bounded device wait timed out).  All pointers
  * are device pointers; ids_out must hold every set bit (at most 32 * n_words
- * indices).  Runs the render path's compaction kernel, but its scratch (look-back
- * words and a small state block, 512 KiB + 256 B) is a static device array of
- * the library, so the call allocates nothing.  Limit: n_words <= 2^26
+ * indices).  Runs the render path's compaction kernel, but its scratch (one
+ * 64-bit look-back word per 32K-index tile, 512 KiB, and an 8,448-byte state
+ * block: 532,736 bytes, 520.25 KiB) is a static device array of the library,
+ * so the call allocates nothing.  Limit: n_words <= 2^26
  * (2^31 indices); larger inputs return FGS_ERR_ARG before any launch.  The
  * first call on a device looks the array's address up (cudaGetSymbolAddress);
  * make that first call before any stream capture.  All calls share the one
@@ -340,6 +341,27 @@ int fgs_batch_image_offsets(const fgs_ctx* ctx, uint64_t* offsets_out);
  * Errors: FGS_ERR_STATE (no set-up), FGS_ERR_CAPACITY (with STATS), CUDA. */
 int fgs_render_batch(fgs_ctx* ctx, void* stream, float* rgb_out, float* T_out, uint32_t flags,
                      fgs_stats* st);
+
+/* Copy the intermediate results of the last fgs_render_batch, so that each
+ * view can be checked against the single-view path: the selected entries
+ * (entry = view * node_stride + node, ascending: view, then node id), their
+ * projected splats (float [M][12], fields as fgs_get_splats, in entry order)
+ * and the sorted Gaussian-tile pairs of the whole batch (keys
+ * (global tile << 32 | depth bits), values = index of the entry in the
+ * selected list).  View v's global tiles are [tile_base_out[v],
+ * tile_base_out[v + 1]) (n_views + 1 values); its tile t (row-major in its own
+ * tile grid) has the global id tile_base_out[v] + t.  All outputs are HOST
+ * buffers; any of the arrays may be NULL; at most sel_cap entries / splat rows
+ * and pair_cap pairs are copied; *M_out and *NP_out receive the batch totals.
+ * With every array NULL the call only reports the totals (a size query).
+ * Synchronising.  Errors: FGS_ERR_ARG, FGS_ERR_STATE (no batch rendered since
+ * the set-up or the last tree load), FGS_ERR_CAPACITY (a total above the cap
+ * of an array that was given, or a capacity error latched by the render),
+ * FGS_ERR_TIMEOUT, FGS_ERR_CUDA. */
+int fgs_batch_get_frame(fgs_ctx* ctx, void* stream, uint32_t* entries_out, float* splat_out,
+                        uint64_t sel_cap, uint64_t* M_out, uint64_t* keys_out, uint32_t* vals_out,
+                        uint64_t pair_cap, uint64_t* NP_out, uint32_t* node_stride_out,
+                        uint32_t* tile_base_out);
 
 /* ---- differentiable form -----------------------------------------------
  * The render as a function of per-node Gaussian parameters, in the 3D Gaussian

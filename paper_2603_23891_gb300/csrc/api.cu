@@ -129,6 +129,7 @@ struct fgs_ctx {
         float* graph_rgb = nullptr;
         float* graph_T = nullptr;
         bool sorted_in_1 = false;
+        bool have_frame = false;                  // a batch has been rendered since the set-up
     } batch;
 };
 
@@ -575,6 +576,7 @@ int fgs_load_tree(fgs_ctx* c, const fgs_tree* t)
     c->tree_mem = nullptr;
     c->has_tree = false;
     c->have_frame = false;
+    c->batch.have_frame = false;
     FGS_CUDA(c, cudaMalloc(&c->tree_mem, total));
     FGS_CUDA(c, cudaMemset(c->tree_mem, 0, total));
     char* base = (char*)c->tree_mem;
@@ -1114,6 +1116,7 @@ int fgs_batch_setup(fgs_ctx* c, const fgs_camera* views, int n_views, const int3
         b.graph = nullptr;
     }
     b.V = n_views;
+    b.have_frame = false;
     b.cams.assign(views, views + n_views);
     b.tile_w.assign(n_views, c->params.tile_w);
     b.tile_h.assign(n_views, c->params.tile_h);
@@ -1261,6 +1264,7 @@ int fgs_render_batch(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, uin
         enqueue_batch(c, rgb_out, T_out, s);
     }
     FGS_CUDA(c, cudaGetLastError());
+    b.have_frame = true;
     if (st) {
         std::memset(st, 0, sizeof *st);
         st->n_launches = (uint32_t)launches;
@@ -1283,6 +1287,44 @@ int fgs_render_batch(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, uin
             return fail(c, FGS_ERR_CAPACITY, "batch selection %u exceeds capacity %llu", c->st_host->M,
                         (unsigned long long)b.sel_cap);
     }
+    return FGS_OK;
+}
+
+int fgs_batch_get_frame(fgs_ctx* c, void* stream, uint32_t* entries_out, float* splat_out,
+                        uint64_t sel_cap, uint64_t* M_out, uint64_t* keys_out, uint32_t* vals_out,
+                        uint64_t pair_cap, uint64_t* NP_out, uint32_t* node_stride_out,
+                        uint32_t* tile_base_out)
+{
+    if (!c || !M_out || !NP_out) return FGS_ERR_ARG;
+    auto& b = c->batch;
+    if (b.V == 0 || !b.have_frame) return fail(c, FGS_ERR_STATE, "no batch rendered");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    FGS_CUDA(c, cudaMemcpyAsync(c->st_host, b.st, sizeof(FrameState), cudaMemcpyDeviceToHost, s));
+    FGS_CUDA(c, cudaStreamSynchronize(s));
+    const uint64_t M = c->st_host->M, np = c->st_host->n_pairs;
+    *M_out = M;
+    *NP_out = np;
+    if (node_stride_out) *node_stride_out = (uint32_t)c->tree.n_pad;
+    if (tile_base_out)
+        for (int v = 0; v <= b.V; ++v) tile_base_out[v] = b.tile_base[v];
+    const uint64_t m = std::min<uint64_t>(std::min<uint64_t>(M, b.sel_cap), sel_cap);
+    const uint64_t n = std::min<uint64_t>(std::min<uint64_t>(np, b.pair_cap), pair_cap);
+    if (m && entries_out) FGS_CUDA(c, cudaMemcpyAsync(entries_out, b.sel, m * 4, cudaMemcpyDeviceToHost, s));
+    if (m && splat_out)
+        FGS_CUDA(c, cudaMemcpyAsync(splat_out, b.splat, m * kSplatStride * 4, cudaMemcpyDeviceToHost, s));
+    if (n && keys_out)
+        FGS_CUDA(c, cudaMemcpyAsync(keys_out, b.sorted_in_1 ? b.keys1 : b.keys0, n * 8, cudaMemcpyDeviceToHost, s));
+    if (n && vals_out)
+        FGS_CUDA(c, cudaMemcpyAsync(vals_out, b.sorted_in_1 ? b.vals1 : b.vals0, n * 4, cudaMemcpyDeviceToHost, s));
+    FGS_CUDA(c, cudaStreamSynchronize(s));
+    if (c->st_host->status)
+        return fail(c, c->st_host->status == kErrCapacity ? FGS_ERR_CAPACITY : FGS_ERR_TIMEOUT,
+                    "batch: device status %d", c->st_host->status);
+    if (((entries_out || splat_out) && M > sel_cap) || ((keys_out || vals_out) && np > pair_cap))
+        return fail(c, FGS_ERR_CAPACITY, "batch M %llu / N_P %llu exceed caps %llu / %llu",
+                    (unsigned long long)M, (unsigned long long)np, (unsigned long long)sel_cap,
+                    (unsigned long long)pair_cap);
     return FGS_OK;
 }
 

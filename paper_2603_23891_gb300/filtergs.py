@@ -41,7 +41,7 @@ EXPORTED = ["fgs_version", "fgs_create", "fgs_destroy", "fgs_last_error", "fgs_s
             "fgs_calibrate_view", "fgs_calibrate_gtc", "fgs_sync", "fgs_validate_tree",
             "fgs_eval_exp", "fgs_compact_selection_noalloc", "fgs_filter_levelwise",
             "fgs_batch_setup", "fgs_batch_set_cameras", "fgs_batch_image_offsets", "fgs_render_batch",
-            "fgs_update_params", "fgs_backward", "fgs_kpc_view", "fgs_probe_wait_timeout"]
+            "fgs_batch_get_frame", "fgs_update_params", "fgs_backward", "fgs_kpc_view", "fgs_probe_wait_timeout"]
 
 FGS_BACKWARD_ACCUMULATE = 1
 GRAD_FIELDS = ("mu", "log_scale", "quat", "logit", "sh")
@@ -129,6 +129,8 @@ def lib():
         "fgs_batch_set_cameras": ([vp, vp, i32], i32),
         "fgs_batch_image_offsets": ([vp, vp], i32),
         "fgs_render_batch": ([vp, vp, vp, vp, u32, C.POINTER(fgs_stats)], i32),
+        "fgs_batch_get_frame": ([vp, vp, vp, vp, u64, C.POINTER(u64), vp, vp, u64, C.POINTER(u64),
+                                 C.POINTER(u32), vp], i32),
         "fgs_update_params": ([vp, vp, C.POINTER(fgs_gauss_params)], i32),
         "fgs_backward": ([vp, vp, vp, C.POINTER(fgs_gauss_params), C.POINTER(fgs_gauss_grads), u32],
                          i32),
@@ -301,6 +303,16 @@ def fgs_batch_image_offsets(ctx, n_views: int) -> np.ndarray:
 def fgs_render_batch(ctx, stream, rgb_out, T_out, flags: int = 0, stats=None):
     return _check(ctx, lib().fgs_render_batch(ctx, stream, _ptr(rgb_out), _ptr(T_out), flags,
                                               C.byref(stats) if stats is not None else None))
+
+
+def fgs_batch_get_frame(ctx, stream, entries_out, splat_out, sel_cap: int, keys_out, vals_out,
+                        pair_cap: int, tile_base_out):
+    """Returns (M, N_P, node_stride) of the last batch; fills the host arrays given."""
+    m, n, stride = C.c_uint64(), C.c_uint64(), C.c_uint32()
+    _check(ctx, lib().fgs_batch_get_frame(ctx, stream, _ptr(entries_out), _ptr(splat_out), sel_cap,
+                                          C.byref(m), _ptr(keys_out), _ptr(vals_out), pair_cap,
+                                          C.byref(n), C.byref(stride), _ptr(tile_base_out)))
+    return int(m.value), int(n.value), int(stride.value)
 
 
 def fgs_render(ctx, stream, rgb_out, T_out, out_is_device: int, flags: int = 0, stats=None):
@@ -634,6 +646,36 @@ class Renderer:
             views.append((rgb[3 * o: 3 * o + 3 * n].view(3, cam.height, cam.width),
                           T[o: o + n].view(cam.height, cam.width)))
         return rgb, T, st, views
+
+    def batch_frame(self):
+        """Per-view intermediate results of the last batch, in the single-view
+        path's terms: a list of dicts with sel (node ids), splat rows, and the
+        view's sorted pairs with the tile ids and values made view-local."""
+        V = len(self.batch_cams)
+        tb = np.zeros(V + 1, np.uint32)
+        M, NP, stride = fgs_batch_get_frame(self.ctx, self.stream, None, None, 0, None, None, 0, tb)
+        ent = np.zeros(max(M, 1), np.uint32)
+        spl = np.zeros((max(M, 1), len(SPLAT_FIELDS)), np.float32)
+        keys = np.zeros(max(NP, 1), np.uint64)
+        vals = np.zeros(max(NP, 1), np.uint32)
+        fgs_batch_get_frame(self.ctx, self.stream, ent, spl, M, keys, vals, NP, tb)
+        ent, spl, keys, vals = ent[:M], spl[:M], keys[:NP], vals[:NP]
+        view = (ent // np.uint32(stride)).astype(np.int64)
+        first = np.searchsorted(view, np.arange(V + 1))
+        gtile = (keys >> np.uint64(32)).astype(np.int64)
+        pfirst = np.searchsorted(gtile, tb.astype(np.int64))
+        out = []
+        for v in range(V):
+            a, b = int(first[v]), int(first[v + 1])
+            pa, pb = int(pfirst[v]), int(pfirst[v + 1])
+            k = keys[pa:pb]
+            local_tile = (k >> np.uint64(32)) - np.uint64(tb[v])
+            out.append(dict(sel=(ent[a:b] - np.uint32(v * stride)).astype(np.uint32),
+                            splat=spl[a:b],
+                            keys=(local_tile << np.uint64(32)) | (k & np.uint64(0xFFFFFFFF)),
+                            vals=(vals[pa:pb].astype(np.int64) - a).astype(np.uint32),
+                            vals_global=vals[pa:pb], M=b - a, NP=pb - pa))
+        return out
 
 
 # ---------------------------------------------------------------- autograd

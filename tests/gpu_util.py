@@ -75,6 +75,17 @@ def assert_frame_parity(g, o, check_image=True):
     return None
 
 
+def batch_view_frame(bv, rgb_v=None, T_v=None):
+    """One view of a batched render (``Renderer.batch_frame()`` entry plus its image
+    planes) in the form ``assert_frame_parity`` takes."""
+    g = dict(sel=bv["sel"], M=bv["M"], NP=bv["NP"], splat=bv["splat"], keys=bv["keys"],
+             vals=bv["vals"])
+    if rgb_v is not None:
+        g["rgb"] = rgb_v.cpu().numpy()
+        g["T"] = T_v.cpu().numpy()
+    return g
+
+
 def orbit_cameras(tree, n, size, seed, dist=(8.0, 40.0), fov=(35.0, 80.0)):
     rng = np.random.default_rng(seed)
     c = tree.mu.mean(axis=1).astype(np.float64)

@@ -3,7 +3,9 @@
 1M-leaf blob tree at 1920x1080: every pose, shrink off and on, whole frames.
 10M-leaf city tree at 1920x1080 (the benchmark workload and launch configuration,
 adaptive shrink): sampled poses; selection, splats and pairs bit for bit, the
-image on sampled pixels that the oracle evaluates one by one."""
+image on sampled pixels that the oracle evaluates one by one.
+The batched form at its own workload's scale: the 32 city views of uneven resolution
+(360p to 2160p) in one CUDA-graph batch; sampled views against the oracle."""
 import math
 
 import numpy as np
@@ -12,7 +14,8 @@ import pytest
 import oracle
 from paper_2603_23891_gb300 import synth
 
-from gpu_util import IMG_TOL, assert_frame_parity, gpu_frame, grad_parity_case, oracle_frame, psnr
+from gpu_util import (IMG_TOL, assert_frame_parity, batch_view_frame, gpu_frame, grad_parity_case,
+                      oracle_frame, psnr)
 
 pytestmark = pytest.mark.gpu
 
@@ -109,3 +112,42 @@ def test_city_gradient_sampled_pixels(renderer, city):
                                     shrink=shrink, pix=pix)
     print(f"city pose 21: M={g['M']} N_P={g['NP']} worst relative gradient error "
           f"{max(worst.values()):.2e}")
+
+
+def test_city_batch_32_views_sampled(renderer, city):
+    """The 32-view batch over the city tree (8 views each at 640x360, 1280x720,
+    1920x1080, 3840x2160; tiles 16x16 with 8x4 warps and 32x8 with 4x8 warps
+    alternating; adaptive shrink at tau = 0.0772; CUDA-graph replay).  Six views, three
+    of them 3840x2160, against the oracle: selection (§3.2: equal to the serial
+    traversal), splat decision fields and the view's sorted pairs bit for bit, and
+    20,000 sampled pixels (transmittance bits, colour within the image tolerance)."""
+    import torch
+    tree, _ = city
+    renderer.load_tree(tree)
+    renderer.set_params(tau_R=3.0, tile=(16, 16))
+    shrink = (0.0772, float(np.float32(math.log(0.0772))))
+    renderer.shrink(*shrink)
+    bc = synth.city_batch_cameras()
+    shapes = [(16, 16, 8) if v % 2 == 0 else (32, 8, 4) for v in range(len(bc))]
+    renderer.batch_setup(bc, tile_shapes=shapes, sel_capacity=48 << 20, pair_capacity=64 << 20)
+    renderer.render_batch(graph=True, stats=True)
+    rgb, T, st, views = renderer.render_batch(graph=True, stats=True)
+    torch.cuda.synchronize()
+    frames = renderer.batch_frame()
+    assert sum(f["M"] for f in frames) == st.n_selected
+    assert sum(f["NP"] for f in frames) == st.n_pairs
+    rng = np.random.default_rng(1)
+    for v in (0, 9, 18, 27, 28, 31):
+        cam, (tw, th, _) = bc[v], shapes[v]
+        o, p = oracle_frame(tree, cam, 3.0, shrink=shrink, tile=(tw, th), blend=False)
+        assert_frame_parity(batch_view_frame(frames[v]), o, check_image=False)
+        n = cam.width * cam.height
+        pix = np.sort(rng.choice(n, size=20000, replace=False))
+        orgb, oT = oracle.render_pixels(o.splat, o.keys, o.vals, cam, p, pix)
+        grgb = views[v][0].cpu().numpy().reshape(3, -1)[:, pix].T.astype(np.float64)
+        gT = views[v][1].cpu().numpy().reshape(-1)[pix]
+        assert np.abs(grgb - orgb).max() <= IMG_TOL, v
+        assert np.array_equal(gT.view(np.uint32), oT.view(np.uint32)), v
+        print(f"batch view {v} ({cam.width}x{cam.height}, tile {tw}x{th}): M={frames[v]['M']} "
+              f"N_P={frames[v]['NP']} sampled max-abs {np.abs(grgb - orgb).max():.2e}")
+    renderer.shrink(None)
