@@ -54,3 +54,37 @@ def test_noalloc_compaction_matches_filter():
                                                       stream) == filtergs.FGS_ERR_ARG
     finally:
         r.close()
+
+
+def test_noalloc_many_tiles_back_to_back():
+    """Cross-tile look-back through the static scratch: 70, 23, 5 and 1 tiles (each
+    with a ragged tail), dense, sparse and empty words, checked bit for bit against
+    the set-bit positions computed on the host, every call."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_23891_gb300 import build, filtergs
+    build.build()
+    rng = np.random.default_rng(11)
+    stream = torch.cuda.current_stream().cuda_stream
+    words_per_tile = 1024
+    cases = [(70 * words_per_tile + 333, 0.5), (23 * words_per_tile + 17, 0.02),
+             (5 * words_per_tile + 1, 0.9), (words_per_tile - 7, 0.3), (70 * words_per_tile, 0.0),
+             (12 * words_per_tile + 500, 0.001)]
+    for n_words, density in cases:
+        bits01 = rng.random(n_words * 32) < density
+        if density > 0:
+            bits01[: 32 * 40] = True                 # a run of full words
+            bits01[32 * 100: 32 * 300] = False       # a run of empty words
+        words = np.packbits(bits01.reshape(-1, 32)[:, ::-1], axis=1).view(">u4").ravel().astype(np.uint32)
+        expect = np.flatnonzero(bits01).astype(np.uint32)
+        bits = torch.from_numpy(words.view(np.int32).copy()).cuda()
+        ids = torch.full((n_words * 32,), -1, dtype=torch.int32, device="cuda")
+        count = torch.zeros(1, dtype=torch.int32, device="cuda")
+        code = filtergs.fgs_compact_selection_noalloc(bits, n_words, ids, count, stream)
+        assert code == filtergs.FGS_OK
+        torch.cuda.synchronize()
+        m = int(count.cpu().numpy().view(np.uint32)[0])
+        assert m == expect.size, (n_words, density, m, expect.size)
+        got = ids[:m].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, expect), (n_words, density)
