@@ -1,7 +1,8 @@
 """CPU oracle of the FilterGS render path (TEST INFRASTRUCTURE).
 
-A plain serial C restatement of the per-frame LoD render path (``oracle.c``)
-behind ctypes.  Only the test-suite, ``__graft_entry__.smoke()`` and the
+A plain C restatement of the per-frame LoD render path (``oracle.c``) behind
+ctypes; serial by construction, its independent loops (nodes, Gaussians, tiles,
+pixels) optionally shared among OpenMP threads with bit-identical results.  Only the test-suite, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package; the product path never
 does.  It shares no code with the CUDA library.
 
@@ -42,14 +43,16 @@ SPLAT_STRIDE = len(SPLAT_FIELDS)
 
 def build_lib(force: bool = False) -> str:
     """Compile the oracle's C sources into liboracle.so beside them (plain gcc,
-    no contraction)."""
-    newest = max(os.path.getmtime(f) for f in _SRCS + [os.path.join(_HERE, "oracle.h")])
+    no contraction; with OpenMP where the compiler has it, else serial)."""
+    newest = max(os.path.getmtime(f) for f in _SRCS + [os.path.join(_HERE, "oracle.h"),
+                                                        os.path.abspath(__file__)])
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", *_SRCS, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c11", "-Wall", "-Wno-unknown-pragmas", "-ffp-contract=off", "-fno-fast-math",
+            "-fPIC", "-shared", *_SRCS, "-o", tmp, "-lm"]
+    if subprocess.run(base + ["-fopenmp"], capture_output=True).returncode != 0:
+        subprocess.run(base, check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -91,6 +94,8 @@ def lib():
         build_lib()
         L = C.CDLL(_LIB)
         vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.oracle_set_threads.argtypes = [C.c_int]
+        L.oracle_set_threads.restype = C.c_int
         L.oracle_expf.argtypes = [C.c_float]
         L.oracle_expf.restype = C.c_float
         L.oracle_sh_basis.argtypes = [C.c_int, vp, vp]
@@ -125,6 +130,12 @@ def lib():
         L.oracle_diff_grad.restype = C.c_int
         _lib = L
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads the oracle's loops use (n <= 0: unchanged); returns the count in
+    use (1 when built without OpenMP).  Results do not depend on it."""
+    return int(lib().oracle_set_threads(int(n)))
 
 
 def _p(a: np.ndarray):

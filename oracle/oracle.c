@@ -8,12 +8,32 @@
  * are noted where they are used.
  *
  * Must be compiled with -ffp-contract=off and without -ffast-math.
+ *
+ * Optional OpenMP (when built with -fopenmp): loops over nodes, selected
+ * Gaussians, tiles and pixels run in parallel.  Every parallel iteration
+ * writes its own outputs and each sum keeps its serial order (KPC is summed
+ * per tile, over the tile's pixels in row-major order, exactly as the serial
+ * loop over the image adds them), so results are bit-identical to one thread.
  */
 #include "oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 #define ALPHA_MAX 0.99f                     /* opacity clamp */
 #define ALPHA_MIN_LN 5.5412635451584258f   /* ln 255: skip below alpha 1/255 */
@@ -180,6 +200,7 @@ static oview view_node(const otree* t, const ocam* cam, int64_t n)
 int oracle_predicate(const otree* t, const ocam* c, float tau_R, uint8_t* P_out,
                      float* radius_out)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t n = 0; n < t->n; ++n) {
         oview o = view_node(t, c, n);
         float R2d = o.in_frustum ? 3.0f * sqrtf(o.lam) : NAN;
@@ -277,6 +298,7 @@ int64_t oracle_project(const otree* t, const ocam* c, const oparams* p, const ui
     const int32_t tiles_x = (c->width + p->tile_w - 1) / p->tile_w;
     const int32_t tiles_y = (c->height + p->tile_h - 1) / p->tile_h;
     int64_t n_pairs = 0;
+#pragma omp parallel for schedule(static) reduction(+ : n_pairs)
     for (int32_t m = 0; m < M; ++m) {
         const int64_t n = sel[m];
         float* s = splat_out + (int64_t)m * ORACLE_SPLAT_STRIDE;
@@ -360,20 +382,30 @@ int64_t oracle_pairs(const float* splat, const int32_t* rect, int32_t M, int32_t
     }
     if (total > cap) return -1;
     opair* pr = (opair*)malloc(sizeof(opair) * (size_t)(total > 0 ? total : 1));
+    /* Gaussian m's pairs start after those of Gaussians 0 .. m-1 */
+    int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(M > 0 ? M : 1));
     int64_t k = 0;
+    for (int32_t m = 0; m < M; ++m) {
+        const int32_t* rc = rect + (int64_t)m * 4;
+        start[m] = k;
+        k += (int64_t)(rc[1] - rc[0]) * (int64_t)(rc[3] - rc[2]);
+    }
+#pragma omp parallel for schedule(static)
     for (int32_t m = 0; m < M; ++m) {
         const int32_t* rc = rect + (int64_t)m * 4;
         float depth = splat[(int64_t)m * ORACLE_SPLAT_STRIDE + ORACLE_SPLAT_DEPTH];
         uint32_t dbits;
         memcpy(&dbits, &depth, sizeof dbits);
+        int64_t q = start[m];
         for (int32_t ty = rc[2]; ty < rc[3]; ++ty)
             for (int32_t tx = rc[0]; tx < rc[1]; ++tx) {
                 uint64_t tile = (uint64_t)ty * (uint64_t)tiles_x + (uint64_t)tx;
-                pr[k].key = (tile << 32) | dbits;
-                pr[k].val = (uint32_t)m;
-                ++k;
+                pr[q].key = (tile << 32) | dbits;
+                pr[q].val = (uint32_t)m;
+                ++q;
             }
     }
+    free(start);
     qsort(pr, (size_t)total, sizeof(opair), cmp_pair);
     for (int64_t i = 0; i < total; ++i) {
         keys_out[i] = pr[i].key;
@@ -471,25 +503,35 @@ static void tile_range(const uint64_t* keys, int64_t n_pairs, uint64_t tile, int
     *e = lo;
 }
 
+/* Every pixel blends the pairs of its own tile, so the image is rendered tile
+ * by tile; within a tile, pixels go row by row (the order in which a pair's
+ * KPC terms are added). */
 int oracle_render(const ocam* c, const oparams* p, const float* splat, const uint64_t* keys,
                   const uint32_t* vals, int64_t n_pairs, double* rgb_out, float* T_out,
                   double* kpc_out)
 {
     const int64_t W = c->width, H = c->height;
     const int32_t tiles_x = (c->width + p->tile_w - 1) / p->tile_w;
+    const int32_t tiles_y = (c->height + p->tile_h - 1) / p->tile_h;
     if (kpc_out) memset(kpc_out, 0, sizeof(double) * (size_t)n_pairs);
-    for (int64_t y = 0; y < H; ++y)
-        for (int64_t x = 0; x < W; ++x) {
-            const uint64_t tile = (uint64_t)(y / p->tile_h) * (uint64_t)tiles_x + (uint64_t)(x / p->tile_w);
-            int64_t b, e;
-            tile_range(keys, n_pairs, tile, &b, &e);
-            double rgb[3];
-            float T;
-            blend_pixel(splat, vals, b, e, (float)x + 0.5f, (float)y + 0.5f, rgb, &T, kpc_out, NULL, NULL);
-            for (int ch = 0; ch < 3; ++ch)
-                rgb_out[ch * W * H + y * W + x] = rgb[ch] + (double)T * (double)p->bg[ch];
-            T_out[y * W + x] = T;
-        }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t tile = 0; tile < (int64_t)tiles_x * tiles_y; ++tile) {
+        const int64_t ty = tile / tiles_x, tx = tile % tiles_x;
+        int64_t b, e;
+        tile_range(keys, n_pairs, (uint64_t)tile, &b, &e);
+        const int64_t y_end = (ty + 1) * p->tile_h < H ? (ty + 1) * p->tile_h : H;
+        const int64_t x_end = (tx + 1) * p->tile_w < W ? (tx + 1) * p->tile_w : W;
+        for (int64_t y = ty * p->tile_h; y < y_end; ++y)
+            for (int64_t x = tx * p->tile_w; x < x_end; ++x) {
+                double rgb[3];
+                float T;
+                blend_pixel(splat, vals, b, e, (float)x + 0.5f, (float)y + 0.5f, rgb, &T, kpc_out, NULL,
+                            NULL);
+                for (int ch = 0; ch < 3; ++ch)
+                    rgb_out[ch * W * H + y * W + x] = rgb[ch] + (double)T * (double)p->bg[ch];
+                T_out[y * W + x] = T;
+            }
+    }
     return 0;
 }
 
@@ -499,6 +541,7 @@ int oracle_render_pixels(const ocam* c, const oparams* p, const float* splat,
 {
     const int64_t W = c->width;
     const int32_t tiles_x = (c->width + p->tile_w - 1) / p->tile_w;
+#pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n_pix; ++i) {
         const int64_t x = pix[i] % W, y = pix[i] / W;
         const uint64_t tile = (uint64_t)(y / p->tile_h) * (uint64_t)tiles_x + (uint64_t)(x / p->tile_w);

@@ -21,6 +21,11 @@
  *   (0xFFFFFFFF past the root).
  *   splat[M][ORACLE_SPLAT_STRIDE] (see ORACLE_SPLAT_* below), rect[M][4] =
  *   x0, x1, y0, y1 (half-open tile ranges).
+ *
+ * Threads: built with OpenMP, the loops over nodes, selected Gaussians, tiles
+ * and pixels are shared among threads; results are bit-identical to one
+ * thread (no sum changes its order).  oracle_set_threads(n) sets the count
+ * (n <= 0 leaves it) and returns the count in use (1 without OpenMP).
  */
 #ifndef FILTERGS_ORACLE_H
 #define FILTERGS_ORACLE_H
@@ -77,6 +82,8 @@ void oracle_sh_basis(int deg, const double dir[3], double* out);
 
 /* R&L predicate P(n) of §3.2 for every node; radius_out[n] = 3*sqrt(lambda_max)
  * (NaN when out of frustum).  Returns 0. */
+int oracle_set_threads(int n);
+
 int oracle_predicate(const otree* t, const ocam* c, float tau_R, uint8_t* P_out,
                      float* radius_out);
 
