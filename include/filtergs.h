@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define FGS_VERSION 1
+#define FGS_VERSION 2
 
 #define FGS_OK 0
 #define FGS_ERR_ARG (-1)       /* invalid argument (NULL, size, NaN camera ...) */
@@ -131,6 +131,10 @@ typedef struct fgs_stats {
     uint64_t blend_evals;     /* FGS_RENDER_COUNT: pixel-Gaussian evaluations (pixels not stopped) */
     uint64_t blend_hits;      /* FGS_RENDER_COUNT: evaluations that reached alpha / T (exp taken) */
     uint64_t blend_active;    /* FGS_RENDER_COUNT: lockstep steps where some pixel reached it */
+    uint64_t filter_in_frustum;  /* FGS_RENDER_COUNT: nodes whose centre passes the frustum test */
+    uint64_t filter_cov_nodes;   /* FGS_RENDER_COUNT: in-frustum internal nodes, the only ones whose
+                                    covariance the R&L filter must read (a leaf passes on the
+                                    frustum test alone) */
 } fgs_stats;
 
 /* Library version (FGS_VERSION). */

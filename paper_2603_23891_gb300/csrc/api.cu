@@ -310,13 +310,13 @@ int check_ready(fgs_ctx* c)
 }
 
 // Enqueue the frame up to tile ranges.  Returns the number of kernel launches.
-int enqueue_front(fgs_ctx* c, const DevCamera& dc, cudaStream_t s, cudaEvent_t* ev)
+int enqueue_front(fgs_ctx* c, const DevCamera& dc, cudaStream_t s, cudaEvent_t* ev, bool count = false)
 {
     int launches = 0;
     const int tiles = dc.tiles_x * dc.tiles_y;
     if (ev) cudaEventRecord(ev[0], s);
     launch_frame_begin(c->st, c->ranges, tiles, s);
-    launch_filter_pred(c->tree, dc, c->pbits, c->sms * c->occ_pred, s);
+    launch_filter_pred(c->tree, dc, c->pbits, count ? c->st : nullptr, c->sms * c->occ_pred, s);
     launches += 2;
     if (ev) cudaEventRecord(ev[1], s);
     launch_filter_anc(c->tree, c->pbits, c->selbits, c->sms * c->occ_anc, s);
@@ -711,7 +711,7 @@ int fgs_filter(fgs_ctx* c, void* stream, uint32_t* sel_out, uint32_t cap, uint32
     cudaStream_t s = (cudaStream_t)stream;
     const DevCamera dc = make_devcam(c, false);
     launch_frame_begin(c->st, c->ranges, dc.tiles_x * dc.tiles_y, s);
-    launch_filter_pred(c->tree, dc, c->pbits, c->sms * c->occ_pred, s);
+    launch_filter_pred(c->tree, dc, c->pbits, nullptr, c->sms * c->occ_pred, s);
     launch_filter_anc(c->tree, c->pbits, c->selbits, c->sms * c->occ_anc, s);
     launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->tree.n_pad, c->lb_compact, c->st,
                    c->sms * c->occ_compact, s);
@@ -805,11 +805,11 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
         ev = c->ev[c->ev_count % kEventSlots];
         ++c->ev_count;
     }
-    int launches = enqueue_front(c, dc, s, ev);
+    const bool count = (flags & FGS_RENDER_COUNT) != 0;
+    int launches = enqueue_front(c, dc, s, ev, count);
     const size_t hw = (size_t)dc.width * dc.height;
     float* rgb_dst = out_is_device ? rgb_out : c->img;
     float* T_dst = out_is_device ? T_out : (T_out ? c->img + 3 * hw : nullptr);
-    const bool count = (flags & FGS_RENDER_COUNT) != 0;
     const bool keep = (flags & FGS_RENDER_KEEP) && !count;
     if (count) flags |= FGS_RENDER_STATS;
     launch_blend(dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, rgb_dst, T_dst,
@@ -839,6 +839,8 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
             st->blend_hits = c->st_host->blend_hits;
             st->blend_active = c->st_host->blend_active;
             st->n_emitting = c->st_host->n_emitting;
+            st->filter_in_frustum = c->st_host->filter_in_frustum;
+            st->filter_cov_nodes = c->st_host->filter_cov_nodes;
         }
         if ((r = latched_status(c))) {
             clear_status(c, s);

@@ -86,6 +86,8 @@ struct FrameState {
     unsigned long long blend_hits;        // evaluations that reached the alpha / T update
     unsigned long long blend_active;      // lockstep steps where some lane reached it
     uint32_t n_emitting;                  // selected Gaussians with at least one pair
+    unsigned long long filter_in_frustum; // counting frames: nodes in the frustum
+    unsigned long long filter_cov_nodes;  // counting frames: in-frustum internal nodes
 
 };
 
@@ -334,7 +336,7 @@ size_t sort_smem_bytes();
 // All launchers enqueue on `s` and read counts (M, N_P) from device memory,
 // so a frame needs no host synchronisation.
 void launch_frame_begin(FrameState* st, uint2* ranges, int n_tiles, cudaStream_t s);
-void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits, int blocks,
+void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits, FrameState* count_st, int blocks,
                         cudaStream_t s);
 void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, int blocks,
                        cudaStream_t s);

@@ -28,6 +28,8 @@ __global__ void frame_begin_kernel(FrameState* st, uint2* ranges, int n_tiles)
         st->blend_hits = 0;
         st->blend_active = 0;
         st->n_emitting = 0;
+        st->filter_in_frustum = 0;
+        st->filter_cov_nodes = 0;
     }
     if (tid < 16) st->tickets[tid] = 0;
     for (int i = tid; i < kMaxSortPasses * 256; i += gridDim.x * blockDim.x)
@@ -44,14 +46,18 @@ void launch_frame_begin(FrameState* st, uint2* ranges, int n_tiles, cudaStream_t
 
 // ---------------------------------------------------------------------------
 // R&L predicate: 4 consecutive nodes per thread, bits assembled per warp.
+// count_st (counting frames only, else null): in-frustum nodes and in-frustum
+// internal nodes are added to its filter counters, one atomic per warp.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) filter_pred_kernel(DevTree t, DevCamera cam, uint32_t* pbits)
+__global__ void __launch_bounds__(256) filter_pred_kernel(DevTree t, DevCamera cam, uint32_t* pbits,
+                                                          FrameState* count_st)
 {
     grid_dep_wait();
     grid_dep_trigger();
     const uint32_t n_chunks = t.n_pad >> 2;               // multiple of 32
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
+    uint32_t n_in = 0, n_cov = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_chunks; i += stride) {
         const uint32_t n0 = i << 2;
         if (i + stride < n_chunks) {
@@ -80,6 +86,8 @@ __global__ void __launch_bounds__(256) filter_pred_kernel(DevTree t, DevCamera c
         }
         uint32_t pnib = inf & leaf;                       // in-frustum leaves pass
         const uint32_t need = inf & ~leaf;                // in-frustum internal nodes
+        n_in += __popc(inf);
+        n_cov += __popc(need);
         if (need) {
             const float* c = t.cov;
             const size_t np = t.n_pad;
@@ -106,16 +114,23 @@ __global__ void __launch_bounds__(256) filter_pred_kernel(DevTree t, DevCamera c
         w |= __shfl_xor_sync(0xffffffffu, w, 4);
         if ((lane & 7) == 0) pbits[i >> 3] = w;
     }
+    if (count_st) {
+        const uint32_t a = warp_sum_u32(n_in), b = warp_sum_u32(n_cov);
+        if (lane == 0) {
+            atomicAdd(&count_st->filter_in_frustum, (unsigned long long)a);
+            atomicAdd(&count_st->filter_cov_nodes, (unsigned long long)b);
+        }
+    }
 }
 
-void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits, int blocks,
-                        cudaStream_t s)
+void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits, FrameState* count_st,
+                        int blocks, cudaStream_t s)
 {
     const uint32_t n_chunks = t.n_pad >> 2;
     int need = (int)((n_chunks + 255) / 256);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    launch_pdl(filter_pred_kernel, blocks, 256, 0, s, t, cam, pbits);
+    launch_pdl(filter_pred_kernel, blocks, 256, 0, s, t, cam, pbits, count_st);
 }
 
 // ---------------------------------------------------------------------------

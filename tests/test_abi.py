@@ -40,7 +40,7 @@ def test_exports_every_declared_symbol(lib):
     for name in declared:
         assert hasattr(L, name), name
     assert set(lib.EXPORTED) == declared
-    assert L.fgs_version() == 1
+    assert L.fgs_version() == 2
 
 
 def test_create_without_gpu_fails_cleanly(lib):

@@ -41,3 +41,24 @@ def test_clock_sampler_without_the_tool():
     s.start()
     out = s.stop()
     assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_cpu_baseline_leg_on_the_tiny_workload():
+    """The CPU-baseline leg: one-thread and all-thread rates of the oracle, and the
+    shrunk image against the unshrunk oracle (here the oracle's own shrunk image, so the
+    error is that of shrinking alone)."""
+    import math
+
+    import numpy as np
+
+    import oracle
+    tree, cams, tau_R, _ = bench.workload("tiny")
+    tau = 0.1
+    ln_tau = float(np.float32(math.log(tau)))
+    p = oracle.Params(tau_R=tau_R, shrink=True, tau=tau, ln_tau=ln_tau)
+    img = {0: oracle.frame(tree, cams[0], p).rgb.astype(np.float32)}
+    out = bench.cpu_baseline(tree, cams, tau_R, tau, ln_tau, img)
+    assert out["value"] > 0 and out["single_core"]["value"] > 0
+    assert out["cores"] >= 1 and out["single_core"]["cores"] == 1
+    e = out["shrink_vs_unshrunk_oracle"]["poses"][0]
+    assert e["pose"] == 0 and e["max_abs"] > 0 and 10 < e["psnr_db"] < 200
