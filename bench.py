@@ -1,8 +1,8 @@
 """Benchmark of the FilterGS LoD render path on one GB300 (or N replicas).
 
 One step = one whole frame of the render path (R&L filter, ancestor filter +
-compaction, projection + SH + shrink + key emission, onesweep sort, tile ranges,
-blending) for one camera pose of the synthetic workload, inputs resident in HBM.
+compaction, projection + SH + shrink + per-tile pair counts, tile ranges, key
+scatter into per-tile buckets, per-tile sort, blending) for one camera pose of the synthetic workload, inputs resident in HBM.
 
 Default workload: the 10M-leaf city tree (~12.5M nodes), 1920x1080, 64-pose
 flythrough, adaptive shrinking with tau calibrated over the 64 poses
@@ -33,7 +33,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-STAGES = ["filter_rl", "ancestor_compact", "project_keys", "sort", "tile_ranges", "blend"]
+STAGES = ["filter_rl", "ancestor_compact", "project", "tile_ranges", "keys", "sort", "blend"]
 METRIC = "1080p ms/frame & FPS on 10M-leaf LoD tree; GS-tile pairs/frame; HBM roofline %"
 
 
@@ -130,19 +130,25 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- roofline
 
-def algorithmic_bytes(tree, M, NP, width, height, sh_floats, E, n_cov):
+def algorithmic_bytes(tree, M, NP, width, height, sh_floats, E, n_cov, tiles):
     """Bytes the method must move per frame, per stage.  E: selected Gaussians that
     emit pairs, the only ones whose SH colour is evaluated; n_cov: in-frustum
     internal nodes, the only ones whose covariance R&L needs (both counted on the
-    device)."""
+    device); tiles: screen tiles."""
     N = tree.n
     D = tree.depth
     return {
         "filter_rl": 12.0 * N + 24.0 * n_cov + N / 8.0 + N / 8.0,
         "ancestor_compact": N / 8.0 + 4.0 * D * M + 4.0 * M,
-        "project_keys": M * (4 + 12 + 24 + 8 + 48) + E * 4 * sh_floats + 12.0 * NP,
-        "sort": NP * (8.0 + 6 * 24.0),
-        "tile_ranges": 8.0 * NP,
+        # id, centre, covariance, opacity + ln opacity in; splat and footprint out;
+        # SH rows of the emitting Gaussians; the per-tile pair counts
+        "project": M * (4 + 12 + 24 + 8 + 48 + 16) + E * 4 * sh_floats + 4.0 * tiles,
+        # counts in; ranges and cursors out
+        "tile_ranges": 16.0 * tiles,
+        # footprints in; one 8-byte item per pair out
+        "keys": 16.0 * M + 8.0 * NP,
+        # items in; keys and values out
+        "sort": 20.0 * NP,
         "blend": NP * (4.0 + 48.0) + 16.0 * width * height,
     }
 
@@ -542,7 +548,8 @@ def run_ours(args):
         M_mean, NP_mean, E_mean = timed_mean("M"), timed_mean("NP"), timed_mean("E")
         cov_mean = timed_mean("cov_nodes")
         sh_floats = (tree.sh_degree + 1) ** 2 * 3
-        ab = algorithmic_bytes(tree, M_mean, NP_mean, W, H, sh_floats, E_mean, cov_mean)
+        n_screen_tiles = ((W + 15) // 16) * ((H + 15) // 16)
+        ab = algorithmic_bytes(tree, M_mean, NP_mean, W, H, sh_floats, E_mean, cov_mean, n_screen_tiles)
         st_mean = stage_ms.mean(axis=0)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}

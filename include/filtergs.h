@@ -6,8 +6,9 @@
  * scene-adaptive Gaussian shrinking):
  *   (a) R&L filter + Ancestor filter over precomputed ancestor paths (§3.2),
  *   (b) compaction of the survivors, EWA projection and SH colour (§3.1),
- *   (c) footprint shrinking to opacity tau (§3.3, Eq. 8), Gaussian-tile key
- *       emission and a (tile | depth) LSD radix sort,
+ *   (c) footprint shrinking to opacity tau (§3.3, Eq. 8), Gaussian-tile pairs
+ *       ordered by (tile, depth, rank): per-tile pair counts, tile ranges, a
+ *       scatter of the pairs into per-tile buckets and a sort of each bucket,
  *   (d) per-tile front-to-back alpha blending (Eq. 2),
  * plus the scene calibration that derives tau from the GTC metric (Eq. 5-8).
  * Every step runs in hand-written CUDA kernels; there is no CPU fallback.
@@ -62,7 +63,8 @@ extern "C" {
                                       context-owned) so that fgs_backward need not recompute
                                       them; ignored with COUNT */
 
-#define FGS_N_STAGES 6             /* filter-R&L, ancestor+compact, project+keys, sort, ranges, blend */
+#define FGS_N_STAGES 7             /* filter R&L, ancestor filter + compaction, projection + per-tile
+                                      pair counts, tile ranges, key scatter, per-tile sort, blend */
 
 /* fgs_render_batch flags (FGS_RENDER_STATS also applies) */
 #define FGS_BATCH_GRAPH 4u         /* replay the batch as one captured CUDA graph */
@@ -207,8 +209,9 @@ int fgs_filter(fgs_ctx* ctx, void* stream, uint32_t* sel_out, uint32_t cap, uint
 int fgs_filter_levelwise(fgs_ctx* ctx, void* stream, uint32_t* sel_out, uint32_t cap,
                          uint32_t* M_out, int out_is_device, uint32_t* levels_out);
 
-/* Render one frame of the current camera: filter, project, shrink, emit keys,
- * sort, tile ranges, blend.  rgb_out: float [3][H][W] planar colour
+/* Render one frame of the current camera: filter, project, shrink, count the
+ * pairs per tile, tile ranges, scatter the pairs into per-tile buckets, sort
+ * each bucket, blend.  rgb_out: float [3][H][W] planar colour
  * C + T * bg; T_out: float [H][W] final transmittance (may be NULL).
  * out_is_device selects device (asynchronous) or host (synchronising)
  * outputs.  flags: FGS_RENDER_STATS fills st->n_selected / n_pairs /
@@ -299,8 +302,8 @@ int fgs_probe_wait_timeout(fgs_ctx* ctx, void* stream, uint32_t* site_out);
  * count_out[0] (0xFFFFFFFF if a bounded device wait timed out).  All pointers
  * are device pointers; ids_out must hold every set bit (at most 32 * n_words
  * indices).  Runs the render path's compaction kernel, but its scratch (one
- * 64-bit look-back word per 32K-index tile, 512 KiB, and an 8,448-byte state
- * block: 532,736 bytes, 520.25 KiB) is a static device array of the library,
+ * 64-bit look-back word per 32K-index tile, 512 KiB, and a 256-byte state
+ * block: 524,544 bytes) is a static device array of the library,
  * so the call allocates nothing.  Limit: n_words <= 2^26
  * (2^31 indices); larger inputs return FGS_ERR_ARG before any launch.  The
  * first call on a device looks the array's address up (cudaGetSymbolAddress);
@@ -334,9 +337,10 @@ int fgs_batch_image_offsets(const fgs_ctx* ctx, uint64_t* offsets_out);
 
 /* Render every view of the batch with one pass of the kernels over all views:
  * multi-view R&L and Ancestor filters (each node and ancestor path read once
- * for all views), one compaction, projection and key emission with global
- * tile ids, one (global tile | depth) radix sort, one blend launch over all
- * views' tiles.  Per view the result equals fgs_render with the same camera
+ * for all views), one compaction, one projection with pairs counted into
+ * global tile ids (a view's first tile + the tile), one tile scan, key scatter
+ * and per-tile sort over every view's tiles, one blend launch over all views'
+ * tiles.  Per view the result equals fgs_render with the same camera
  * and tile shape.  rgb_out / T_out are DEVICE buffers of 3 * total and total
  * pixels (see fgs_batch_image_offsets); T_out may be NULL.  flags:
  * FGS_BATCH_GRAPH replays a CUDA graph captured on first use for these output

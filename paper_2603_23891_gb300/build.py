@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfiltergs.so")
-SOURCES = ["api.cu", "filter.cu", "project.cu", "sort.cu", "blend.cu", "noalloc.cu", "levelwise.cu", "batch.cu", "backward.cu"]
+SOURCES = ["api.cu", "filter.cu", "project.cu", "pairs.cu", "blend.cu", "noalloc.cu", "levelwise.cu", "batch.cu", "backward.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -45,8 +45,7 @@ struct fgs_ctx {
     std::string err;
     fgs_params params{};
     // occupancy (resident blocks per SM)
-    int occ_pred = 1, occ_anc = 1, occ_compact = 1, occ_proj = 1, occ_emit = 1, occ_sort = 1,
-        occ_ranges = 1;
+    int occ_pred = 1, occ_anc = 1, occ_compact = 1, occ_proj = 1, occ_scatter = 1, occ_segsort = 1;
     // tree
     bool has_tree = false;
     DevTree tree{};
@@ -72,7 +71,6 @@ struct fgs_ctx {
     float* splat = nullptr;
     unsigned long long* lb_compact = nullptr;
     uint4* foot = nullptr;          // per selected Gaussian: rect, pair count, depth bits
-    uint32_t* tile_total = nullptr; // pair total per 256 selected Gaussians
     // pair-sized buffers
     uint64_t pair_cap = 0;
     unsigned long long* keys0 = nullptr;
@@ -80,10 +78,11 @@ struct fgs_ctx {
     uint32_t* vals0 = nullptr;
     uint32_t* vals1 = nullptr;
     float* kpc = nullptr;
-    unsigned long long* lb_sort = nullptr;
     // tile-sized buffers
     size_t tile_cap = 0;
     uint2* ranges = nullptr;
+    uint32_t* tile_cnt = nullptr;   // pairs per tile, then the tile's scatter cursor
+    uint32_t* large = nullptr;      // tiles whose pairs one block sorts
     float* G = nullptr;
     // image staging for host outputs: rgb planes + T
     size_t img_cap = 0;
@@ -103,7 +102,6 @@ struct fgs_ctx {
     bool have_frame = false;
     bool frame_rendered = false;    // the last frame came from fgs_render (not a calibration)
     bool frame_kept = false;        // ... with FGS_RENDER_KEEP
-    bool sorted_in_1 = false;
     // batched multi-view state
     struct Batch {
         int V = 0;
@@ -112,23 +110,22 @@ struct fgs_ctx {
         std::vector<uint32_t> tile_base;          // V + 1
         std::vector<unsigned long long> img_off;  // V + 1 (pixels)
         uint32_t total_tiles = 0;
-        int passes = 0;
         uint64_t sel_cap = 0, pair_cap = 0;
         DevCamera* d_cams = nullptr;
         DevCamera* h_cams = nullptr;              // pinned staging
         uint32_t* d_tile_base = nullptr;
         unsigned long long* d_img_off = nullptr;
-        uint32_t *pbits = nullptr, *selbits = nullptr, *sel = nullptr, *tile_total = nullptr;
+        uint32_t *pbits = nullptr, *selbits = nullptr, *sel = nullptr;
         float* splat = nullptr;
         uint4* foot = nullptr;
-        unsigned long long *keys0 = nullptr, *keys1 = nullptr, *lb_compact = nullptr, *lb_sort = nullptr;
-        uint32_t *vals0 = nullptr, *vals1 = nullptr;
+        unsigned long long *items = nullptr, *keys = nullptr, *lb_compact = nullptr;
+        uint32_t* vals = nullptr;
         uint2* ranges = nullptr;
+        uint32_t *tile_cnt = nullptr, *large = nullptr;
         FrameState* st = nullptr;
         cudaGraphExec_t graph = nullptr;
         float* graph_rgb = nullptr;
         float* graph_T = nullptr;
-        bool sorted_in_1 = false;
         bool have_frame = false;                  // a batch has been rendered since the set-up
     } batch;
 };
@@ -184,8 +181,6 @@ int ensure_pairs(fgs_ctx* c, uint64_t cap)
     if ((r = grow(c, (void**)&c->vals0, n * 4))) return r;
     if ((r = grow(c, (void**)&c->vals1, n * 4))) return r;
     if ((r = grow(c, (void**)&c->kpc, n * 4))) return r;
-    const size_t sort_tiles = (size_t)((cap + kSortTile - 1) / kSortTile);
-    if ((r = grow(c, (void**)&c->lb_sort, sort_tiles * 256 * 8))) return r;
     c->pair_cap = cap;
     c->have_frame = false;
     return FGS_OK;
@@ -201,7 +196,6 @@ int ensure_nodes(fgs_ctx* c, size_t n_pad)
     if ((r = grow(c, (void**)&c->splat, n_pad * kSplatStride * 4))) return r;
     if ((r = grow(c, (void**)&c->lb_compact, (n_pad / 32 / kCompactWords + 2) * 8))) return r;
     if ((r = grow(c, (void**)&c->foot, n_pad * sizeof(uint4)))) return r;
-    if ((r = grow(c, (void**)&c->tile_total, (n_pad / kProjThreads + 8) * 4))) return r;
     c->node_cap = n_pad;
     return FGS_OK;
 }
@@ -211,6 +205,8 @@ int ensure_tiles(fgs_ctx* c, size_t tiles, size_t pixels)
     int r;
     if (tiles > c->tile_cap) {
         if ((r = grow(c, (void**)&c->ranges, tiles * sizeof(uint2)))) return r;
+        if ((r = grow(c, (void**)&c->tile_cnt, tiles * 4))) return r;
+        if ((r = grow(c, (void**)&c->large, tiles * 4))) return r;
         if ((r = grow(c, (void**)&c->G, tiles * 4))) return r;
         c->tile_cap = tiles;
     }
@@ -255,9 +251,6 @@ DevCamera make_devcam(const fgs_ctx* c, bool force_shrink_off)
     d.tau = c->tau;
     d.ln_tau = c->ln_tau;
     std::memcpy(d.bg, c->params.bg, sizeof d.bg);
-    const int tiles = d.tiles_x * d.tiles_y;
-    const int tile_bits = ilog2(tiles);
-    d.sort_passes = 4 + (tile_bits + 7) / 8;
     d.warp_shift = c->params.blend_warp_w == 4 ? 2 : 3;
     return d;
 }
@@ -287,7 +280,6 @@ DevCamera make_devcam_for(const fgs_ctx* c, const fgs_camera& cam, int tile_w, i
     d.tau = c->tau;
     d.ln_tau = c->ln_tau;
     std::memcpy(d.bg, c->params.bg, sizeof d.bg);
-    d.sort_passes = 0;
     d.warp_shift = warp_w == 4 ? 2 : 3;
     return d;
 }
@@ -309,34 +301,31 @@ int check_ready(fgs_ctx* c)
     return FGS_OK;
 }
 
-// Enqueue the frame up to tile ranges.  Returns the number of kernel launches.
+// Enqueue the frame up to the sorted pair list and its tile ranges.  Returns
+// the number of kernel launches.  Stage events (if ev): filter R&L | ancestor
+// filter + compaction | projection + pair counts | tile ranges | key scatter |
+// per-tile sort; the caller records the blend's end.
 int enqueue_front(fgs_ctx* c, const DevCamera& dc, cudaStream_t s, cudaEvent_t* ev, bool count = false)
 {
-    int launches = 0;
-    const int tiles = dc.tiles_x * dc.tiles_y;
+    const uint32_t tiles = (uint32_t)(dc.tiles_x * dc.tiles_y);
     if (ev) cudaEventRecord(ev[0], s);
-    launch_frame_begin(c->st, c->ranges, tiles, s);
+    launch_frame_begin(c->st, c->tile_cnt, (int)tiles, s);
     launch_filter_pred(c->tree, dc, c->pbits, count ? c->st : nullptr, c->sms * c->occ_pred, s);
-    launches += 2;
     if (ev) cudaEventRecord(ev[1], s);
     launch_filter_anc(c->tree, c->pbits, c->selbits, c->sms * c->occ_anc, s);
     launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->tree.n_pad, c->lb_compact, c->st,
                    c->sms * c->occ_compact, s);
-    launches += 2;
     if (ev) cudaEventRecord(ev[2], s);
-    launch_project_emit(c->tree, dc, c->sel, c->splat, c->foot, c->tile_total, c->keys0, c->vals0,
-                        c->pair_cap, c->st, c->sms * c->occ_proj, c->sms * c->occ_emit, s);
-    launches += 2;
+    launch_project(c->tree, dc, c->sel, c->splat, c->foot, c->tile_cnt, c->st, c->sms * c->occ_proj, s);
     if (ev) cudaEventRecord(ev[3], s);
-    launches += launch_sort(c->keys0, c->vals0, c->keys1, c->vals1, c->pair_cap, dc.sort_passes,
-                            c->lb_sort, c->st, c->sms * c->occ_sort, s);
-    c->sorted_in_1 = (dc.sort_passes & 1) != 0;
+    launch_tile_scan(c->tile_cnt, c->ranges, tiles, c->large, c->pair_cap, c->st, s);
     if (ev) cudaEventRecord(ev[4], s);
-    launch_tile_ranges(c->sorted_in_1 ? c->keys1 : c->keys0, c->pair_cap, c->ranges, c->st,
-                       c->sms * c->occ_ranges, s);
-    ++launches;
+    launch_scatter(dc, c->foot, c->tile_cnt, c->keys0, c->pair_cap, c->st, c->sms * c->occ_scatter, s);
     if (ev) cudaEventRecord(ev[5], s);
-    return launches;
+    launch_segsort(c->ranges, tiles, c->large, c->keys0, c->keys1, c->vals1, c->st,
+                   c->sms * c->occ_segsort, s);
+    if (ev) cudaEventRecord(ev[6], s);
+    return 8;
 }
 
 int read_state(fgs_ctx* c, cudaStream_t s)
@@ -392,9 +381,8 @@ int fgs_create(fgs_ctx** out, int device)
     c->occ_anc = occ_filter_anc();
     c->occ_compact = occ_compact();
     c->occ_proj = occ_project();
-    c->occ_emit = occ_emit();
-    c->occ_sort = occ_sort_pass();
-    c->occ_ranges = occ_tile_ranges();
+    c->occ_scatter = occ_scatter();
+    c->occ_segsort = occ_segsort();
     c->params.tau_R = 3.0f;
     c->params.tile_w = 16;
     c->params.tile_h = 16;
@@ -422,15 +410,14 @@ int fgs_destroy(fgs_ctx* c)
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
     void* bufs[] = {c->child_start, c->children, c->frontier0, c->frontier1, c->d_counter,
-                    c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->foot, c->tile_total,
-                    c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->lb_sort, c->ranges,
+                    c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->foot,
+                    c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->ranges, c->tile_cnt, c->large,
                     c->G, c->img, c->keep, c->st, c->gsplat};
     for (void* p : bufs) free_ptr(p);
     {
         auto& b = c->batch;
-        void* bb[] = {b.d_cams, b.d_tile_base, b.d_img_off, b.pbits, b.selbits, b.sel, b.tile_total,
-                      b.splat, b.foot, b.keys0, b.keys1, b.lb_compact, b.lb_sort, b.vals0, b.vals1,
-                      b.ranges, b.st};
+        void* bb[] = {b.d_cams, b.d_tile_base, b.d_img_off, b.pbits, b.selbits, b.sel, b.splat,
+                      b.foot, b.items, b.keys, b.vals, b.lb_compact, b.ranges, b.tile_cnt, b.large, b.st};
         for (void* p : bb) free_ptr(p);
         if (b.h_cams) cudaFreeHost(b.h_cams);
         if (b.graph) cudaGraphExecDestroy(b.graph);
@@ -710,7 +697,7 @@ int fgs_filter(fgs_ctx* c, void* stream, uint32_t* sel_out, uint32_t cap, uint32
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const DevCamera dc = make_devcam(c, false);
-    launch_frame_begin(c->st, c->ranges, dc.tiles_x * dc.tiles_y, s);
+    launch_frame_begin(c->st, c->tile_cnt, dc.tiles_x * dc.tiles_y, s);
     launch_filter_pred(c->tree, dc, c->pbits, nullptr, c->sms * c->occ_pred, s);
     launch_filter_anc(c->tree, c->pbits, c->selbits, c->sms * c->occ_anc, s);
     launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->tree.n_pad, c->lb_compact, c->st,
@@ -745,7 +732,7 @@ int fgs_filter_levelwise(fgs_ctx* c, void* stream, uint32_t* sel_out, uint32_t c
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const DevCamera dc = make_devcam(c, false);
-    launch_frame_begin(c->st, c->ranges, dc.tiles_x * dc.tiles_y, s);
+    launch_frame_begin(c->st, c->tile_cnt, dc.tiles_x * dc.tiles_y, s);
     FGS_CUDA(c, cudaMemsetAsync(c->selbits, 0, c->tree.n_pad / 32 * 4, s));
     c->h_counter[0] = c->root;
     FGS_CUDA(c, cudaMemcpyAsync(c->frontier0, c->h_counter, 4, cudaMemcpyHostToDevice, s));
@@ -812,10 +799,9 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
     float* T_dst = out_is_device ? T_out : (T_out ? c->img + 3 * hw : nullptr);
     const bool keep = (flags & FGS_RENDER_KEEP) && !count;
     if (count) flags |= FGS_RENDER_STATS;
-    launch_blend(dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, rgb_dst, T_dst,
-                 keep ? c->keep : nullptr, c->st, count, s);
+    launch_blend(dc, c->ranges, c->vals1, c->splat, rgb_dst, T_dst, keep ? c->keep : nullptr, c->st, count, s);
     ++launches;
-    if (ev) cudaEventRecord(ev[6], s);
+    if (ev) cudaEventRecord(ev[kStages], s);
     FGS_CUDA(c, cudaGetLastError());
     c->have_frame = true;
     c->frame_rendered = true;
@@ -881,8 +867,8 @@ int fgs_get_pairs(fgs_ctx* c, void* stream, uint64_t* keys_out, uint32_t* vals_o
     const uint64_t np = c->st_host->n_pairs;
     *n_out = np;
     const uint64_t n = std::min<uint64_t>(std::min<uint64_t>(np, c->pair_cap), cap);
-    const unsigned long long* k = c->sorted_in_1 ? c->keys1 : c->keys0;
-    const uint32_t* v = c->sorted_in_1 ? c->vals1 : c->vals0;
+    const unsigned long long* k = c->keys1;
+    const uint32_t* v = c->vals1;
     const cudaMemcpyKind kind = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (n && keys_out) FGS_CUDA(c, cudaMemcpyAsync(keys_out, k, n * 8, kind, s));
     if (n && vals_out) FGS_CUDA(c, cudaMemcpyAsync(vals_out, v, n * 4, kind, s));
@@ -928,8 +914,7 @@ int kpc_view(fgs_ctx* c, void* stream, bool force_3sigma, double* gbar_out, floa
     const DevCamera dc = make_devcam(c, force_3sigma);
     enqueue_front(c, dc, s, nullptr);
     FGS_CUDA(c, cudaMemsetAsync(c->kpc, 0, c->pair_cap * 4, s));
-    launch_blend_kpc(dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat, c->kpc, c->G,
-                     c->st, s);
+    launch_blend_kpc(dc, c->ranges, c->vals1, c->splat, c->kpc, c->G, c->st, s);
     FGS_CUDA(c, cudaGetLastError());
     c->have_frame = true;
     c->frame_rendered = false;
@@ -1091,7 +1076,7 @@ int fgs_backward(fgs_ctx* c, void* stream, const float* dL_drgb, const fgs_gauss
     cudaStream_t s = (cudaStream_t)stream;
     const float* params[5] = {p->mu, p->log_scale, p->quat, p->logit, p->sh};
     float* grads[5] = {gr->mu, gr->log_scale, gr->quat, gr->logit, gr->sh};
-    launch_backward(c->tree, dc, c->ranges, c->sorted_in_1 ? c->vals1 : c->vals0, c->splat,
+    launch_backward(c->tree, dc, c->ranges, c->vals1, c->splat,
                     c->frame_kept ? c->keep : nullptr, c->sel,
                     dL_drgb, c->gsplat, params, grads, (flags & FGS_BACKWARD_ACCUMULATE) != 0, c->sms, c->st,
                     s);
@@ -1144,8 +1129,6 @@ int fgs_batch_setup(fgs_ctx* c, const fgs_camera* views, int n_views, const int3
         b.img_off[v + 1] = b.img_off[v] + (unsigned long long)views[v].width * views[v].height;
     }
     b.total_tiles = b.tile_base[n_views];
-    b.passes = 4 + (ilog2((int)b.total_tiles) + 7) / 8;
-    if (b.passes > kMaxSortPasses) return fail(c, FGS_ERR_ARG, "too many tiles in the batch");
     const uint64_t sel_cap = sel_capacity ? sel_capacity : std::min<uint64_t>((uint64_t)n_views * c->tree.n_pad, 64ull << 20);
     const uint64_t pair_cap = pair_capacity ? pair_capacity : (128ull << 20);
     if (pair_cap > kMaxPairCap) return fail(c, FGS_ERR_ARG, "pair capacity too large");
@@ -1162,19 +1145,18 @@ int fgs_batch_setup(fgs_ctx* c, const fgs_camera* views, int n_views, const int3
         if ((r = grow(c, (void**)&b.sel, 4 * sel_cap))) return r;
         if ((r = grow(c, (void**)&b.splat, 4 * kSplatStride * sel_cap))) return r;
         if ((r = grow(c, (void**)&b.foot, sizeof(uint4) * sel_cap))) return r;
-        if ((r = grow(c, (void**)&b.tile_total, 4 * (sel_cap / kProjThreads + 8)))) return r;
         b.sel_cap = sel_cap;
     }
     if (pair_cap != b.pair_cap) {
         const size_t n = pair_cap + 8;
-        if ((r = grow(c, (void**)&b.keys0, 8 * n))) return r;
-        if ((r = grow(c, (void**)&b.keys1, 8 * n))) return r;
-        if ((r = grow(c, (void**)&b.vals0, 4 * n))) return r;
-        if ((r = grow(c, (void**)&b.vals1, 4 * n))) return r;
-        if ((r = grow(c, (void**)&b.lb_sort, 8 * 256 * (pair_cap / kSortTile + 2)))) return r;
+        if ((r = grow(c, (void**)&b.items, 8 * n))) return r;
+        if ((r = grow(c, (void**)&b.keys, 8 * n))) return r;
+        if ((r = grow(c, (void**)&b.vals, 4 * n))) return r;
         b.pair_cap = pair_cap;
     }
     if ((r = grow(c, (void**)&b.ranges, sizeof(uint2) * b.total_tiles))) return r;
+    if ((r = grow(c, (void**)&b.tile_cnt, 4 * b.total_tiles))) return r;
+    if ((r = grow(c, (void**)&b.large, 4 * b.total_tiles))) return r;
     if (!b.st) {
         if ((r = grow(c, (void**)&b.st, sizeof(FrameState)))) return r;
     }
@@ -1212,12 +1194,11 @@ namespace {
 void enqueue_batch(fgs_ctx* c, float* rgb, float* T, cudaStream_t s)
 {
     auto& b = c->batch;
-    launch_batch_front(c->tree, b.d_cams, b.V, b.total_tiles, b.d_tile_base, b.passes, b.pbits,
-                       b.selbits, b.sel, (uint32_t)b.sel_cap, b.splat, b.foot, b.tile_total, b.keys0, b.vals0, b.keys1,
-                       b.vals1, b.pair_cap, b.lb_compact, b.lb_sort, b.ranges, b.st, c->sms, s);
-    b.sorted_in_1 = (b.passes & 1) != 0;
-    launch_batch_blend(b.d_cams, b.V, b.total_tiles, b.d_tile_base, b.d_img_off, b.ranges,
-                       b.sorted_in_1 ? b.vals1 : b.vals0, b.splat, rgb, T, b.st, s);
+    launch_batch_front(c->tree, b.d_cams, b.V, b.total_tiles, b.d_tile_base, b.pbits, b.selbits, b.sel,
+                       (uint32_t)b.sel_cap, b.splat, b.foot, b.tile_cnt, b.large, b.items, b.keys, b.vals,
+                       b.pair_cap, b.lb_compact, b.ranges, b.st, c->sms, s);
+    launch_batch_blend(b.d_cams, b.V, b.total_tiles, b.d_tile_base, b.d_img_off, b.ranges, b.vals, b.splat,
+                       rgb, T, b.st, s);
 }
 
 }  // namespace
@@ -1233,11 +1214,10 @@ int fgs_render_batch(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, uin
     cudaStream_t s = (cudaStream_t)stream;
     for (int v = 0; v < b.V; ++v) {
         DevCamera d = make_devcam_for(c, b.cams[v], b.tile_w[v], b.tile_h[v], b.warp_w[v]);
-        d.sort_passes = b.passes;
         b.h_cams[v] = d;
     }
     FGS_CUDA(c, cudaMemcpyAsync(b.d_cams, b.h_cams, sizeof(DevCamera) * b.V, cudaMemcpyHostToDevice, s));
-    const int launches = 8 + b.passes;
+    const int launches = 9;
     if (flags & FGS_BATCH_GRAPH) {
         if (!b.graph || b.graph_rgb != rgb_out || b.graph_T != T_out) {
             if (b.graph) {
@@ -1316,9 +1296,9 @@ int fgs_batch_get_frame(fgs_ctx* c, void* stream, uint32_t* entries_out, float* 
     if (m && splat_out)
         FGS_CUDA(c, cudaMemcpyAsync(splat_out, b.splat, m * kSplatStride * 4, cudaMemcpyDeviceToHost, s));
     if (n && keys_out)
-        FGS_CUDA(c, cudaMemcpyAsync(keys_out, b.sorted_in_1 ? b.keys1 : b.keys0, n * 8, cudaMemcpyDeviceToHost, s));
+        FGS_CUDA(c, cudaMemcpyAsync(keys_out, b.keys, n * 8, cudaMemcpyDeviceToHost, s));
     if (n && vals_out)
-        FGS_CUDA(c, cudaMemcpyAsync(vals_out, b.sorted_in_1 ? b.vals1 : b.vals0, n * 4, cudaMemcpyDeviceToHost, s));
+        FGS_CUDA(c, cudaMemcpyAsync(vals_out, b.vals, n * 4, cudaMemcpyDeviceToHost, s));
     FGS_CUDA(c, cudaStreamSynchronize(s));
     if (c->st_host->status)
         return fail(c, c->st_host->status == kErrCapacity ? FGS_ERR_CAPACITY : FGS_ERR_TIMEOUT,

@@ -9,21 +9,23 @@
 //  * compaction      the per-view selection bits are one concatenated bit array
 //                    [V][words]; the render path's compaction kernel turns it into
 //                    global entries v * n_pad + node (ascending: view, then node);
-//  * bproject / bemit projection, shrink and key emission with a global tile id
-//                    (the view's first tile + the tile), so one stable radix sort
-//                    of (global tile | depth) keys orders every view at once;
-//  * tile ranges, then bblend over all views' tiles; a CTA finds its view by
-//    binary search over the views' first tiles and blends with that camera.
+//  * bproject        projection and shrink of every entry with its view's camera;
+//                    pairs are counted into global tile ids (the view's first
+//                    tile + the tile), so the render path's tile scan, key
+//                    scatter and per-tile sort order every view at once;
+//  * bblend over all views' tiles; a CTA finds its view by binary search over
+//    the views' first tiles and blends with that camera.
 // Per view, selection, pairs, their order and every pixel are those of the
 // single-view path with the same camera and tile shape.
 #include "blend_impl.cuh"
+#include "pairs_impl.cuh"
 #include "project_impl.cuh"
 
 namespace fgs {
 
 constexpr int kMaxBatchViews = 64;
 
-__global__ void bframe_begin_kernel(FrameState* st, uint2* ranges, uint32_t n_tiles)
+__global__ void bframe_begin_kernel(FrameState* st, uint32_t* tile_cnt, uint32_t n_tiles)
 {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid == 0) {
@@ -32,8 +34,7 @@ __global__ void bframe_begin_kernel(FrameState* st, uint2* ranges, uint32_t n_ti
         st->n_pairs = 0;
     }
     if (tid < 16) st->tickets[tid] = 0;
-    for (uint32_t i = tid; i < kMaxSortPasses * 256; i += gridDim.x * blockDim.x) (&st->hist[0][0])[i] = 0;
-    for (uint32_t i = tid; i < n_tiles; i += gridDim.x * blockDim.x) ranges[i] = make_uint2(0, 0);
+    for (uint32_t i = tid; i < n_tiles; i += gridDim.x * blockDim.x) tile_cnt[i] = 0;
 }
 
 // R&L for V views: 4 consecutive nodes per thread, cameras in shared memory.
@@ -145,143 +146,33 @@ __global__ void __launch_bounds__(256) banc_kernel(DevTree t, int V, const uint3
     }
 }
 
-// Projection of every selected entry g (entry = view * n_pad + node).
+// Projection of every selected entry (entry = view * n_pad + node), with the
+// pairs counted into global tile ids.
 __global__ void __launch_bounds__(kProjThreads) bproject_kernel(
-    DevTree t, const DevCamera* __restrict__ cams, int V, const uint32_t* __restrict__ sel,
-    float* __restrict__ splat, uint4* __restrict__ foot, uint32_t* __restrict__ tile_total,
-    FrameState* st)
+    DevTree t, const DevCamera* __restrict__ cams, int V, const uint32_t* __restrict__ tile_base,
+    const uint32_t* __restrict__ sel, float* __restrict__ splat, uint4* __restrict__ foot,
+    uint32_t* __restrict__ tile_cnt, FrameState* st)
 {
     __shared__ DevCamera s_cam[kMaxBatchViews];
-    __shared__ uint32_t s_warp_tot[kProjThreads / 32];
+    __shared__ uint32_t s_base[kMaxBatchViews];
     for (int i = threadIdx.x; i < V * (int)(sizeof(DevCamera) / 4); i += blockDim.x)
         reinterpret_cast<uint32_t*>(s_cam)[i] = reinterpret_cast<const uint32_t*>(cams)[i];
+    for (int i = threadIdx.x; i < V; i += blockDim.x) s_base[i] = tile_base[i];
     __syncthreads();
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t M = st->M;
-    const uint32_t n_tiles = (M + kProjThreads - 1) / kProjThreads;
-    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const uint32_t m = tile * kProjThreads + tid;
-        uint32_t cnt = 0;
+    const uint32_t n_groups = (M + kProjThreads - 1) / kProjThreads;
+    for (uint32_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        const uint32_t m = g * kProjThreads + threadIdx.x;
+        uint4 f = make_uint4(0, 0, 0, 0);
+        uint32_t tiles_x = 1, tbase = 0;
         if (m < M) {
             const uint32_t e = __ldg(sel + m);
             const uint32_t v = e / t.n_pad;
-            cnt = proj::project_one(t, s_cam[v], e - v * t.n_pad, m, splat, foot);
+            f = proj::project_one(t, s_cam[v], e - v * t.n_pad, m, splat, foot);
+            tiles_x = (uint32_t)s_cam[v].tiles_x;
+            tbase = s_base[v];
         }
-        const uint32_t wsum = warp_sum_u32(cnt);
-        if (lane == 0) s_warp_tot[warp] = wsum;
-        __syncthreads();
-        if (tid == 0) {
-            uint32_t tot = 0;
-#pragma unroll
-            for (int w = 0; w < kProjThreads / 32; ++w) tot += s_warp_tot[w];
-            tile_total[tile] = tot;
-        }
-        __syncthreads();
-    }
-}
-
-// Key emission with global tile ids (same slots and order rules as emit_kernel).
-__global__ void __launch_bounds__(kProjThreads) bemit_kernel(
-    const DevCamera* __restrict__ cams, const uint32_t* __restrict__ tile_base, uint32_t n_pad,
-    int passes, const uint32_t* __restrict__ sel, const uint4* __restrict__ foot,
-    const uint32_t* __restrict__ tile_total, unsigned long long* __restrict__ keys,
-    uint32_t* __restrict__ vals, unsigned long long cap, FrameState* st)
-{
-    __shared__ uint32_t s_warp_tot[kProjThreads / 32];
-    __shared__ unsigned long long s_red[kProjThreads / 32];
-    __shared__ uint32_t s_hist[kMaxSortPasses][256];
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < kMaxSortPasses * 256; i += kProjThreads) (&s_hist[0][0])[i] = 0;
-    const uint32_t M = st->M;
-    const uint32_t n_tiles = (M + kProjThreads - 1) / kProjThreads;
-    const uint32_t n_groups = (n_tiles + kEmitTiles - 1) / kEmitTiles;
-    bool any = false;
-    for (uint32_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
-        any = true;
-        const uint32_t t0 = g * kEmitTiles;
-        unsigned long long part = 0;
-        for (uint32_t i = tid; i < t0; i += kProjThreads) part += __ldg(tile_total + i);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) s_red[warp] = part;
-        __syncthreads();
-        unsigned long long prefix = 0;
-#pragma unroll
-        for (int w = 0; w < kProjThreads / 32; ++w) prefix += s_red[w];
-        for (uint32_t tile = t0; tile < t0 + kEmitTiles && tile < n_tiles; ++tile) {
-            const uint32_t m = tile * kProjThreads + tid;
-            uint4 f = make_uint4(0, 0, 0, 0);
-            uint32_t tiles_x = 1, tbase = 0;
-            if (m < M) {
-                f = __ldg(foot + m);
-                const uint32_t v = __ldg(sel + m) / n_pad;
-                tiles_x = (uint32_t)cams[v].tiles_x;
-                tbase = __ldg(tile_base + v);
-            }
-            const uint32_t cnt = f.z;
-            uint32_t incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t up = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= (uint32_t)o) incl += up;
-            }
-            if (lane == 31) s_warp_tot[warp] = incl;
-            __syncthreads();
-            uint32_t off = 0, total = 0;
-#pragma unroll
-            for (int w = 0; w < kProjThreads / 32; ++w) {
-                const uint32_t tw = s_warp_tot[w];
-                off += (w < (int)warp) ? tw : 0u;
-                total += tw;
-            }
-            const unsigned long long wfirst = prefix + off;
-            const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
-            const uint32_t excl = incl - cnt;
-            const int32_t x0 = (int32_t)(f.x & 0xFFFFu), x1 = (int32_t)(f.x >> 16);
-            const int32_t y0 = (int32_t)(f.y & 0xFFFFu);
-            const int32_t rw = x1 - x0;
-            if (lane == 0 && wtot && wfirst + wtot > cap) set_status(st, kErrCapacity, 0x310u);
-            for (uint32_t q0 = 0; q0 < wtot; q0 += 32) {
-                const uint32_t q = q0 + lane;
-                uint32_t lo = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const uint32_t probe = __shfl_sync(0xffffffffu, incl, lo + step - 1);
-                    if (probe <= q) lo += step;
-                }
-                const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, lo);
-                const int32_t o_x0 = __shfl_sync(0xffffffffu, x0, lo);
-                const int32_t o_rw = __shfl_sync(0xffffffffu, rw, lo);
-                const int32_t o_y0 = __shfl_sync(0xffffffffu, y0, lo);
-                const uint32_t o_d = __shfl_sync(0xffffffffu, f.w, lo);
-                const uint32_t o_m = __shfl_sync(0xffffffffu, m, lo);
-                const uint32_t o_tx = __shfl_sync(0xffffffffu, tiles_x, lo);
-                const uint32_t o_tb = __shfl_sync(0xffffffffu, tbase, lo);
-                if (q < wtot) {
-                    const unsigned long long idx = wfirst + q;
-                    if (idx < cap) {
-                        const int32_t k = (int32_t)(q - o_excl);
-                        const uint32_t ty = (uint32_t)(o_y0 + k / o_rw);
-                        const uint32_t tx = (uint32_t)(o_x0 + k % o_rw);
-                        const unsigned long long tl = (unsigned long long)(o_tb + ty * o_tx + tx);
-                        const unsigned long long key = (tl << 32) | o_d;
-                        keys[idx] = key;
-                        vals[idx] = o_m;
-                        for (int p = 0; p < passes; ++p)
-                            atomicAdd(&s_hist[p][(uint32_t)(key >> (8 * p)) & 0xFFu], 1u);
-                    }
-                }
-            }
-            prefix += total;
-            if (tile == n_tiles - 1 && tid == 0) st->n_pairs = prefix;
-            __syncthreads();
-        }
-    }
-    if (!any) return;
-    __syncthreads();
-    for (int i = tid; i < passes * 256; i += kProjThreads) {
-        const uint32_t c = (&s_hist[0][0])[i];
-        if (c) atomicAdd(&st->hist[0][0] + i, c);
+        warp_count_pairs(f.z, f.x, f.y, tiles_x, tbase, tile_cnt);
     }
 }
 
@@ -317,16 +208,15 @@ __global__ void __launch_bounds__(256) bblend_kernel(const DevCamera* __restrict
 // launchers
 // ---------------------------------------------------------------------------
 void launch_batch_front(const DevTree& t, const DevCamera* cams, int V, uint32_t total_tiles,
-                        const uint32_t* tile_base, int passes, uint32_t* pbits, uint32_t* selbits,
-                        uint32_t* sel, uint32_t sel_cap, float* splat, uint4* foot, uint32_t* tile_total,
-                        unsigned long long* keys0, uint32_t* vals0, unsigned long long* keys1,
-                        uint32_t* vals1, unsigned long long cap, unsigned long long* lb_compact,
-                        unsigned long long* lb_sort, uint2* ranges, FrameState* st, int sms,
-                        cudaStream_t s)
+                        const uint32_t* tile_base, uint32_t* pbits, uint32_t* selbits, uint32_t* sel,
+                        uint32_t sel_cap, float* splat, uint4* foot, uint32_t* tile_cnt, uint32_t* large,
+                        unsigned long long* items, unsigned long long* keys, uint32_t* vals,
+                        unsigned long long cap, unsigned long long* lb_compact, uint2* ranges,
+                        FrameState* st, int sms, cudaStream_t s)
 {
     const uint32_t n_words = t.n_pad >> 5;
     int b0 = (int)((total_tiles + 255) / 256);
-    bframe_begin_kernel<<<b0 < 8 ? 8 : b0, 256, 0, s>>>(st, ranges, total_tiles);
+    bframe_begin_kernel<<<b0 < 8 ? 8 : b0, 256, 0, s>>>(st, tile_cnt, total_tiles);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bpred_kernel, 256, 0);
     bpred_kernel<<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(t, cams, V, pbits);
@@ -335,15 +225,11 @@ void launch_batch_front(const DevTree& t, const DevCamera* cams, int V, uint32_t
     launch_compact(selbits, (uint32_t)((size_t)n_words * V), sel, sel_cap, lb_compact, st,
                    sms * occ_compact(), s);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bproject_kernel, kProjThreads, 0);
-    bproject_kernel<<<sms * (occ > 0 ? occ : 1), kProjThreads, 0, s>>>(t, cams, V, sel, splat, foot,
-                                                                       tile_total, st);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bemit_kernel, kProjThreads, 0);
-    bemit_kernel<<<sms * (occ > 0 ? occ : 1), kProjThreads, 0, s>>>(cams, tile_base, t.n_pad, passes,
-                                                                    sel, foot, tile_total, keys0, vals0,
-                                                                    cap, st);
-    launch_sort(keys0, vals0, keys1, vals1, cap, passes, lb_sort, st, sms * occ_sort_pass(), s);
-    const bool odd = (passes & 1) != 0;
-    launch_tile_ranges(odd ? keys1 : keys0, cap, ranges, st, sms * occ_tile_ranges(), s);
+    bproject_kernel<<<sms * (occ > 0 ? occ : 1), kProjThreads, 0, s>>>(t, cams, V, tile_base, sel, splat,
+                                                                       foot, tile_cnt, st);
+    launch_tile_scan(tile_cnt, ranges, total_tiles, large, cap, st, s);
+    launch_scatter_batch(cams, tile_base, t.n_pad, sel, foot, tile_cnt, items, cap, st, sms * occ_scatter(), s);
+    launch_segsort(ranges, total_tiles, large, items, keys, vals, st, sms * occ_segsort(), s);
 }
 
 void launch_batch_blend(const DevCamera* cams, int V, uint32_t total_tiles, const uint32_t* tile_base,

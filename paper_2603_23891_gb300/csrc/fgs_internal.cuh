@@ -15,19 +15,15 @@
 
 namespace fgs {
 
-constexpr int kStages = 6;
+constexpr int kStages = 7;
 constexpr uint32_t kApPad = 0xFFFFFFFFu;
 constexpr int kSplatStride = 12;          // floats per splat record (48 B)
-constexpr int kSortTileItems = 16;        // keys per thread in a sort tile
-constexpr int kSortThreads = 256;
-constexpr int kSortTile = kSortTileItems * kSortThreads;   // 4096 keys
-constexpr int kMaxSortPasses = 8;         // 64-bit keys: 32 depth bits + up to 32 (global) tile bits
-constexpr int kLookbackRows = 8;          // predecessor tiles read per look-back round trip
+constexpr int kSegSmall = 256;            // pairs of a tile sorted by one warp in registers
+constexpr int kSegSmem = 2048;            // pairs of a tile sorted by one block in shared memory
 constexpr int kFilterTile = 4096;         // node arrays are padded to a multiple of this
 constexpr int kCompactWords = 1024;       // 32-bit selection words per compaction tile (32K nodes)
 constexpr int kAncCacheWords = 4096;      // P-bit words of the lowest node ids kept in shared memory
 constexpr int kProjThreads = 256;         // selected Gaussians per projection tile
-constexpr int kEmitTiles = 4;             // projection tiles per emission block
 constexpr uint64_t kSpinLimit = 1ull << 24;   // bounded spin-waits
 
 // device status codes (mirrors FGS_ERR_* of the C ABI)
@@ -49,7 +45,6 @@ struct DevCamera {
     int32_t shrink;
     float tau, ln_tau;
     float bg[3];
-    int32_t sort_passes;
     int32_t warp_shift;        // blend warps cover (1 << warp_shift) x (32 >> warp_shift) pixels
 };
 
@@ -80,7 +75,7 @@ struct FrameState {
     uint32_t tickets[16];      // dynamic tile counters (one per kernel use)
     int32_t status;            // latched error (0 = ok)
     uint32_t status_info;
-    uint32_t hist[kMaxSortPasses][256];   // radix digit histograms
+    uint32_t n_large;                     // tiles whose pairs one block sorts (> kSegSmall)
     unsigned long long blend_entries;     // lockstep warp steps of the list walk (counting frames only)
     unsigned long long blend_evals;       // pixel-Gaussian evaluations (lanes not yet stopped)
     unsigned long long blend_hits;        // evaluations that reached the alpha / T update
@@ -92,7 +87,7 @@ struct FrameState {
 };
 
 // Ticket slots
-enum : int { kTicketCompact = 0, kTicketSortBase = 2 };
+enum : int { kTicketCompact = 0, kTicketSegSort = 2 };
 
 // ---------------------------------------------------------------------
 // decision-exact binary32 helpers
@@ -328,14 +323,12 @@ int occ_filter_pred();
 int occ_filter_anc();
 int occ_compact();
 int occ_project();
-int occ_emit();
-int occ_sort_pass();
-int occ_tile_ranges();
-size_t sort_smem_bytes();
+int occ_scatter();
+int occ_segsort();
 
 // All launchers enqueue on `s` and read counts (M, N_P) from device memory,
 // so a frame needs no host synchronisation.
-void launch_frame_begin(FrameState* st, uint2* ranges, int n_tiles, cudaStream_t s);
+void launch_frame_begin(FrameState* st, uint32_t* tile_cnt, int n_tiles, cudaStream_t s);
 void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits, FrameState* count_st, int blocks,
                         cudaStream_t s);
 void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, int blocks,
@@ -349,18 +342,26 @@ constexpr uint32_t kProbeSite = 0x7F0u;
 void launch_wait_probe(const unsigned long long* lb, FrameState* st, cudaStream_t s);
 void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel, uint32_t cap,
                     unsigned long long* lookback, FrameState* st, int blocks, cudaStream_t s);
-void launch_project_emit(const DevTree& t, const DevCamera& cam, const uint32_t* sel,
-                         float* splat, uint4* foot, uint32_t* tile_total,
-                         unsigned long long* keys, uint32_t* vals, unsigned long long cap,
-                         FrameState* st, int proj_blocks, int emit_blocks, cudaStream_t s);
-// Sorts keys0/vals0 in place through keys1/vals1 (an even number of passes
-// leaves the result in keys0/vals0; an odd number in keys1/vals1).
-// The digit histograms of all passes are accumulated during key emission.
-int launch_sort(unsigned long long* keys0, uint32_t* vals0, unsigned long long* keys1,
-                uint32_t* vals1, unsigned long long cap, int passes,
-                unsigned long long* lookback, FrameState* st, int sort_blocks, cudaStream_t s);
-void launch_tile_ranges(const unsigned long long* keys, unsigned long long cap, uint2* ranges,
-                        const FrameState* st, int blocks, cudaStream_t s);
+// Projection (splat records, footprints) and the per-tile pair counts
+// tile_cnt[tiles] (zeroed by launch_frame_begin).
+void launch_project(const DevTree& t, const DevCamera& cam, const uint32_t* sel, float* splat,
+                    uint4* foot, uint32_t* tile_cnt, FrameState* st, int blocks, cudaStream_t s);
+// Tile ranges (clamped to cap), scatter cursors (in tile_cnt), N_P and the list
+// of tiles with more than kSegSmall pairs (large[], FrameState::n_large).
+void launch_tile_scan(uint32_t* tile_cnt, uint2* ranges, uint32_t n_tiles, uint32_t* large,
+                      unsigned long long cap, FrameState* st, cudaStream_t s);
+// Every pair into its tile's bucket of items[] (depth bits << 32 | rank).
+void launch_scatter(const DevCamera& cam, const uint4* foot, uint32_t* cursor, unsigned long long* items,
+                    unsigned long long cap, FrameState* st, int blocks, cudaStream_t s);
+void launch_scatter_batch(const DevCamera* cams, const uint32_t* tile_base, uint32_t n_pad,
+                          const uint32_t* sel, const uint4* foot, uint32_t* cursor,
+                          unsigned long long* items, unsigned long long cap, FrameState* st, int blocks,
+                          cudaStream_t s);
+// Sorts every tile's bucket of items[] into keys_out (tile << 32 | depth bits)
+// and vals_out (rank), in place of the bucket's slots.
+void launch_segsort(const uint2* ranges, uint32_t n_tiles, const uint32_t* large, unsigned long long* items,
+                    unsigned long long* keys_out, uint32_t* vals_out, FrameState* st, int blocks,
+                    cudaStream_t s);
 // count: use the counting variant (fills FrameState::blend_* work counters)
 void launch_blend(const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
                   const float* splat, float* rgb, float* T, uint2* keep, FrameState* st, bool count,
@@ -370,12 +371,11 @@ void launch_blend_kpc(const DevCamera& cam, const uint2* ranges, const uint32_t*
 
 void launch_eval_exp(const float* x, float* y, uint64_t n, cudaStream_t s);
 void launch_batch_front(const DevTree& t, const DevCamera* cams, int V, uint32_t total_tiles,
-                        const uint32_t* tile_base, int passes, uint32_t* pbits, uint32_t* selbits,
-                        uint32_t* sel, uint32_t sel_cap, float* splat, uint4* foot, uint32_t* tile_total,
-                        unsigned long long* keys0, uint32_t* vals0, unsigned long long* keys1,
-                        uint32_t* vals1, unsigned long long cap, unsigned long long* lb_compact,
-                        unsigned long long* lb_sort, uint2* ranges, FrameState* st, int sms,
-                        cudaStream_t s);
+                        const uint32_t* tile_base, uint32_t* pbits, uint32_t* selbits, uint32_t* sel,
+                        uint32_t sel_cap, float* splat, uint4* foot, uint32_t* tile_cnt, uint32_t* large,
+                        unsigned long long* items, unsigned long long* keys, uint32_t* vals,
+                        unsigned long long cap, unsigned long long* lb_compact, uint2* ranges,
+                        FrameState* st, int sms, cudaStream_t s);
 void launch_batch_blend(const DevCamera* cams, int V, uint32_t total_tiles, const uint32_t* tile_base,
                         const unsigned long long* img_off, const uint2* ranges, const uint32_t* vals,
                         const float* splat, float* rgb, float* T, FrameState* st, cudaStream_t s);

@@ -14,7 +14,7 @@
 
 namespace fgs {
 
-__global__ void frame_begin_kernel(FrameState* st, uint2* ranges, int n_tiles)
+__global__ void frame_begin_kernel(FrameState* st, uint32_t* tile_cnt, int n_tiles)
 {
     grid_dep_wait();
     grid_dep_trigger();
@@ -32,16 +32,14 @@ __global__ void frame_begin_kernel(FrameState* st, uint2* ranges, int n_tiles)
         st->filter_cov_nodes = 0;
     }
     if (tid < 16) st->tickets[tid] = 0;
-    for (int i = tid; i < kMaxSortPasses * 256; i += gridDim.x * blockDim.x)
-        (&st->hist[0][0])[i] = 0;
-    for (int i = tid; i < n_tiles; i += gridDim.x * blockDim.x) ranges[i] = make_uint2(0, 0);
+    for (int i = tid; i < n_tiles; i += gridDim.x * blockDim.x) tile_cnt[i] = 0;
 }
 
-void launch_frame_begin(FrameState* st, uint2* ranges, int n_tiles, cudaStream_t s)
+void launch_frame_begin(FrameState* st, uint32_t* tile_cnt, int n_tiles, cudaStream_t s)
 {
     int blocks = (n_tiles + 255) / 256;
     blocks = blocks < 8 ? 8 : blocks;
-    launch_pdl(frame_begin_kernel, blocks, 256, 0, s, st, ranges, n_tiles);
+    launch_pdl(frame_begin_kernel, blocks, 256, 0, s, st, tile_cnt, n_tiles);
 }
 
 // ---------------------------------------------------------------------------

@@ -27,9 +27,9 @@ constexpr uint64_t kNoAllocMaxWords = 1ull << 26;                 // 2^31 nodes
 constexpr uint64_t kNoAllocTiles = kNoAllocMaxWords / kCompactWords;  // 65536 look-back words
 constexpr size_t kStateBytes = (sizeof(FrameState) + 255) / 256 * 256;
 constexpr size_t kNoAllocScratchBytes = kStateBytes + kNoAllocTiles * sizeof(unsigned long long);
-// The size the header documents (512 KiB of look-back words + an 8,448-byte
+// The size the header documents (512 KiB of look-back words + a 256-byte
 // state block); a change of FrameState must update the documentation too.
-static_assert(kNoAllocScratchBytes == 532736, "documented scratch size of the no-alloc entry point");
+static_assert(kNoAllocScratchBytes == 524544, "documented scratch size of the no-alloc entry point");
 
 // FrameState block first, then one 64-bit look-back word per compaction tile.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];

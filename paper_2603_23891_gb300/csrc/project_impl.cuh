@@ -87,8 +87,8 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi)
 
 // Project node n (selected rank m) with camera cam: writes the 48-byte splat
 // record splat[m] and the footprint record foot[m] = {x0 | x1 << 16,
-// y0 | y1 << 16, pair count, depth bits}; returns the pair count.
-__device__ __forceinline__ uint32_t project_one(const DevTree& t, const DevCamera& cam, uint32_t n,
+// y0 | y1 << 16, pair count, depth bits}, and returns the footprint record.
+__device__ __forceinline__ uint4 project_one(const DevTree& t, const DevCamera& cam, uint32_t n,
                                                 uint32_t m, float* __restrict__ splat,
                                                 uint4* __restrict__ foot)
 {
@@ -137,8 +137,9 @@ __device__ __forceinline__ uint32_t project_one(const DevTree& t, const DevCamer
             if (x1 > x0 && y1 > y0) cnt = (uint32_t)((x1 - x0) * (y1 - y0));
         }
     }
-    foot[m] = make_uint4((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16),
-                         cnt, __float_as_uint(vz));
+    const uint4 fr = make_uint4((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16),
+                                cnt, __float_as_uint(vz));
+    foot[m] = fr;
     // ---- colour (FMA allowed: decides nothing), only for a Gaussian that emits
     // pairs: no pixel ever reads the colour of one that does not (about 40% of
     // the selection under shrinking), so its SH row is not fetched
@@ -153,7 +154,7 @@ __device__ __forceinline__ uint32_t project_one(const DevTree& t, const DevCamer
     out[0] = make_float4(u, v, A, B);
     out[1] = make_float4(C, lthr, a0, vz);
     out[2] = make_float4(rgb[0], rgb[1], rgb[2], radius);
-    return cnt;
+    return fr;
 }
 
 }  // namespace proj

@@ -29,10 +29,10 @@ FGS_SHRINK_ON = 1
 FGS_RENDER_STATS = 1
 FGS_RENDER_STAGE_EVENTS = 2
 FGS_RENDER_COUNT = 8
-FGS_N_STAGES = 6
+FGS_N_STAGES = 7
 FGS_BATCH_GRAPH = 4
 FGS_RENDER_KEEP = 16
-STAGE_NAMES = ["filter_rl", "ancestor_compact", "project_keys", "sort", "tile_ranges", "blend"]
+STAGE_NAMES = ["filter_rl", "ancestor_compact", "project", "tile_ranges", "keys", "sort", "blend"]
 SPLAT_FIELDS = ["u", "v", "A", "B", "C", "lthr", "a0", "depth", "r", "g", "b", "radius"]
 
 EXPORTED = ["fgs_version", "fgs_create", "fgs_destroy", "fgs_last_error", "fgs_set_params",

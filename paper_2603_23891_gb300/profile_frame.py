@@ -3,8 +3,11 @@
   python -m paper_2603_23891_gb300.profile_frame --workload city --frames 3 \
       [--tau 0.0772 --ln-tau -2.5616] [--pose 0]
 
-With --tau the frames use that shrink threshold and no calibration kernels run,
-so the launch sequence is exactly the per-frame path (12 kernels per frame).
+With --batch the 32-view batch of the city workload is rendered --frames times
+(shrink as given by --tau).  With --tau the frames use that shrink threshold and no calibration kernels run,
+so the launch sequence is exactly the per-frame path (9 kernels per frame:
+frame_begin, filter_pred, filter_anc, compact, project, tile_scan, scatter,
+segsort, blend).
 Without it the frames use the 3-sigma footprint.  With --backward the tree's
 attributes are first recomputed from its parameters (one prep_params launch)
 and every frame is followed by the differentiable form's backward for
@@ -30,6 +33,8 @@ def main():
     ap.add_argument("--tau", type=float, default=None)
     ap.add_argument("--ln-tau", dest="ln_tau", type=float, default=None)
     ap.add_argument("--backward", action="store_true")
+    ap.add_argument("--batch", action="store_true",
+                    help="render the 32-view city batch (16x16 tiles, 8x4 warps) instead")
     args = ap.parse_args()
 
     import torch
@@ -45,6 +50,17 @@ def main():
     r.load_tree(tree)
     if args.tau is not None:
         r.shrink(args.tau, args.ln_tau)
+    if args.batch:
+        bc = synth.city_batch_cameras()
+        r.batch_setup(bc, sel_capacity=96 << 20, pair_capacity=256 << 20)
+        t0 = time.time()
+        for _ in range(args.frames):
+            _, _, st, _ = r.render_batch(stats=True)
+        torch.cuda.synchronize()
+        print(f"{args.frames} batches of {len(bc)} views, entries={st.n_selected} N_P={st.n_pairs} "
+              f"launches/batch={st.n_launches} ({time.time() - t0:.3f}s)")
+        r.close()
+        return
     cam = cams[args.pose % len(cams)]
     r.set_camera(cam)
     P = G = dL = None

@@ -327,9 +327,9 @@ def test_blend_counters_consistent(renderer, tiny):
 
 
 def test_crowded_tiles_sorted_in_global_memory(renderer):
-    """Tiles holding more than 4096 pairs (the per-tile sort's shared-memory limit):
-    20k Gaussians seen at 64x48 on 16x16 tiles (12 tiles), sorted by the global-memory
-    bitonic network; pairs and image against the oracle."""
+    """Tiles holding more than 4096 pairs (the block sort's shared-memory limit): 20k
+    Gaussians seen at 64x48 on 16x16 tiles (12 tiles), each bucket sorted by one block
+    in global memory; pairs and image against the oracle."""
     tree = synth.random_small_tree(21, n_leaves=20000, branching=(2, 6), sh_degree=0,
                                    extent=6.0, log_scale_mean=-1.0)
     cam = synth.look_at_camera([0.0, -16.0, 8.0], [0.0, 0.0, 0.0], 64, 48, 60.0)
@@ -342,9 +342,9 @@ def test_crowded_tiles_sorted_in_global_memory(renderer):
     assert_frame_parity(g, o)
 
 
-def test_large_tile_grid_uses_radix_sort(renderer):
-    """A 4096x4096 image on 16x16 tiles (65,536 tiles: more than the tile-bucketing
-    prefix holds) takes the global radix sort; pairs bit for bit, sampled pixels."""
+def test_large_tile_grid(renderer):
+    """A 4096x4096 image on 16x16 tiles (65,536 tiles, the most a view may have: the
+    tile scan runs 16 rounds); pairs bit for bit, sampled pixels."""
     tree = synth.tiny_tree()
     cam = synth.look_at_camera([0.0, -60.0, 30.0], [0.0, 0.0, 0.0], 4096, 4096, 60.0)
     renderer.load_tree(tree)
@@ -399,4 +399,46 @@ def test_tile_grid_limit_rejected(renderer):
     cam = synth.tiny_camera()
     g = gpu_frame(renderer, tree, cam, 3.0)
     o, _ = oracle_frame(tree, cam, 3.0)
+    assert_frame_parity(g, o)
+
+
+@pytest.mark.parametrize("ties", [True, False])
+def test_bucket_sizes_at_sort_boundaries(renderer, ties):
+    """One row of 16x16 tiles whose tiles hold exactly 0, 1, 2, 32, 33, 64, 65, 128, 129,
+    256, 257, 511, 512, 513, 1024, 1025, 2048, 2049, 4096 and 4097 pairs (each Gaussian a
+    few pixels wide, inside one tile): every size class of the per-tile sort (one warp
+    with 1, 2, 4 or 8 items a lane; one block by radix with 2, 4 or 8 items a thread;
+    one block by bitonic network in shared or global memory) and its edges, with and
+    without depth ties inside the buckets (a tie sends a radix-sorted bucket to the
+    network); pairs, splats and image against the oracle."""
+    counts = [1, 32, 33, 64, 65, 128, 129, 256, 257, 511, 512, 513, 1024, 1025, 2048, 2049, 4096,
+              4097, 0, 2]
+    W, H = 16 * len(counts), 16
+    cam = synth.look_at_camera([0.0, 0.0, 0.0], [0.0, 1.0, 0.0], W, H, 60.0)
+    R = np.asarray(cam.R, np.float64).reshape(3, 3)
+    t = np.asarray(cam.t, np.float64)
+    rng = np.random.default_rng(17)
+    pts = []
+    for i, c in enumerate(counts):
+        u = 16 * i + rng.uniform(3.5, 12.5, c)
+        v = rng.uniform(3.5, 12.5, c)
+        if ties:                                                     # repeated depths
+            z = rng.choice(rng.uniform(5.0, 40.0, max(c // 3, 1)), c)
+        else:                                                        # distinct depths
+            z = rng.permutation(5.0 + np.arange(c) * (35.0 / max(c, 1)))
+        xc = (u - cam.cx) * z / cam.fx
+        yc = (v - cam.cy) * z / cam.fy
+        cpts = np.stack([xc, yc, z], 1)
+        pts.append((cpts - t) @ R)                                   # world = R^T (c - t)
+    mu = np.concatenate(pts)
+    n = mu.shape[0]
+    tree = synth.tree_from_gaussians(mu, np.full((n, 3), -6.0), np.tile([1.0, 0, 0, 0], (n, 1)),
+                                     rng.normal(0, 1, n), rng.normal(0, 1, (n, 1, 3)), 0)
+    renderer.load_tree(tree)
+    g = gpu_frame(renderer, tree, cam, -1.0)
+    o, _ = oracle_frame(tree, cam, -1.0)
+    per_tile = np.bincount((o.keys >> np.uint64(32)).astype(np.int64), minlength=len(counts))
+    assert np.array_equal(per_tile, counts), per_tile
+    depth_tie = (o.keys[1:] == o.keys[:-1])
+    assert depth_tie.any() == ties
     assert_frame_parity(g, o)
