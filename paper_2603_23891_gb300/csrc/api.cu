@@ -1076,8 +1076,7 @@ int fgs_backward(fgs_ctx* c, void* stream, const float* dL_drgb, const fgs_gauss
     cudaStream_t s = (cudaStream_t)stream;
     const float* params[5] = {p->mu, p->log_scale, p->quat, p->logit, p->sh};
     float* grads[5] = {gr->mu, gr->log_scale, gr->quat, gr->logit, gr->sh};
-    launch_backward(c->tree, dc, c->ranges, c->vals1, c->splat,
-                    c->frame_kept ? c->keep : nullptr, c->sel,
+    launch_backward(c->tree, dc, c->ranges, c->vals1, c->splat, c->keep, c->frame_kept, c->sel,
                     dL_drgb, c->gsplat, params, grads, (flags & FGS_BACKWARD_ACCUMULATE) != 0, c->sms, c->st,
                     s);
     FGS_CUDA(c, cudaGetLastError());

@@ -16,6 +16,8 @@
 // 12 shuffles for 9 values) and added per Gaussian; project_bwd_kernel then
 // applies the chain rule to the parameters.
 #include "blend_impl.cuh"
+
+#include <type_traits>
 #include "project_impl.cuh"
 
 namespace fgs {
@@ -143,81 +145,106 @@ __global__ void __launch_bounds__(256) prep_sh_kernel(DevTree t, const float* __
 // ---------------------------------------------------------------------------
 // blend backward
 // ---------------------------------------------------------------------------
-template <bool kWalk>
-struct BwdSmem {
-    blendk::BlendSmem<false> S;
-    blendk::GroupSmem<kWalk> G;     // the re-walk's scratch (not needed with kept state)
-    uint32_t m[256];
-    uint32_t lim[8];
+// Shared memory of the blend backward: the forward's half-block walk (used to
+// recompute each pixel's final T and stop position) and the back-to-front
+// gradient walk over half-block lists, one after the other.
+struct BwdWalkSmem {
+    uint32_t vals[blendk::kValsSlots];
+    float4 g0[blendk::kChunk];                  // u, v, A', B'
+    float4 g1[blendk::kChunk];                  // C', lthr, alpha0, depth
+    float4 g2[blendk::kChunk];                  // r, g, b, radius
+    uint32_t m[blendk::kChunk];                 // selected rank of each chunk entry
+    uint16_t hmask[blendk::kChunk];
+    alignas(16) uint8_t hl[blendk::kHalfBlocks][blendk::kChunk];
+    uint32_t hlim[blendk::kHalfBlocks];         // last stop position of each half-block
+    uint64_t bar;
+    int timed_out;
 };
+union BwdSmem {
+    blendk::HalfSmem fwd;
+    BwdWalkSmem bwd;
+};
+__device__ __forceinline__ BwdWalkSmem& walk_smem(BwdSmem& b) { return b.bwd; }
+__device__ __forceinline__ BwdWalkSmem& walk_smem(BwdWalkSmem& b) { return b; }
 
-// Sum over the warp of v[0..8], scattered: on return the lane given by
-// lane_component() holds the warp sum of its component.  Recursive halving
-// (xor 16, 8, 4, 2 split the value set, xor 1 completes the sums): 12
-// shuffles instead of 45 for nine butterfly reductions.
-__device__ __forceinline__ float warp_reduce9(const float v[9], uint32_t lane)
+// Sum over each half-warp (16 lanes) of v[0..8], scattered: on return the lane
+// given by half_component() holds its half's sum of that component.  Recursive
+// halving within the half (xor 8, 4, 2, 1 split the value set): 11 shuffles.
+__device__ __forceinline__ float half_reduce9(const float v[9], uint32_t lane)
 {
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    const bool b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
     float a[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         const float lo = v[i], hi = (5 + i < 9) ? v[5 + i] : 0.0f;
-        a[i] = (b4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b4 ? lo : hi, 16);
+        a[i] = (b3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8);
     }
     float b[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float lo = a[i], hi = (3 + i < 5) ? a[3 + i] : 0.0f;
-        b[i] = (b3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8);
+        b[i] = (b2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
     }
     float c[2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const float lo = b[i], hi = (2 + i < 3) ? b[2 + i] : 0.0f;
-        c[i] = (b2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
+        c[i] = (b1 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b1 ? lo : hi, 2);
     }
-    const float d = (b1 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b1 ? c[0] : c[1], 2);
-    return d + __shfl_xor_sync(0xffffffffu, d, 1);
+    return (b0 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b0 ? c[0] : c[1], 1);
 }
 
-// Component whose sum warp_reduce9 leaves in this lane (even lanes only; -1 for
-// lanes holding padding or the duplicate odd copy).
-__device__ __forceinline__ int lane_component(uint32_t lane)
+// Component whose half sum half_reduce9 leaves in this lane (-1: padding).
+__device__ __forceinline__ int half_component(uint32_t lane)
 {
-    const int pc = (lane >> 1) & 1;
-    const int pb = 2 * ((lane >> 2) & 1) + pc;
-    const int pa = 3 * ((lane >> 3) & 1) + pb;
-    const int comp = 5 * ((lane >> 4) & 1) + pa;
-    return (!(lane & 1) && pb < 3 && pa < 5 && comp < 9) ? comp : -1;
+    const int pb = 2 * ((lane >> 1) & 1) + (lane & 1);
+    const int pa = 3 * ((lane >> 2) & 1) + pb;
+    const int comp = 5 * ((lane >> 3) & 1) + pa;
+    return (pb < 3 && pa < 5 && comp < 9) ? comp : -1;
 }
 
-// kKept: the forward kept {final T, stop} per pixel (FGS_RENDER_KEEP).  Otherwise
-// a first front-to-back walk over the tile recomputes them with the forward's
-// exact decisions (nothing but the image is stored by the forward).
+// kKept: the forward kept {final T, stop} per pixel (FGS_RENDER_KEEP) in keep.
+// Otherwise the forward's own half-block walk runs first, without colour, and
+// writes them there.  Then the tile is walked back to front over half-block
+// lists (a 4x4 half-warp tests only the Gaussians whose threshold box meets
+// it, as in the forward), the two halves of a warp in lockstep, each from its
+// list's last entry before its last stop.
 template <bool kKept>
 __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uint2* __restrict__ ranges,
                                                         const uint32_t* __restrict__ vals,
                                                         const float* __restrict__ splat,
-                                                        const uint2* __restrict__ keep,
+                                                        uint2* __restrict__ keep,
                                                         const float* __restrict__ dL_drgb,
                                                         float* __restrict__ gsplat, FrameState* st)
 {
-    __shared__ __align__(128) BwdSmem<!kKept> B;
-    blendk::BlendSmem<false>& S = B.S;
+    // (with kept state the forward walk's shared memory is not needed)
+    __shared__ __align__(128) typename std::conditional<kKept, BwdWalkSmem, BwdSmem>::type B;
     const uint32_t tile = blockIdx.x;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if constexpr (!kKept) {
+        blendk::blend_tile_half<false, true>(cam, tile, tile, B.fwd, ranges, vals, splat, nullptr, nullptr,
+                                            keep, st);
+        __syncthreads();
+        if (B.fwd.timed_out) return;
+    }
+    BwdWalkSmem& S = walk_smem(B);
     const int32_t tx0 = (int32_t)(tile % (uint32_t)cam.tiles_x) * cam.tile_w;
     const int32_t ty0 = (int32_t)(tile / (uint32_t)cam.tiles_x) * cam.tile_h;
     int32_t wx0, wy0;
     blendk::warp_origin(cam, tx0, ty0, warp, wx0, wy0);
-    const int32_t x = wx0 + (int32_t)(lane & ((1u << cam.warp_shift) - 1u));
-    const int32_t y = wy0 + (int32_t)(lane >> cam.warp_shift);
+    const uint32_t half = lane >> 4, q = lane & 15u;
+    const bool wide = cam.warp_shift == 3;
+    const int32_t x = wx0 + (int32_t)(q & 3u) + (wide ? 4 * (int32_t)half : 0);
+    const int32_t y = wy0 + (int32_t)(q >> 2) + (wide ? 0 : 4 * (int32_t)half);
+    const uint32_t hb = ((uint32_t)(y - ty0) >> 2 << (cam.tile_shift_x - 2)) | ((uint32_t)(x - tx0) >> 2);
+    const uint32_t hb0 = __shfl_sync(0xffffffffu, hb, 0), hb1 = __shfl_sync(0xffffffffu, hb, 16);
     const bool inside = x < cam.width && y < cam.height;
     const float px = fa((float)x, 0.5f), py = fa((float)y, 0.5f);
     const uint2 rg = ranges[tile];
     const uint32_t M = st->M;
     const uint32_t s = rg.x;
-    const int comp = lane_component(lane);
+    const int comp = half_component(lane);
+    const uint32_t lt = (1u << lane) - 1u;
 
     // this pixel's forward outcome: final T, stop position, and dL/dC
     float T = 1.0f;
@@ -225,92 +252,34 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
     float dC[3] = {0.0f, 0.0f, 0.0f};
     if (inside) {
         const size_t hw = (size_t)cam.width * cam.height, pix = (size_t)y * cam.width + x;
-        if (kKept) {
-            const uint2 kp = keep[pix];
-            T = __uint_as_float(kp.x);
-            lim = kp.y;
-        }
+        const uint2 kp = keep[pix];
+        T = __uint_as_float(kp.x);
+        lim = kp.y;
         dC[0] = __ldg(dL_drgb + pix);
         dC[1] = __ldg(dL_drgb + hw + pix);
         dC[2] = __ldg(dL_drgb + 2 * hw + pix);
     }
+    // each half-block's last stop position; the tile's bounds the chunks
+    const uint32_t hmax = max(lim, __shfl_xor_sync(0xffffffffu, lim, 8));
+    const uint32_t hmax2 = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, 4));
+    const uint32_t hmax3 = max(hmax2, __shfl_xor_sync(0xffffffffu, hmax2, 2));
+    const uint32_t hlim = max(hmax3, __shfl_xor_sync(0xffffffffu, hmax3, 1));
+    if (q == 0) S.hlim[hb] = hlim;
     if (tid == 0) {
         blendk::mbar_init(&S.bar, 1);
         S.timed_out = 0;
     }
     __syncthreads();
-    uint32_t phase = 0;
-    if (!kKept) {
-        // recompute final T and the stop position: the forward walk without colour
-        bool done = !inside;
-        lim = inside ? rg.y : s;
-        for (uint32_t s0 = s; s0 < rg.y; s0 += blendk::kChunk) {
-            const uint32_t e0 = min(rg.y, s0 + blendk::kChunk);
-            const uint32_t cnt = e0 - s0;
-            const uint32_t off = blendk::stage_vals(S.vals, &S.bar, &S.timed_out, vals, s0, e0, phase, st);
-            if (S.timed_out) return;
-            if (tid < cnt) {
-                uint32_t m = S.vals[off + tid];
-                if (m >= M) m = 0;
-                const float4* g = reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride);
-                const float4 a = __ldg(g), b = __ldg(g + 1);
-                blendk::put_coeffs(S.g0[tid], S.g1[tid], a, b);
-                S.wmask[tid] = blendk::warp_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
-            }
-            __syncthreads();
-            uint32_t wcnt = 0;
-            for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
-                const uint32_t j = j0 + lane;
-                const bool mine = j < cnt && ((S.wmask[j] >> warp) & 1u);
-                const uint32_t bb = __ballot_sync(0xffffffffu, mine);
-                if (mine) S.wlist[warp][wcnt + __popc(bb & ((1u << lane) - 1u))] = (uint16_t)j;
-                wcnt += __popc(bb);
-            }
-            if (wcnt + lane < ((wcnt + 3u) & ~3u)) S.wlist[warp][wcnt + lane] = 0;
-            __syncwarp();
-            // the forward's group walk: lockstep tests, then each lane applies its
-            // own hits in order (same operations and order as the forward)
-            float (*pw)[32] = B.G.pw[warp];
-            float4* grp = B.G.grp[warp];
-            for (uint32_t i0 = 0; i0 < wcnt; i0 += blendk::kGroup) {
-                if (__all_sync(0xffffffffu, done)) break;
-                const uint32_t ng = min((uint32_t)blendk::kGroup, wcnt - i0);
-                uint32_t hits = blendk::group_tests(S.g0, S.g1, &S.wlist[warp][i0], ng, px, py, pw, lane);
-                if (done) hits = 0;
-                if (lane < ng) grp[lane].x = S.g1[S.wlist[warp][i0 + lane]].z;
-                __syncwarp();
-                while (__any_sync(0xffffffffu, hits != 0u)) {
-                    if (hits) {
-                        const uint32_t e = __ffs(hits) - 1;
-                        hits &= hits - 1u;
-                        float alpha = fm(grp[e].x, exp_nonpos(pw[e][lane]));
-                        alpha = alpha < 0.99f ? alpha : 0.99f;
-                        const float Tn = fm(T, fs(1.0f, alpha));
-                        if (Tn < 0.0001f) {
-                            done = true;
-                            hits = 0;
-                            lim = s0 + S.wlist[warp][i0 + e];
-                        } else {
-                            T = Tn;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-            if (__syncthreads_count(done) == (int)blockDim.x) break;
-        }
-    }
-    const uint32_t wlim = __reduce_max_sync(0xffffffffu, lim);
-    if (lane == 0) B.lim[warp] = wlim;
-    __syncthreads();
-    uint32_t e = B.lim[0];
+    uint32_t e = S.hlim[0];
 #pragma unroll
-    for (int w = 1; w < 8; ++w) e = max(e, B.lim[w]);
+    for (int h = 1; h < blendk::kHalfBlocks; ++h) e = max(e, S.hlim[h]);
     e = min(e, rg.y);                    // no pixel of the tile reaches past e
+    const uint32_t hlim0 = S.hlim[hb0], hlim1 = S.hlim[hb1];
 
     float Bk[3] = {cam.bg[0] * T, cam.bg[1] * T, cam.bg[2] * T};   // colour behind, absolute
     float Tc = T;                                                    // transmittance after
     if (e <= s) return;
+    uint32_t phase = 0;
     const uint32_t n_chunks = (e - s + blendk::kChunk - 1) / blendk::kChunk;
     for (int c = (int)n_chunks - 1; c >= 0; --c) {
         const uint32_t s0 = s + (uint32_t)c * blendk::kChunk, e0 = min(e, s0 + blendk::kChunk);
@@ -324,30 +293,42 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
             const float4 a = __ldg(g), b = __ldg(g + 1);
             blendk::put_coeffs(S.g0[tid], S.g1[tid], a, b);
             S.g2[tid] = __ldg(g + 2);
-            S.wmask[tid] = blendk::warp_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
-            B.m[tid] = m;
+            S.hmask[tid] = (uint16_t)blendk::half_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
+            S.m[tid] = m;
         }
         __syncthreads();
-        // this warp's ordered list of the chunk entries before its last stop
-        uint32_t wcnt = 0;
+        // this warp's two half-block lists of the chunk entries before their last stops
+        uint32_t n0 = 0, n1 = 0;
         for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
             const uint32_t j = j0 + lane;
-            const bool mine = j < cnt && s0 + j < wlim && ((S.wmask[j] >> warp) & 1u);
-            const uint32_t bb = __ballot_sync(0xffffffffu, mine);
-            if (mine) S.wlist[warp][wcnt + __popc(bb & ((1u << lane) - 1u))] = (uint16_t)j;
-            wcnt += __popc(bb);
+            const uint32_t hm = j < cnt ? (uint32_t)S.hmask[j] : 0u;
+            const bool in0 = ((hm >> hb0) & 1u) && s0 + j < hlim0;
+            const bool in1 = ((hm >> hb1) & 1u) && s0 + j < hlim1;
+            const uint32_t b0 = __ballot_sync(0xffffffffu, in0);
+            const uint32_t b1 = __ballot_sync(0xffffffffu, in1);
+            if (in0) S.hl[hb0][n0 + __popc(b0 & lt)] = (uint8_t)j;
+            if (in1) S.hl[hb1][n1 + __popc(b1 & lt)] = (uint8_t)j;
+            n0 += __popc(b0);
+            n1 += __popc(b1);
         }
         __syncwarp();
-        for (int i = (int)wcnt - 1; i >= 0; --i) {
-            const uint32_t j = S.wlist[warp][i];
+        const uint32_t nmax = max(n0, n1);
+        const uint32_t nh = half ? n1 : n0;
+        const uint8_t* myl = S.hl[hb];
+        // step k: each half takes its entry k - (nmax - nh), the lists' ends aligned
+        for (int k = (int)nmax - 1; k >= 0; --k) {
+            const int i = k - (int)(nmax - nh);
+            const bool valid = i >= 0;
+            const uint32_t j = valid ? myl[i] : 0u;
             // branch-free: every lane evaluates; the lanes whose pixel applied the
             // Gaussian in the forward (same decisions) contribute, the others add 0
             const float4 g0 = S.g0[j];
             const float4 g1 = S.g1[j];
             const float dx = fs(g0.x, px), dy = fs(g0.y, py);
             const float power = blendk::power_of(g0.z, g0.w, g1.x, dx, dy);
-            const bool hit = s0 + j < lim && !(power > 0.0f || power < g1.y);
-            if (!__any_sync(0xffffffffu, hit)) continue;
+            const bool hit = valid && s0 + j < lim && !(power > 0.0f || power < g1.y);
+            const uint32_t hb_any = __ballot_sync(0xffffffffu, hit);
+            if (!hb_any) continue;
             const float ex = exp_nonpos(fminf(power, 0.0f));
             const float raw = fm(g1.z, ex);
             const bool clamped = !(raw < 0.99f);
@@ -375,8 +356,9 @@ __global__ void __launch_bounds__(256) blend_bwd_kernel(DevCamera cam, const uin
             // d power / du = -(A dx + B dy) = 2 A' dx + B' dy, likewise for v
             g[0] = gpow * (2.0f * g0.z * dx + g0.w * dy);          // u
             g[1] = gpow * (2.0f * g1.x * dy + g0.w * dx);          // v
-            const float v = warp_reduce9(g, lane);
-            if (comp >= 0) atomicAdd(gsplat + (size_t)B.m[j] * kGS + comp, v);
+            const float v = half_reduce9(g, lane);
+            const bool my_half_hit = ((hb_any >> (half << 4)) & 0xFFFFu) != 0u;
+            if (comp >= 0 && my_half_hit) atomicAdd(gsplat + (size_t)S.m[j] * kGS + comp, v);
         }
         __syncthreads();
     }
@@ -704,13 +686,13 @@ static void launch_project_bwd(const DevTree& t, const DevCamera& cam, const Par
 }
 
 void launch_backward(const DevTree& t, const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
-                     const float* splat, const uint2* keep, const uint32_t* sel, const float* dL_drgb,
+                     const float* splat, uint2* keep, bool kept, const uint32_t* sel, const float* dL_drgb,
                      float* gsplat, const float* const params[5], float* const grads[5], bool accumulate,
                      int sms, FrameState* st, cudaStream_t s)
 {
     // gsplat rows of the selected Gaussians start at zero: the blend backward adds into them
     zero_rows_kernel<<<sms * 8, 128, 0, s>>>(reinterpret_cast<float4*>(gsplat), st);
-    if (keep)
+    if (kept)
         blend_bwd_kernel<true><<<cam.tiles_x * cam.tiles_y, 256, 0, s>>>(cam, ranges, vals, splat, keep, dL_drgb,
                                                                      gsplat, st);
     else

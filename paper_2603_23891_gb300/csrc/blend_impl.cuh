@@ -72,15 +72,8 @@ struct BlendSmem {
     int timed_out;
 };
 
-// Per-warp scratch of the backward's group walk over per-warp lists: each
-// lane's binary32 power for every entry of the group, and the entries' alpha0
-// and colour.  (The forward's half-block walk keeps the same in HalfSmem.)
+// Entries of a half-block list whose powers a walk tests before applying hits.
 constexpr int kGroup = 32;
-template <bool kUsed>
-struct GroupSmem {
-    float pw[kUsed ? 8 : 1][kUsed ? kGroup : 1][32];
-    float4 grp[kUsed ? 8 : 1][kUsed ? kGroup : 1];   // alpha0, r, g, b
-};
 
 // The Gaussian's exponent at offset (dx, dy) = (u - px, v - py):
 // -1/2 (A dx^2 + 2 B dx dy + C dy^2) = (A' dx + B' dy) dx + (C' dy) dy with the
@@ -97,35 +90,6 @@ __device__ __forceinline__ void put_coeffs(float4& d0, float4& d1, float4 a, flo
 {
     d0 = make_float4(a.x, a.y, fm(-0.5f, a.z), -a.w);
     d1 = make_float4(fm(-0.5f, b.x), b.y, b.z, b.w);
-}
-
-// Phase 1 of the group walk: this lane's binary32 power for each of the ng
-// (<= kGroup) entries of the warp list wl (chunk slots), parked in pw[e][lane],
-// and the bit mask of the entries whose power passes both skip tests.  The list
-// is read four entries at a time; it must be padded with valid slots to a
-// multiple of 4 (the padding's bits are cleared).
-__device__ __forceinline__ uint32_t group_tests(const float4* __restrict__ g0s,
-                                                const float4* __restrict__ g1s, const uint16_t* wl,
-                                                uint32_t ng, float px, float py, float (*pw)[32],
-                                                uint32_t lane)
-{
-    const uint2* wl4 = reinterpret_cast<const uint2*>(wl);
-    uint32_t hits = 0;
-    for (uint32_t e = 0; e < ng; e += 4) {
-        const uint2 jj = wl4[e >> 2];
-        const uint32_t jx[4] = {jj.x & 0xffffu, jj.x >> 16, jj.y & 0xffffu, jj.y >> 16};
-        uint32_t nib = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float4 a = g0s[jx[k]];
-            const float4 b = g1s[jx[k]];
-            const float power = power_of(a.z, a.w, b.x, fs(a.x, px), fs(a.y, py));
-            pw[e + k][lane] = power;
-            nib |= (uint32_t)!(power > 0.0f || power < b.y) << k;
-        }
-        hits |= nib << e;
-    }
-    return ng >= 32u ? hits : hits & ((1u << ng) - 1u);
 }
 
 // Bring chunk [s0, e0) of the sorted values into shared memory with one TMA bulk
@@ -374,10 +338,13 @@ __device__ __forceinline__ uint32_t half_mask(const DevCamera& cam, int32_t tx0,
     return mask;
 }
 
-// group_tests over a list of 8-bit chunk slots: the warp-uniform bound ngw
-// covers both halves' groups; bits past this half's own ng are cleared.  Any
-// 8-bit slot indexes the chunk arrays, so entries read past a list's end are
-// harmless and masked.
+// Phase 1 of the group walk: this lane's binary32 power for each entry of its
+// half-block's group (the list wl of 8-bit chunk slots), parked in pw[e][lane],
+// and the bit mask of the entries whose power passes both skip tests.  The
+// list is read four entries at a time; the warp-uniform bound ngw covers both
+// halves' groups and bits past this half's own ng are cleared.  Any 8-bit slot
+// indexes the chunk arrays, so entries read past a list's end are harmless and
+// masked.
 __device__ __forceinline__ uint32_t half_group_tests(const float4* __restrict__ g0s,
                                                      const float4* __restrict__ g1s, const uint8_t* wl,
                                                      uint32_t ngw, uint32_t ng, float px, float py,
@@ -552,12 +519,14 @@ __device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t t
         const int n_done = __syncthreads_count(done);
         if (n_done == (int)blockDim.x) break;
     }
-    if (inside && rgb) {
+    if (inside) {
         const size_t hw = (size_t)cam.width * cam.height;
         const size_t pix = (size_t)y * cam.width + x;
-        rgb[pix] = fmaf(T, cam.bg[0], Cacc.x);
-        rgb[hw + pix] = fmaf(T, cam.bg[1], Cacc.y);
-        rgb[2 * hw + pix] = fmaf(T, cam.bg[2], Cacc.z);
+        if (rgb) {
+            rgb[pix] = fmaf(T, cam.bg[0], Cacc.x);
+            rgb[hw + pix] = fmaf(T, cam.bg[1], Cacc.y);
+            rgb[2 * hw + pix] = fmaf(T, cam.bg[2], Cacc.z);
+        }
         if (Tout) Tout[pix] = T;
         if (kKeep && !done) keep_out[pix] = make_uint2(__float_as_uint(T), e);   // did not stop
     }

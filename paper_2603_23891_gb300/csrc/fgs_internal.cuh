@@ -381,8 +381,10 @@ void launch_batch_blend(const DevCamera* cams, int V, uint32_t total_tiles, cons
                         const float* splat, float* rgb, float* T, FrameState* st, cudaStream_t s);
 void launch_prep_params(const DevTree& t, const float* mu, const float* log_scale, const float* quat,
                         const float* logit, const float* sh, int blocks, cudaStream_t s);
+// keep: per-pixel {final T, stop} buffer; kept: the last forward filled it
+// (FGS_RENDER_KEEP), otherwise the blend backward recomputes it there.
 void launch_backward(const DevTree& t, const DevCamera& cam, const uint2* ranges, const uint32_t* vals,
-                     const float* splat, const uint2* keep, const uint32_t* sel, const float* dL_drgb,
+                     const float* splat, uint2* keep, bool kept, const uint32_t* sel, const float* dL_drgb,
                      float* gsplat,
                      const float* const params[5], float* const grads[5], bool accumulate, int proj_blocks,
                      FrameState* st, cudaStream_t s);
