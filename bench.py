@@ -165,9 +165,34 @@ OPS_PER_HIT = 24.0    # exp (15: k by one FMA and a subtraction, reduction 2 FMA
                       # clamp, 1 - alpha, T update, stop test, weight, 3 colour FMAs
 
 
+# source files of each frame kernel (a kernel's committed DRAM figure is used only
+# while these files are unchanged)
+KERNEL_SOURCES = {
+    "frame_begin_kernel": ["filter.cu", "fgs_internal.cuh"],
+    "filter_pred_kernel": ["filter.cu", "fgs_internal.cuh"],
+    "filter_anc_kernel": ["filter.cu", "fgs_internal.cuh"],
+    "compact_kernel": ["filter.cu", "fgs_internal.cuh"],
+    "project_kernel": ["project.cu", "project_impl.cuh", "pairs_impl.cuh", "fgs_internal.cuh"],
+    "tile_scan_kernel": ["pairs.cu", "pairs_impl.cuh", "fgs_internal.cuh"],
+    "scatter_kernel": ["pairs.cu", "pairs_impl.cuh", "fgs_internal.cuh"],
+    "segsort_kernel": ["pairs.cu", "pairs_impl.cuh", "fgs_internal.cuh"],
+    "blend_kernel": ["blend.cu", "blend_impl.cuh", "fgs_internal.cuh"],
+}
+# the kernels of each bench stage
+STAGE_KERNELS = {
+    "filter_rl": ["frame_begin_kernel", "filter_pred_kernel"],
+    "ancestor_compact": ["filter_anc_kernel", "compact_kernel"],
+    "project": ["project_kernel"],
+    "tile_ranges": ["tile_scan_kernel"],
+    "keys": ["scatter_kernel"],
+    "sort": ["segsort_kernel"],
+    "blend": ["blend_kernel"],
+}
+
+
 def _kernel_sources_sha(kernel):
     import hashlib
-    files = {"blend_kernel": ["blend.cu", "blend_impl.cuh", "fgs_internal.cuh"]}.get(kernel)
+    files = KERNEL_SOURCES.get(kernel)
     if not files:
         return None
     h = hashlib.sha256()
@@ -177,9 +202,10 @@ def _kernel_sources_sha(kernel):
 
 
 def profiled_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (profiles/traffic.txt: '<kernel> <source sha16> <bytes>'), or None if the
-    kernel source changed since it was captured."""
+    """Mean DRAM bytes per launch of `kernel` on the bench workload's timed poses,
+    from the committed ncu summary (profiles/traffic.txt: '<kernel> <source
+    sha16> <bytes>'), or None if the kernel source changed since it was
+    captured."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -558,8 +584,10 @@ def run_ours(args):
         stages = {}
         for i, nm in enumerate(STAGES):
             gbs = ab[nm] / (st_mean[i] * 1e-3) / 1e9 if st_mean[i] > 0 else 0.0
+            traffic = [profiled_traffic(k) for k in STAGE_KERNELS[nm]]
             stages[nm] = {"ms": round(float(st_mean[i]), 5), "algo_bytes": round(ab[nm]),
-                          "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)}
+                          "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4),
+                          "dram_bytes": None if None in traffic else int(sum(traffic))}
         dom = STAGES[int(np.argmax(st_mean))]
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         if dom == "blend":

@@ -28,7 +28,11 @@
  *    pointers synchronise the stream before returning.
  *  - Errors raised on the device (pair capacity exceeded, a bounded spin-wait
  *    that timed out) are latched in a device status word and returned by the
- *    next synchronising call or fgs_sync().
+ *    next synchronising call or fgs_sync().  After FGS_ERR_TIMEOUT from a
+ *    render (a blend's staging copy whose wait gave up may still have been in
+ *    flight when its block exited) the frame and the context are not to be
+ *    trusted: destroy the context.  (fgs_probe_wait_timeout's timeout is the
+ *    exception: its wait has no copy in flight.)
  *  - A context is not thread-safe; use one context per host thread.
  */
 #ifndef FILTERGS_H

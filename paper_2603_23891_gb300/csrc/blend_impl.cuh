@@ -95,7 +95,11 @@ __device__ __forceinline__ void put_coeffs(float4& d0, float4& d1, float4 a, flo
 // Bring chunk [s0, e0) of the sorted values into shared memory with one TMA bulk
 // copy of the 16-byte aligned superset [s0 & ~3, (e0 + 3) & ~3).  Returns the
 // offset of s0 inside the staged copy.  Called by all threads; thread 0 issues
-// the copy and waits on the mbarrier (bounded).
+// the copy and waits on the mbarrier (bounded).  If the wait gives up, the
+// status FGS_ERR_TIMEOUT is latched and the callers leave the tile; the copy may
+// still be in flight into the block's shared memory as the block exits, so
+// after such a timeout neither the frame's output nor the context can be
+// trusted (the caller must destroy the context).
 __device__ __forceinline__ uint32_t stage_vals(uint32_t* dst, uint64_t* bar, int* timed_out,
                                                const uint32_t* vals, uint32_t s0, uint32_t e0,
                                                uint32_t& phase, FrameState* st)

@@ -3,7 +3,7 @@
   python -m paper_2603_23891_gb300.profile_frame --workload city --frames 3 \
       [--tau 0.0772 --ln-tau -2.5616] [--pose 0]
 
-With --batch the 32-view batch of the city workload is rendered --frames times
+With --cycle frame k renders pose (pose + k) mod poses.  With --batch the 32-view batch of the city workload is rendered --frames times
 (shrink as given by --tau).  With --tau the frames use that shrink threshold and no calibration kernels run,
 so the launch sequence is exactly the per-frame path (9 kernels per frame:
 frame_begin, filter_pred, filter_anc, compact, project, tile_scan, scatter,
@@ -33,6 +33,8 @@ def main():
     ap.add_argument("--tau", type=float, default=None)
     ap.add_argument("--ln-tau", dest="ln_tau", type=float, default=None)
     ap.add_argument("--backward", action="store_true")
+    ap.add_argument("--cycle", action="store_true",
+                    help="frame k renders pose (pose + k) mod poses (the bench's timed poses)")
     ap.add_argument("--batch", action="store_true",
                     help="render the 32-view city batch (16x16 tiles, 8x4 warps) instead")
     args = ap.parse_args()
@@ -75,7 +77,9 @@ def main():
         r.update_params(P)
     t0 = time.time()
     st = None
-    for _ in range(args.frames):
+    for k in range(args.frames):
+        if args.cycle:
+            r.set_camera(cams[(args.pose + k) % len(cams)])
         _, _, st = r.render(stats=True, keep=args.backward)
         if args.backward:
             r.backward(dL, P, G, accumulate=True)
