@@ -477,31 +477,36 @@ __device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t t
             __syncwarp();
             const float4* grp = H.grp[warp][half];
             uint32_t proc = 0, n_eval = ng;
-            while (__any_sync(0xffffffffu, hits != 0u)) {
-                if (hits) {
-                    const uint32_t e = __ffs(hits) - 1;
-                    hits &= hits - 1u;
-                    const float4 qv = grp[e];
-                    float alpha = fm(qv.x, exp_nonpos(pw[e][lane]));
-                    alpha = alpha < 0.99f ? alpha : 0.99f;
-                    const float Tn = fm(T, fs(1.0f, alpha));
-                    if (kCount) {
-                        ++c_hits;
-                        proc |= 1u << e;
-                    }
-                    if (Tn < 0.0001f) {
-                        done = true;                    // stop before adding this Gaussian
-                        hits = 0;
-                        n_eval = e + 1;
-                        if (kKeep)
-                            keep_out[(size_t)y * cam.width + x] = make_uint2(__float_as_uint(T), s0 + myl[i0 + e]);
-                    } else {
-                        const float w = alpha * T;
-                        Cacc.x = fmaf(qv.y, w, Cacc.x);
-                        Cacc.y = fmaf(qv.z, w, Cacc.y);
-                        Cacc.z = fmaf(qv.w, w, Cacc.z);
-                        T = Tn;
-                    }
+            // as many rounds as the lane with most hits; a hit's power is at least
+            // its skip threshold, -ln 255 - ln alpha0 >= -5.55, so exp_hit applies
+            const uint32_t n_rounds = __reduce_max_sync(0xffffffffu, (uint32_t)__popc(hits));
+            for (uint32_t round = 0; round < n_rounds; ++round) {
+                // branch-free: a lane without a hit left (or whose application
+                // stops) computes on entry 0 and adds nothing
+                const bool valid = hits != 0u;
+                const uint32_t e = valid ? (uint32_t)(__ffs(hits) - 1) : 0u;
+                hits &= hits - 1u;
+                const float4 qv = grp[e];
+                float alpha = fm(qv.x, exp_hit(pw[e][lane]));
+                alpha = alpha < 0.99f ? alpha : 0.99f;
+                const float Tn = fm(T, fs(1.0f, alpha));
+                const bool stop = valid && Tn < 0.0001f;       // stop before adding this Gaussian
+                const bool apply = valid && !(Tn < 0.0001f);
+                const float w = apply ? alpha * T : 0.0f;
+                Cacc.x = fmaf(apply ? qv.y : 0.0f, w, Cacc.x);
+                Cacc.y = fmaf(apply ? qv.z : 0.0f, w, Cacc.y);
+                Cacc.z = fmaf(apply ? qv.w : 0.0f, w, Cacc.z);
+                if (kCount && valid) {
+                    ++c_hits;
+                    proc |= 1u << e;
+                }
+                if (kKeep && stop)
+                    keep_out[(size_t)y * cam.width + x] = make_uint2(__float_as_uint(T), s0 + myl[i0 + e]);
+                T = apply ? Tn : T;
+                if (stop) {
+                    done = true;
+                    hits = 0;
+                    n_eval = e + 1;
                 }
             }
             __syncwarp();

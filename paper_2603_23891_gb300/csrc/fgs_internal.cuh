@@ -100,14 +100,14 @@ __device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
 
 __device__ __forceinline__ float ff(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
-// e^x in binary32, x <= 0 or NaN: Cody & Waite argument reduction (x = k ln2 + r,
-// k the integer nearest x log2(e), taken from the binary32 sum x log2(e) +
-// 1.5 * 2^23 formed with one rounding; ln 2 split into a short leading part and
-// a correction), the degree-7 Taylor polynomial of e^r by Horner's rule with
-// fused multiply-adds, scaled by 2^k from exponent bits (k = the low bits of
-// that sum).  Explicitly rounded operations, so the bits do not depend on the
-// compiler; for x <= 0 the same as exp_cw below.
-__device__ __forceinline__ float exp_nonpos(float x)
+// e^x in binary32 for x in [-87, 0]: Cody & Waite argument reduction
+// (x = k ln2 + r, k the integer nearest x log2(e), taken from the binary32 sum
+// x log2(e) + 1.5 * 2^23 formed with one rounding; ln 2 split into a short
+// leading part and a correction), the degree-7 Taylor polynomial of e^r by
+// Horner's rule with fused multiply-adds, scaled by 2^k from exponent bits
+// (k = the low bits of that sum; k + 127 lies in [1, 254] for x >= -87).
+// Explicitly rounded operations, so the bits do not depend on the compiler.
+__device__ __forceinline__ float exp_hit(float x)
 {
     const float t = ff(x, 1.44269504088896341f, 12582912.0f);
     const float kf = fs(t, 12582912.0f);
@@ -121,10 +121,14 @@ __device__ __forceinline__ float exp_nonpos(float x)
     p = ff(p, r, 0.5f);
     p = ff(p, r, 1.0f);
     p = ff(p, r, 1.0f);
-    // (k + 127) << 23 with k = bits(t) - bits(1.5 * 2^23); only the low 9 bits of
-    // bits(t) survive the shift, and k + 127 lies in [1, 254] for x >= -87
     const float two_k = __uint_as_float((__float_as_uint(t) + (uint32_t)(127 - 0x4B400000)) << 23);
-    const float y = fm(p, two_k);
+    return fm(p, two_k);
+}
+
+// The same for x <= 0 or NaN (0 below -87); for x <= 0 the same as exp_cw below.
+__device__ __forceinline__ float exp_nonpos(float x)
+{
+    const float y = exp_hit(x);
     return x < -87.0f ? 0.0f : y;
 }
 

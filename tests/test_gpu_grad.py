@@ -83,15 +83,21 @@ def test_accumulate_and_autograd(renderer):
     dLt = torch.from_numpy(dL).cuda()
     acc = renderer.backward(dLt, P)
     renderer.backward(dLt, P, grads=acc, accumulate=True)
+    # each gradient is a sum of float atomic additions whose order differs from run
+    # to run, so two runs agree to rounding relative to the field's scale
     for k in oracle.GRAD_FIELDS:
-        np.testing.assert_allclose(acc[k].cpu().numpy(), 2 * g["grads"][k], rtol=1e-5, atol=1e-7)
+        ref = 2 * g["grads"][k]
+        np.testing.assert_allclose(acc[k].cpu().numpy(), ref, rtol=1e-5,
+                                   atol=1e-6 * float(np.abs(ref).max()))
     # torch autograd through the hand-written backward
     leaves = [P[k].clone().requires_grad_(True) for k in oracle.GRAD_FIELDS]
     rgb = filtergs.render_differentiable(renderer, *leaves)
     np.testing.assert_array_equal(rgb.detach().cpu().numpy(), g["rgb"])
     (rgb * dLt).sum().backward()
     for k, leaf in zip(oracle.GRAD_FIELDS, leaves):
-        np.testing.assert_allclose(leaf.grad.cpu().numpy(), g["grads"][k], rtol=1e-5, atol=1e-7)
+        ref = g["grads"][k]
+        np.testing.assert_allclose(leaf.grad.cpu().numpy(), ref, rtol=1e-5,
+                                   atol=1e-6 * float(np.abs(ref).max()))
 
 
 def test_backward_state_and_argument_errors(renderer):
