@@ -70,6 +70,7 @@ struct fgs_ctx {
     uint32_t* sel = nullptr;
     float* splat = nullptr;
     unsigned long long* lb_compact = nullptr;
+    uint32_t* sel_cnt = nullptr;    // selected nodes per compaction tile (the Ancestor filter's counts)
     uint4* foot = nullptr;          // per selected Gaussian: rect, pair count, depth bits
     // pair-sized buffers
     uint64_t pair_cap = 0;
@@ -195,6 +196,7 @@ int ensure_nodes(fgs_ctx* c, size_t n_pad)
     if ((r = grow(c, (void**)&c->sel, n_pad * 4))) return r;
     if ((r = grow(c, (void**)&c->splat, n_pad * kSplatStride * 4))) return r;
     if ((r = grow(c, (void**)&c->lb_compact, (n_pad / 32 / kCompactWords + 2) * 8))) return r;
+    if ((r = grow(c, (void**)&c->sel_cnt, (n_pad / 32 / kCompactWords + 2) * 4))) return r;
     if ((r = grow(c, (void**)&c->foot, n_pad * sizeof(uint4)))) return r;
     c->node_cap = n_pad;
     return FGS_OK;
@@ -293,6 +295,9 @@ bool valid_camera(const fgs_camera* cam)
            cam->width >= 1 && cam->height >= 1 && cam->width <= 16384 && cam->height <= 16384;
 }
 
+// Compaction tiles of the loaded tree's selection bits.
+size_t n_sel_tiles(const fgs_ctx* c) { return (c->tree.n_pad / 32 + kCompactWords - 1) / kCompactWords; }
+
 int check_ready(fgs_ctx* c)
 {
     if (!c) return FGS_ERR_ARG;
@@ -309,12 +314,11 @@ int enqueue_front(fgs_ctx* c, const DevCamera& dc, cudaStream_t s, cudaEvent_t* 
 {
     const uint32_t tiles = (uint32_t)(dc.tiles_x * dc.tiles_y);
     if (ev) cudaEventRecord(ev[0], s);
-    launch_frame_begin(c->st, c->tile_cnt, (int)tiles, s);
+    launch_frame_begin(c->st, c->tile_cnt, (int)tiles, c->sel_cnt, (int)n_sel_tiles(c), s);
     launch_filter_pred(c->tree, dc, c->pbits, count ? c->st : nullptr, c->sms * c->occ_pred, s);
     if (ev) cudaEventRecord(ev[1], s);
-    launch_filter_anc(c->tree, c->pbits, c->selbits, c->sms * c->occ_anc, s);
-    launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->tree.n_pad, c->lb_compact, c->st,
-                   c->sms * c->occ_compact, s);
+    launch_filter_anc(c->tree, c->pbits, c->selbits, c->sel_cnt, c->sms * c->occ_anc, s);
+    launch_compact_counted(c->selbits, c->tree.n_pad / 32, c->sel, c->tree.n_pad, c->sel_cnt, c->st, s);
     if (ev) cudaEventRecord(ev[2], s);
     launch_project(c->tree, dc, c->sel, c->splat, c->foot, c->tile_cnt, c->st, c->sms * c->occ_proj, s);
     if (ev) cudaEventRecord(ev[3], s);
@@ -410,7 +414,7 @@ int fgs_destroy(fgs_ctx* c)
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
     void* bufs[] = {c->child_start, c->children, c->frontier0, c->frontier1, c->d_counter,
-                    c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->foot,
+                    c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->sel_cnt, c->foot,
                     c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->ranges, c->tile_cnt, c->large,
                     c->G, c->img, c->keep, c->st, c->gsplat};
     for (void* p : bufs) free_ptr(p);
@@ -697,11 +701,10 @@ int fgs_filter(fgs_ctx* c, void* stream, uint32_t* sel_out, uint32_t cap, uint32
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const DevCamera dc = make_devcam(c, false);
-    launch_frame_begin(c->st, c->tile_cnt, dc.tiles_x * dc.tiles_y, s);
+    launch_frame_begin(c->st, c->tile_cnt, dc.tiles_x * dc.tiles_y, c->sel_cnt, (int)n_sel_tiles(c), s);
     launch_filter_pred(c->tree, dc, c->pbits, nullptr, c->sms * c->occ_pred, s);
-    launch_filter_anc(c->tree, c->pbits, c->selbits, c->sms * c->occ_anc, s);
-    launch_compact(c->selbits, c->tree.n_pad / 32, c->sel, c->tree.n_pad, c->lb_compact, c->st,
-                   c->sms * c->occ_compact, s);
+    launch_filter_anc(c->tree, c->pbits, c->selbits, c->sel_cnt, c->sms * c->occ_anc, s);
+    launch_compact_counted(c->selbits, c->tree.n_pad / 32, c->sel, c->tree.n_pad, c->sel_cnt, c->st, s);
     FGS_CUDA(c, cudaGetLastError());
     c->have_frame = false;
     if (out_is_device) {
@@ -732,7 +735,7 @@ int fgs_filter_levelwise(fgs_ctx* c, void* stream, uint32_t* sel_out, uint32_t c
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const DevCamera dc = make_devcam(c, false);
-    launch_frame_begin(c->st, c->tile_cnt, dc.tiles_x * dc.tiles_y, s);
+    launch_frame_begin(c->st, c->tile_cnt, dc.tiles_x * dc.tiles_y, c->sel_cnt, (int)n_sel_tiles(c), s);
     FGS_CUDA(c, cudaMemsetAsync(c->selbits, 0, c->tree.n_pad / 32 * 4, s));
     c->h_counter[0] = c->root;
     FGS_CUDA(c, cudaMemcpyAsync(c->frontier0, c->h_counter, 4, cudaMemcpyHostToDevice, s));

@@ -332,11 +332,15 @@ int occ_segsort();
 
 // All launchers enqueue on `s` and read counts (M, N_P) from device memory,
 // so a frame needs no host synchronisation.
-void launch_frame_begin(FrameState* st, uint32_t* tile_cnt, int n_tiles, cudaStream_t s);
+// Zeroes the frame's counters: FrameState, the per-tile pair counts tile_cnt and
+// the per-compaction-tile selection counts sel_cnt.
+void launch_frame_begin(FrameState* st, uint32_t* tile_cnt, int n_tiles, uint32_t* sel_cnt, int n_sel_tiles,
+                        cudaStream_t s);
 void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits, FrameState* count_st, int blocks,
                         cudaStream_t s);
-void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, int blocks,
-                       cudaStream_t s);
+// Also adds each word's selected nodes to sel_cnt[word / kCompactWords].
+void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, uint32_t* sel_cnt,
+                       int blocks, cudaStream_t s);
 // Writes at most cap ids; more survivors latch FGS_ERR_CAPACITY and M = cap.
 // Failure-detection probe: one warp waits through warp_lookback on an entry of
 // lb that nothing publishes (a tag no frame uses), gives up after kProbeSpins
@@ -346,6 +350,9 @@ constexpr uint32_t kProbeSite = 0x7F0u;
 void launch_wait_probe(const unsigned long long* lb, FrameState* st, cudaStream_t s);
 void launch_compact(const uint32_t* selbits, uint32_t n_words, uint32_t* sel, uint32_t cap,
                     unsigned long long* lookback, FrameState* st, int blocks, cudaStream_t s);
+// The same result from the Ancestor filter's per-tile counts (one block a tile).
+void launch_compact_counted(const uint32_t* selbits, uint32_t n_words, uint32_t* sel, uint32_t cap,
+                            const uint32_t* sel_cnt, FrameState* st, cudaStream_t s);
 // Projection (splat records, footprints) and the per-tile pair counts
 // tile_cnt[tiles] (zeroed by launch_frame_begin).
 void launch_project(const DevTree& t, const DevCamera& cam, const uint32_t* sel, float* splat,

@@ -7,14 +7,20 @@
 //                     test alone).  Output: one bit per node.
 //  filter_anc         Ancestor filter: a node with P walks its ancestor path AP
 //                     (parent first, stopping at the first ancestor with P); one bit
-//                     per node for the survivors.
-//  compact            Stream compaction of the survivor bits into ascending node ids
-//                     (popcounts, block scan, decoupled look-back across tiles).
+//                     per node for the survivors, and the survivors of every
+//                     compaction tile counted.
+//  compact_counted    Stream compaction of the survivor bits into ascending node ids
+//                     (each tile's first slot from the counts of the tiles before
+//                     it, popcounts, block scan).
+//  compact            The same compaction without the counts (decoupled look-back
+//                     across tiles): the level-wise filter, the batched form and
+//                     the allocation-free entry point.
 #include "fgs_internal.cuh"
 
 namespace fgs {
 
-__global__ void frame_begin_kernel(FrameState* st, uint32_t* tile_cnt, int n_tiles)
+__global__ void frame_begin_kernel(FrameState* st, uint32_t* tile_cnt, int n_tiles, uint32_t* sel_cnt,
+                                   int n_sel_tiles)
 {
     grid_dep_wait();
     grid_dep_trigger();
@@ -33,13 +39,15 @@ __global__ void frame_begin_kernel(FrameState* st, uint32_t* tile_cnt, int n_til
     }
     if (tid < 16) st->tickets[tid] = 0;
     for (int i = tid; i < n_tiles; i += gridDim.x * blockDim.x) tile_cnt[i] = 0;
+    for (int i = tid; i < n_sel_tiles; i += gridDim.x * blockDim.x) sel_cnt[i] = 0;
 }
 
-void launch_frame_begin(FrameState* st, uint32_t* tile_cnt, int n_tiles, cudaStream_t s)
+void launch_frame_begin(FrameState* st, uint32_t* tile_cnt, int n_tiles, uint32_t* sel_cnt, int n_sel_tiles,
+                        cudaStream_t s)
 {
     int blocks = (n_tiles + 255) / 256;
     blocks = blocks < 8 ? 8 : blocks;
-    launch_pdl(frame_begin_kernel, blocks, 256, 0, s, st, tile_cnt, n_tiles);
+    launch_pdl(frame_begin_kernel, blocks, 256, 0, s, st, tile_cnt, n_tiles, sel_cnt, n_sel_tiles);
 }
 
 // ---------------------------------------------------------------------------
@@ -167,7 +175,8 @@ __device__ __forceinline__ bool ancestor_blocked16(const DevTree& t, const uint3
 }
 
 __global__ void __launch_bounds__(256) filter_anc_kernel(DevTree t, const uint32_t* __restrict__ pbits,
-                                                         uint32_t* __restrict__ selbits)
+                                                         uint32_t* __restrict__ selbits,
+                                                         uint32_t* __restrict__ sel_cnt)
 {
     __shared__ uint32_t s_pb[kAncCacheWords];
     grid_dep_wait();
@@ -187,19 +196,22 @@ __global__ void __launch_bounds__(256) filter_anc_kernel(DevTree t, const uint32
         bool keep = ((pw >> lane) & 1u) && n < t.n;
         if (keep) keep = !ancestor_blocked16(t, pbits, s_pb, cw, n);
         const uint32_t b = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) selbits[w] = b;
+        if (lane == 0) {
+            selbits[w] = b;
+            if (b) atomicAdd(sel_cnt + w / kCompactWords, (uint32_t)__popc(b));
+        }
         pw = pw_next;
     }
 }
 
-void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, int blocks,
-                       cudaStream_t s)
+void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, uint32_t* sel_cnt,
+                       int blocks, cudaStream_t s)
 {
     const uint32_t n_words = t.n_pad >> 5;
     int need = (int)((n_words * 32 + 255) / 256);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    launch_pdl(filter_anc_kernel, blocks, 256, 0, s, t, pbits, selbits);
+    launch_pdl(filter_anc_kernel, blocks, 256, 0, s, t, pbits, selbits, sel_cnt);
 }
 
 // Stream compaction of the selection bits into ascending node ids.  Tiles of
@@ -288,6 +300,93 @@ __global__ void __launch_bounds__(256) compact_kernel(const uint32_t* __restrict
         }
         __syncthreads();
     }
+}
+
+// Compaction of the frame's selection bits when the Ancestor filter has also
+// counted the selected nodes of every compaction tile (sel_cnt): one block per
+// tile takes its first slot as the sum of the counts of the tiles before it, so
+// no block waits on another (no look-back chain); then the popcounts, block scan
+// and warp-cooperative bit expansion of compact_kernel.
+__global__ void __launch_bounds__(256) compact_counted_kernel(const uint32_t* __restrict__ selbits,
+                                                              uint32_t n_words, uint32_t* __restrict__ sel,
+                                                              uint32_t cap, const uint32_t* __restrict__ sel_cnt,
+                                                              FrameState* st)
+{
+    __shared__ uint32_t s_warp_tot[8];
+    __shared__ uint32_t s_prefix;
+    grid_dep_wait();
+    grid_dep_trigger();
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t tile = blockIdx.x;
+    const uint32_t n_tiles = (n_words + kCompactWords - 1) / kCompactWords;
+    uint32_t part = 0;
+    for (uint32_t j = tid; j < tile; j += 256) part += sel_cnt[j];
+    part = warp_sum_u32(part);
+    if (lane == 0) s_warp_tot[warp] = part;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t p = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) p += s_warp_tot[w];
+        s_prefix = p;
+    }
+    __syncthreads();
+    const uint32_t prefix = s_prefix;
+    const uint32_t wbase = tile * kCompactWords + tid * 4;
+    uint4 wv = make_uint4(0, 0, 0, 0);
+    if (wbase + 3 < n_words) {
+        wv = *reinterpret_cast<const uint4*>(selbits + wbase);
+    } else {
+        if (wbase < n_words) wv.x = selbits[wbase];
+        if (wbase + 1 < n_words) wv.y = selbits[wbase + 1];
+        if (wbase + 2 < n_words) wv.z = selbits[wbase + 2];
+    }
+    const uint32_t c0 = __popc(wv.x), c1 = __popc(wv.y), c2 = __popc(wv.z), c3 = __popc(wv.w);
+    const uint32_t cnt = c0 + c1 + c2 + c3;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += u;
+    }
+    __syncthreads();                               // s_warp_tot reused
+    if (lane == 31) s_warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t off = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t tw = s_warp_tot[w];
+        off += (w < (int)warp) ? tw : 0u;
+        total += tw;
+    }
+    if (tid == 0 && tile == n_tiles - 1) {
+        // more survivors than slots: latch the error, keep M within the buffer
+        const uint32_t m_all = prefix + total;
+        if (m_all > cap) set_status(st, kErrCapacity, 0x120u);
+        st->M = m_all < cap ? m_all : cap;
+    }
+    // warp-cooperative expansion: the warp's 128 words in order, one bit per lane
+    const uint32_t p0 = prefix + off + incl - cnt;        // first slot of this lane's words
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t wbase_warp = tile * kCompactWords + warp * 128;
+    for (uint32_t q = 0; q < 128; ++q) {
+        const uint32_t owner = q >> 2, sub = q & 3;
+        const uint32_t mine = sub == 0 ? wv.x : sub == 1 ? wv.y : sub == 2 ? wv.z : wv.w;
+        const uint32_t before = sub == 0 ? 0u : sub == 1 ? c0 : sub == 2 ? c0 + c1 : c0 + c1 + c2;
+        const uint32_t wq = __shfl_sync(0xffffffffu, mine, owner);
+        if (wq == 0u) continue;
+        const uint32_t bq = __shfl_sync(0xffffffffu, p0 + before, owner);
+        const uint32_t pos = bq + __popc(wq & lt);
+        if (((wq >> lane) & 1u) && pos < cap) sel[pos] = ((wbase_warp + q) << 5) + lane;
+    }
+}
+
+void launch_compact_counted(const uint32_t* selbits, uint32_t n_words, uint32_t* sel, uint32_t cap,
+                            const uint32_t* sel_cnt, FrameState* st, cudaStream_t s)
+{
+    const int n_tiles = (int)((n_words + kCompactWords - 1) / kCompactWords);
+    launch_pdl(compact_counted_kernel, n_tiles < 1 ? 1 : n_tiles, 256, 0, s, selbits, n_words, sel, cap, sel_cnt,
+               st);
 }
 
 // One warp looks back from tile 1 at tile 0 with a tag whose low four bits
