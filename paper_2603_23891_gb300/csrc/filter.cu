@@ -144,12 +144,16 @@ void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits,
 // ---------------------------------------------------------------------------
 
 // Ancestor filter (§3.2): sel(n) = P(n) and no node of AP(n) has P.  One node per
-// lane, a warp per 32-node word of the bit arrays (grid-stride over words, the
-// next word's P bits prefetched).  A node with P reads up to 16 levels of its
-// ancestor path in one batch of independent loads, then the ancestors' P bits,
-// so a walk costs two dependent round trips for trees up to 16 levels deep.
-// The P bits of the lowest kAncCacheWords * 32 node ids sit in shared memory:
-// with level-major ids those are the upper levels every path crosses.
+// lane, a warp per 32-node word of the bit arrays; warp g takes words g, g + W,
+// g + 2W, ... (W warps in the grid), so the words of the frustum's id ranges spread
+// over every warp.  Lane i loads the P bits of the warp's i-th next word, so one
+// load brings 32 words' bits and a word without a P bit costs a ballot.  A node
+// with P reads up to 16 levels of its ancestor path in one batch of independent
+// loads, then the ancestors' P bits, so a walk costs two dependent round trips
+// for trees up to 16 levels deep.  The P bits of the lowest kAncCacheWords * 32
+// node ids sit in shared memory: with level-major ids those are the upper levels
+// every path crosses.  (Walking two words at a time, with their loads in flight
+// together, measured no faster: fewer warps fit.)
 __device__ __forceinline__ bool ancestor_blocked16(const DevTree& t, const uint32_t* __restrict__ pbits,
                                                    const uint32_t* s_pb, uint32_t cached_words,
                                                    uint32_t n)
@@ -187,20 +191,26 @@ __global__ void __launch_bounds__(256) filter_anc_kernel(DevTree t, const uint32
     for (uint32_t i = threadIdx.x; i < cw; i += blockDim.x) s_pb[i] = __ldg(pbits + i);
     __syncthreads();
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
-    uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    uint32_t pw = w < n_words ? __ldg(pbits + w) : 0u;
-    for (; w < n_words; w += n_warps) {
-        const uint32_t wn = w + n_warps;
-        const uint32_t pw_next = wn < n_words ? __ldg(pbits + wn) : 0u;
-        const uint32_t n = (w << 5) + lane;
-        bool keep = ((pw >> lane) & 1u) && n < t.n;
-        if (keep) keep = !ancestor_blocked16(t, pbits, s_pb, cw, n);
-        const uint32_t b = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) {
-            selbits[w] = b;
-            if (b) atomicAdd(sel_cnt + w / kCompactWords, (uint32_t)__popc(b));
+    for (uint32_t wb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wb < n_words; wb += 32u * n_warps) {
+        // this lane's word of the warp's next 32 (word indices stay below 2^32:
+        // n_words <= 2^26 and 32 W is below 2^21)
+        const uint32_t wl = wb + lane * n_warps;
+        const uint32_t pw_l = wl < n_words ? __ldg(pbits + wl) : 0u;
+        uint32_t act = __ballot_sync(0xffffffffu, pw_l != 0u);
+        uint32_t res = 0;
+        while (act) {
+            const uint32_t i = (uint32_t)__ffs(act) - 1u;
+            act &= act - 1u;
+            const uint32_t pw = __shfl_sync(0xffffffffu, pw_l, i);
+            const uint32_t w = wb + i * n_warps;
+            const uint32_t n = (w << 5) + lane;
+            bool keep = ((pw >> lane) & 1u) && n < t.n;
+            if (keep) keep = !ancestor_blocked16(t, pbits, s_pb, cw, n);
+            const uint32_t b = __ballot_sync(0xffffffffu, keep);
+            if (lane == i) res = b;
+            if (lane == 0 && b) atomicAdd(sel_cnt + w / kCompactWords, (uint32_t)__popc(b));
         }
-        pw = pw_next;
+        if (wl < n_words) selbits[wl] = res;
     }
 }
 

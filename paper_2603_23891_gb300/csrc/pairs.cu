@@ -289,14 +289,62 @@ __device__ __forceinline__ void block_or_and(unsigned long long vor, unsigned lo
     __syncthreads();
 }
 
+// Equal depths found after a depth-only sort: the run of equal keys starting at
+// i (keys[i - 1] differs, keys[i + 1] is equal) is put in rank order by
+// insertion sort of its values, if it is at most kTieRun long; returns false,
+// changing nothing, for a longer run.  Only this thread writes the run, and the
+// keys (which other threads read) do not change.
+constexpr uint32_t kTieRun = 32;
+__device__ __forceinline__ bool sort_tie_run(const uint32_t* keys, uint32_t* vals, uint32_t i, uint32_t n)
+{
+    uint32_t j = i + 1;
+    while (j < n && keys[j] == keys[i]) {
+        if (j - i >= kTieRun) return false;
+        ++j;
+    }
+    for (uint32_t a = i + 1; a < j; ++a) {
+        const uint32_t x = vals[a];
+        uint32_t b = a;
+        while (b > i && vals[b - 1] > x) {
+            vals[b] = vals[b - 1];
+            --b;
+        }
+        vals[b] = x;
+    }
+    return true;
+}
+
+// The same for 64-bit items (depth bits << 32 | rank): a run of equal depths
+// sorted by item is sorted by rank.
+__device__ __forceinline__ bool sort_tie_run64(unsigned long long* items, uint32_t i, uint32_t n)
+{
+    const uint32_t d = (uint32_t)(items[i] >> 32);
+    uint32_t j = i + 1;
+    while (j < n && (uint32_t)(items[j] >> 32) == d) {
+        if (j - i >= kTieRun) return false;
+        ++j;
+    }
+    for (uint32_t a = i + 1; a < j; ++a) {
+        const unsigned long long x = items[a];
+        uint32_t b = a;
+        while (b > i && items[b - 1] > x) {
+            items[b] = items[b - 1];
+            --b;
+        }
+        items[b] = x;
+    }
+    return true;
+}
+
 // A block sorts n <= 256 I items of one tile by depth with a stable LSD radix
 // sort over the depth bytes in which the items differ, items held in registers
 // and exchanged through shared memory (skeys / svals) after every pass.  Item i
 // of the input order is item it, lane L of warp w with i = (w I + it) 32 + L.
-// Equal depths keep that order, which is the scatter's and not the rank order:
-// if two depths are equal, false is returned and nothing is written (the caller
-// sorts the bucket by (depth, rank) instead); otherwise the sorted pairs are
-// written and true is returned.
+// Equal depths keep that order, which is the scatter's and not the rank order,
+// so each run of equal depths is then put in rank order where it lies (by the
+// thread holding its first element).  If a run is longer than kTieRun, false is
+// returned and nothing is written (the caller sorts the bucket by (depth, rank)
+// instead); otherwise the sorted pairs are written and true is returned.
 template <int I>
 __device__ bool block_radix_bucket(const unsigned long long* items, uint32_t n, uint32_t tile,
                                    unsigned long long* keys_out, uint32_t* vals_out, uint32_t* skeys,
@@ -345,55 +393,47 @@ __device__ bool block_radix_bucket(const unsigned long long* items, uint32_t n, 
         }
         __syncthreads();
     }
-    // ties: two equal depths next to each other in the sorted order
-    bool tie = false;
-#pragma unroll
-    for (int it = 0; it < I; ++it) {
-        const uint32_t i = (warp * I + it) * 32 + lane;
-        if (i < n) skeys[i] = key[it];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < I; ++it) {
-        const uint32_t i = (warp * I + it) * 32 + lane;
-        if (i > 0 && i < n && skeys[i] == skeys[i - 1]) tie = true;
-    }
-    if (__syncthreads_or(tie)) return false;
+    // the depth order into shared memory, then each run of equal depths in rank order
 #pragma unroll
     for (int it = 0; it < I; ++it) {
         const uint32_t i = (warp * I + it) * 32 + lane;
         if (i < n) {
-            keys_out[i] = ((unsigned long long)tile << 32) | key[it];
-            vals_out[i] = val[it];
+            skeys[i] = key[it];
+            svals[i] = val[it];
         }
+    }
+    __syncthreads();
+    bool long_run = false;
+    for (uint32_t i = tid; i + 1 < n; i += kSegThreads) {
+        if (skeys[i + 1] == skeys[i] && (i == 0 || skeys[i - 1] != skeys[i]))
+            long_run |= !sort_tie_run(skeys, svals, i, n);
+    }
+    if (__syncthreads_or(long_run)) return false;
+    for (uint32_t i = tid; i < n; i += kSegThreads) {
+        keys_out[i] = ((unsigned long long)tile << 32) | skeys[i];
+        vals_out[i] = svals[i];
     }
     __syncthreads();
     return true;
 }
 
-// A block sorts a bucket of any size by (depth, rank): a stable LSD radix sort
-// over every byte of the 64-bit items in which they differ (rank bytes first,
-// so equal depths end in rank order), each pass a histogram sweep and a
+// A block sorts a bucket of any size by (depth, rank) with stable LSD radix
+// passes over bytes of the 64-bit items, each pass a histogram sweep and a
 // scatter sweep over chunks of 256 I items, between the bucket (a) and the
-// tile's slots of the key output (b) as scratch.  The sorted pairs are
-// written to keys_out (which is b) and vals_out.
+// tile's slots of the key output (b) as scratch.  First only the depth bytes in
+// which the items differ: equal depths then keep the scatter's order, so each
+// run of equal depths is put in rank order where it lies; if a run is longer
+// than kTieRun the sort is repeated over every byte in which the items differ
+// (rank bytes first, so equal depths end in rank order; the input order does
+// not matter, (depth, rank) being unique).  The sorted pairs are written
+// to keys_out (which is b) and vals_out.
 constexpr int kRadixGlobalItems = 8;
-__device__ void block_radix_global(unsigned long long* a, unsigned long long* b, uint32_t n, uint32_t tile,
-                                   unsigned long long* keys_out, uint32_t* vals_out, RadixSmem& R)
+__device__ void radix_global_passes(unsigned long long*& src, unsigned long long*& dst, uint32_t n,
+                                    unsigned long long diff, RadixSmem& R)
 {
     constexpr int I = kRadixGlobalItems;
     constexpr uint32_t kChunk = 256u * I;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    unsigned long long vor = 0ull, vand = ~0ull;
-    for (uint32_t i = tid; i < n; i += kSegThreads) {
-        const unsigned long long x = a[i];
-        vor |= x;
-        vand &= x;
-    }
-    block_or_and(vor, vand, R);
-    const unsigned long long diff = R.vor & ~R.vand;
-    unsigned long long* src = a;
-    unsigned long long* dst = b;
     for (uint32_t shift = 0; shift < 64; shift += 8) {
         if (((diff >> shift) & 0xFFull) == 0ull) continue;
         // histogram of the digit over the bucket, then each digit's first slot
@@ -437,6 +477,32 @@ __device__ void block_radix_global(unsigned long long* a, unsigned long long* b,
         src = dst;
         dst = t;
     }
+}
+
+__device__ void block_radix_global(unsigned long long* a, unsigned long long* b, uint32_t n, uint32_t tile,
+                                   unsigned long long* keys_out, uint32_t* vals_out, RadixSmem& R)
+{
+    const uint32_t tid = threadIdx.x;
+    unsigned long long vor = 0ull, vand = ~0ull;
+    for (uint32_t i = tid; i < n; i += kSegThreads) {
+        const unsigned long long x = a[i];
+        vor |= x;
+        vand &= x;
+    }
+    block_or_and(vor, vand, R);
+    const unsigned long long diff = R.vor & ~R.vand;
+    unsigned long long* src = a;
+    unsigned long long* dst = b;
+    radix_global_passes(src, dst, n, diff & 0xFFFFFFFF00000000ull, R);
+    // each run of equal depths in rank order where it lies; a run longer than
+    // kTieRun: the full sort instead
+    bool long_run = false;
+    for (uint32_t i = tid; i + 1 < n; i += kSegThreads) {
+        const uint32_t d = (uint32_t)(src[i] >> 32);
+        if ((uint32_t)(src[i + 1] >> 32) == d && (i == 0 || (uint32_t)(src[i - 1] >> 32) != d))
+            long_run |= !sort_tie_run64(src, i, n);
+    }
+    if (__syncthreads_or(long_run)) radix_global_passes(src, dst, n, diff, R);
     // src holds the sorted items; a slot of keys_out (= b) is read and then
     // rewritten by the same thread
     for (uint32_t i = tid; i < n; i += kSegThreads) put_pair(src[i], tile, keys_out, vals_out, i);
@@ -535,7 +601,62 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(uint32_t* __res
 // indexes entries view * n_pad + node, and a pair's tile is its view's first
 // tile plus the tile in the view) goes to its tile's bucket as
 // depth bits << 32 | m.  Slots at or beyond cap are not written (the scan has
-// latched FGS_ERR_CAPACITY).
+// latched FGS_ERR_CAPACITY).  A Gaussian with more than kBigPairs pairs is
+// scattered by the whole block after its group.
+// One warp's Gaussians (lane L: pair count cnt, footprint f, its view's grid
+// width and first tile, rank m) into their tiles' buckets, kScatterRounds rounds
+// at a time so that their cursor increments are in flight together; one
+// increment per tile and round, the group's lanes taking consecutive slots
+// after the returned base.
+__device__ __forceinline__ void scatter_warp(uint32_t cnt, const uint4& f, uint32_t tiles_x, uint32_t tbase,
+                                             uint32_t m, uint32_t* __restrict__ cursor,
+                                             unsigned long long* __restrict__ items, unsigned long long cap)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const WarpPairs wp(cnt, f.x, f.y, tiles_x, tbase, f.w, m);
+    for (uint32_t q0 = 0; q0 < wp.wtot; q0 += 32 * kScatterRounds) {
+        uint32_t tile[kScatterRounds], d[kScatterRounds], mm[kScatterRounds], grp[kScatterRounds],
+            base[kScatterRounds];
+#pragma unroll
+        for (int r = 0; r < kScatterRounds; ++r) {
+            const bool valid = wp.get(q0 + 32 * r, tile[r], d[r], mm[r]);
+            grp[r] = tile_group(valid, tile[r]);
+            base[r] = 0;
+            if (grp[r] && lane == (uint32_t)(__ffs(grp[r]) - 1))
+                base[r] = atomicAdd(cursor + tile[r], (uint32_t)__popc(grp[r]));
+        }
+#pragma unroll
+        for (int r = 0; r < kScatterRounds; ++r) {
+            const uint32_t leader = grp[r] ? (uint32_t)(__ffs(grp[r]) - 1) : lane;
+            const uint32_t b = __shfl_sync(0xffffffffu, base[r], leader);
+            if (grp[r]) {
+                const uint32_t pos = b + (uint32_t)__popc(grp[r] & ((1u << lane) - 1u));
+                if (pos < cap) items[pos] = ((unsigned long long)d[r] << 32) | mm[r];
+            }
+        }
+    }
+}
+
+// The pairs of one set-aside Gaussian (rank m, footprint f) by the whole block,
+// kScatterRounds slots a thread in flight.
+__device__ __forceinline__ void scatter_block(const uint4& f, uint32_t m, uint32_t tiles_x, uint32_t tbase,
+                                              uint32_t* __restrict__ cursor,
+                                              unsigned long long* __restrict__ items, unsigned long long cap)
+{
+    const unsigned long long item = ((unsigned long long)f.w << 32) | m;
+    for (uint32_t k0 = 0; k0 < f.z; k0 += kScatterRounds * kProjThreads) {
+        uint32_t pos[kScatterRounds];
+#pragma unroll
+        for (int r = 0; r < kScatterRounds; ++r) {
+            const uint32_t k = k0 + r * kProjThreads + threadIdx.x;
+            pos[r] = k < f.z ? atomicAdd(cursor + rect_tile(f, k, tiles_x, tbase), 1u) : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int r = 0; r < kScatterRounds; ++r)
+            if (pos[r] != 0xFFFFFFFFu && pos[r] < cap) items[pos[r]] = item;
+    }
+}
+
 template <bool kBatch>
 __global__ void __launch_bounds__(kProjThreads) scatter_kernel(
     DevCamera cam, const DevCamera* __restrict__ cams, const uint32_t* __restrict__ tile_base,
@@ -543,8 +664,10 @@ __global__ void __launch_bounds__(kProjThreads) scatter_kernel(
     uint32_t* __restrict__ cursor, unsigned long long* __restrict__ items, unsigned long long cap,
     FrameState* st)
 {
+    __shared__ BigPairs s_big;
     grid_dep_wait();
     grid_dep_trigger();
+    big_pairs_init(s_big);
     const uint32_t M = st->M;
     const uint32_t n_groups = (M + kProjThreads - 1) / kProjThreads;
     for (uint32_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
@@ -561,33 +684,14 @@ __global__ void __launch_bounds__(kProjThreads) scatter_kernel(
                 tiles_x = (uint32_t)cam.tiles_x;
             }
         }
-        if (__ballot_sync(0xffffffffu, f.z != 0) == 0u) continue;
-        const uint32_t lane = threadIdx.x & 31;
-        const WarpPairs wp(f.z, f.x, f.y, tiles_x, tbase, f.w, m);
-        // kScatterRounds rounds at a time, so that their cursor increments are in
-        // flight together; one increment per tile and round, the group's lanes
-        // taking consecutive slots after the returned base
-        for (uint32_t q0 = 0; q0 < wp.wtot; q0 += 32 * kScatterRounds) {
-            uint32_t tile[kScatterRounds], d[kScatterRounds], mm[kScatterRounds], grp[kScatterRounds],
-                base[kScatterRounds];
-#pragma unroll
-            for (int r = 0; r < kScatterRounds; ++r) {
-                const bool valid = wp.get(q0 + 32 * r, tile[r], d[r], mm[r]);
-                grp[r] = tile_group(valid, tile[r]);
-                base[r] = 0;
-                if (grp[r] && lane == (uint32_t)(__ffs(grp[r]) - 1))
-                    base[r] = atomicAdd(cursor + tile[r], (uint32_t)__popc(grp[r]));
-            }
-#pragma unroll
-            for (int r = 0; r < kScatterRounds; ++r) {
-                const uint32_t leader = grp[r] ? (uint32_t)(__ffs(grp[r]) - 1) : lane;
-                const uint32_t b = __shfl_sync(0xffffffffu, base[r], leader);
-                if (grp[r]) {
-                    const uint32_t pos = b + (uint32_t)__popc(grp[r] & ((1u << lane) - 1u));
-                    if (pos < cap) items[pos] = ((unsigned long long)d[r] << 32) | mm[r];
-                }
-            }
-        }
+        const uint32_t cnt = big_pairs_defer(s_big, f.z, m, tiles_x, tbase);
+        if (__ballot_sync(0xffffffffu, cnt != 0) != 0u) scatter_warp(cnt, f, tiles_x, tbase, m, cursor, items, cap);
+        const uint32_t nb = big_pairs_take(s_big);
+        if (nb == 0u) continue;
+        for (uint32_t b = 0; b < nb; ++b)
+            scatter_block(__ldg(foot + s_big.m[b]), s_big.m[b], s_big.tiles_x[b], s_big.tile_base[b], cursor,
+                          items, cap);
+        big_pairs_done(s_big);
     }
 }
 

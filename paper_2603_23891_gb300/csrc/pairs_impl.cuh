@@ -88,4 +88,77 @@ __device__ __forceinline__ void warp_count_pairs(uint32_t cnt, uint32_t rect_x, 
     }
 }
 
+// A Gaussian with more than kBigPairs pairs (a near, wide footprint) would keep
+// its warp walking hundreds of rounds alone while the rest of the grid has
+// finished, so it is set aside in a block-local list and its pairs are
+// enumerated by the whole block after the group of kProjThreads Gaussians it
+// belongs to (a group sets aside at most kProjThreads, so the list never fills).
+constexpr uint32_t kBigPairs = 128;
+constexpr uint32_t kBigList = kProjThreads;
+
+struct BigPairs {
+    uint32_t n;                     // Gaussians set aside
+    uint32_t m[kBigList];           // their ranks
+    uint32_t tiles_x[kBigList];     // their view's tile-grid width
+    uint32_t tile_base[kBigList];   // their view's first tile id
+};
+
+__device__ __forceinline__ void big_pairs_init(BigPairs& L)
+{
+    if (threadIdx.x == 0) L.n = 0;
+    __syncthreads();
+}
+
+// The pair count this lane's warp enumerates: 0 for a Gaussian set aside.
+__device__ __forceinline__ uint32_t big_pairs_defer(BigPairs& L, uint32_t cnt, uint32_t m, uint32_t tiles_x,
+                                                    uint32_t tile_base)
+{
+    if (cnt <= kBigPairs) return cnt;
+    const uint32_t slot = atomicAdd(&L.n, 1u);
+    L.m[slot] = m;
+    L.tiles_x[slot] = tiles_x;
+    L.tile_base[slot] = tile_base;
+    return 0u;
+}
+
+// After a group (all threads call it): how many Gaussians the group set aside.
+// Every thread has read the count before any thread sets one aside again.
+__device__ __forceinline__ uint32_t big_pairs_take(const BigPairs& L)
+{
+    __syncthreads();
+    const uint32_t nb = L.n;
+    __syncthreads();
+    return nb;
+}
+
+// After the set-aside Gaussians of a group are enumerated (all threads call
+// it, only when big_pairs_take returned a nonzero count): empty the list.
+__device__ __forceinline__ void big_pairs_done(BigPairs& L)
+{
+    if (threadIdx.x == 0) L.n = 0;
+    __syncthreads();
+}
+
+// Tile of pair k of footprint f (row-major in its rectangle).
+__device__ __forceinline__ uint32_t rect_tile(const uint4& f, uint32_t k, uint32_t tiles_x, uint32_t tile_base)
+{
+    const uint32_t x0 = f.x & 0xFFFFu, rw = (f.x >> 16) - x0;
+    const uint32_t y0 = f.y & 0xFFFFu;
+    return tile_base + (y0 + k / rw) * tiles_x + (x0 + k % rw);
+}
+
+// The projection's end of a group: count the pairs of its set-aside Gaussians
+// into tile_cnt (foot holds their footprint records).  All threads call it.
+__device__ __forceinline__ void big_pairs_count(BigPairs& L, const uint4* foot, uint32_t* tile_cnt)
+{
+    const uint32_t nb = big_pairs_take(L);
+    if (nb == 0u) return;
+    for (uint32_t b = 0; b < nb; ++b) {
+        const uint4 f = foot[L.m[b]];
+        for (uint32_t k = threadIdx.x; k < f.z; k += blockDim.x)
+            atomicAdd(tile_cnt + rect_tile(f, k, L.tiles_x[b], L.tile_base[b]), 1u);
+    }
+    big_pairs_done(L);
+}
+
 }  // namespace fgs

@@ -160,6 +160,41 @@ def test_gaussian_covering_whole_screen(renderer):
     assert g["NP"] >= tiles
 
 
+def test_wide_footprints(renderer):
+    """Gaussians whose footprints cover more than 128 tiles (up to the whole 640x360
+    screen) among small ones: their pairs are counted and scattered by the whole block
+    after their group of 256 Gaussians instead of by their warp.  Ranks 0-299 are all
+    wide (a group of 256 wide ones, then a partial group), every fifth rank beyond;
+    pairs, splats and image against the oracle, with and without shrinking."""
+    W, H = 640, 360
+    cam = synth.look_at_camera([0.0, 0.0, 0.0], [0.0, 1.0, 0.0], W, H, 60.0)
+    R = np.asarray(cam.R, np.float64).reshape(3, 3)
+    t = np.asarray(cam.t, np.float64)
+    rng = np.random.default_rng(23)
+    n = 1400
+    u = rng.uniform(0.0, W, n)
+    v = rng.uniform(0.0, H, n)
+    z = rng.uniform(8.0, 30.0, n)
+    xc = (u - cam.cx) * z / cam.fx
+    yc = (v - cam.cy) * z / cam.fy
+    mu = (np.stack([xc, yc, z], 1) - t) @ R
+    rank = np.empty(n, np.int64)                  # the leaves' selection ranks (Morton order)
+    rank[np.argsort(synth.morton_codes(mu), kind="stable")] = np.arange(n)
+    wide = (rank < 300) | (rank % 5 == 0)
+    sigma_px = np.where(wide, rng.uniform(50.0, 120.0, n), rng.uniform(0.5, 3.0, n))
+    log_s = np.log(sigma_px * z / cam.fx)
+    tree = synth.tree_from_gaussians(mu, np.repeat(log_s[:, None], 3, 1), np.tile([1.0, 0, 0, 0], (n, 1)),
+                                     np.where(wide, rng.normal(2.0, 0.5, n), rng.normal(-1.0, 1.0, n)),
+                                     rng.normal(0, 1, (n, 1, 3)), 0)
+    renderer.load_tree(tree)
+    for shrink in (None, (0.05, float(np.float32(np.log(np.float32(0.05)))))):
+        g = gpu_frame(renderer, tree, cam, -1.0, shrink=shrink)
+        o, _ = oracle_frame(tree, cam, -1.0, shrink=shrink)
+        per_g = np.bincount(o.vals.astype(np.int64), minlength=len(o.sel))
+        assert (per_g[:256] > 128).sum() >= 200 and per_g.max() > 400, np.sort(per_g)[-5:]
+        assert_frame_parity(g, o)
+
+
 def test_depth_ties_break_by_id(renderer):
     """Duplicated Gaussians at one depth: equal keys keep ascending selection order."""
     mu = np.array([[0.0, 10.0, 0.0]] * 6 + [[0.3, 10.0, 0.2]] * 3)
@@ -402,15 +437,18 @@ def test_tile_grid_limit_rejected(renderer):
     assert_frame_parity(g, o)
 
 
-@pytest.mark.parametrize("ties", [True, False])
+@pytest.mark.parametrize("ties", ["none", "short", "long"])
 def test_bucket_sizes_at_sort_boundaries(renderer, ties):
     """One row of 16x16 tiles whose tiles hold exactly 0, 1, 2, 32, 33, 64, 65, 128, 129,
     256, 257, 511, 512, 513, 1024, 1025, 2048, 2049, 4096 and 4097 pairs (each Gaussian a
     few pixels wide, inside one tile): every size class of the per-tile sort (one warp
-    with 1, 2, 4 or 8 items a lane; one block by radix with 2, 4 or 8 items a thread;
-    one block by bitonic network in shared or global memory) and its edges, with and
-    without depth ties inside the buckets (a tie sends a radix-sorted bucket to the
-    network); pairs, splats and image against the oracle."""
+    with 1, 2, 4 or 8 items a lane; one block by depth radix in shared memory with 2, 4
+    or 8 items a thread; one block by radix passes in global memory) and its edges,
+    without depth ties, with short runs of equal depths inside the buckets (put in rank
+    order where they lie after the depth sort) and with one run of 40 equal depths per
+    bucket (longer than the in-place fix takes: the bitonic network in shared memory,
+    or the full radix passes in global memory); pairs, splats and image against the
+    oracle."""
     counts = [1, 32, 33, 64, 65, 128, 129, 256, 257, 511, 512, 513, 1024, 1025, 2048, 2049, 4096,
               4097, 0, 2]
     W, H = 16 * len(counts), 16
@@ -422,10 +460,12 @@ def test_bucket_sizes_at_sort_boundaries(renderer, ties):
     for i, c in enumerate(counts):
         u = 16 * i + rng.uniform(3.5, 12.5, c)
         v = rng.uniform(3.5, 12.5, c)
-        if ties:                                                     # repeated depths
+        if ties == "short":                                          # repeated depths
             z = rng.choice(rng.uniform(5.0, 40.0, max(c // 3, 1)), c)
         else:                                                        # distinct depths
             z = rng.permutation(5.0 + np.arange(c) * (35.0 / max(c, 1)))
+            if ties == "long" and c >= 80:                           # one run of 40
+                z[rng.choice(c, 40, replace=False)] = z[0]
         xc = (u - cam.cx) * z / cam.fx
         yc = (v - cam.cy) * z / cam.fy
         cpts = np.stack([xc, yc, z], 1)
@@ -440,5 +480,5 @@ def test_bucket_sizes_at_sort_boundaries(renderer, ties):
     per_tile = np.bincount((o.keys >> np.uint64(32)).astype(np.int64), minlength=len(counts))
     assert np.array_equal(per_tile, counts), per_tile
     depth_tie = (o.keys[1:] == o.keys[:-1])
-    assert depth_tie.any() == ties
+    assert depth_tie.any() == (ties != "none")
     assert_frame_parity(g, o)
