@@ -66,6 +66,11 @@ extern "C" {
 #define FGS_RENDER_KEEP 16u        /* keep per-pixel final T and stop position (8 bytes a pixel,
                                       context-owned) so that fgs_backward need not recompute
                                       them; ignored with COUNT */
+#define FGS_RENDER_ASYNC 32u       /* host outputs without waiting: the image is copied to the
+                                      host buffers on a context-owned copy stream while the
+                                      caller's stream goes on with the next frame (two frames in
+                                      flight, two context-owned device images); the buffers hold
+                                      the frame once fgs_sync returns; not with STATS / COUNT */
 
 #define FGS_N_STAGES 7             /* filter R&L, ancestor filter + compaction, projection + per-tile
                                       pair counts, tile ranges, key scatter, per-tile sort, blend */
@@ -218,7 +223,13 @@ int fgs_filter_levelwise(fgs_ctx* ctx, void* stream, uint32_t* sel_out, uint32_t
  * each bucket, blend.  rgb_out: float [3][H][W] planar colour
  * C + T * bg; T_out: float [H][W] final transmittance (may be NULL).
  * out_is_device selects device (asynchronous) or host (synchronising)
- * outputs.  flags: FGS_RENDER_STATS fills st->n_selected / n_pairs /
+ * outputs; with FGS_RENDER_ASYNC host outputs do not synchronise either: the
+ * call returns once the frame and its copy are enqueued, the copy (a pinned
+ * host buffer lets it overlap the next frame's kernels) runs on the context's
+ * copy stream, latched device errors are reported by fgs_sync, and the host
+ * buffers must not be read or reused before fgs_sync returns.  The third
+ * pipelined frame's blend waits on the device for the first one's copy.
+ * flags: FGS_RENDER_STATS fills st->n_selected / n_pairs /
  * device_status (synchronising); FGS_RENDER_STAGE_EVENTS records stage events
  * into the next slot of a 256-slot ring (see fgs_stage_times).  st may be
  * NULL.  Errors: FGS_ERR_STATE (no tree or camera), FGS_ERR_ARG,

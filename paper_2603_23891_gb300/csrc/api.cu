@@ -89,6 +89,16 @@ struct fgs_ctx {
     size_t img_cap = 0;
     float* img = nullptr;
     uint2* keep = nullptr;          // per pixel: final T bits, stop position (for the backward)
+    // pipelined host outputs (FGS_RENDER_ASYNC): two device images, each frame's
+    // copy to the host on copy_stream; ev_blend[i] marks image i written,
+    // ev_copied[i] its copy done (the frame after next waits for it)
+    size_t ring_cap = 0;
+    float* ring[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_blend[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    bool ring_busy[2] = {false, false};
+    int ring_next = 0;
     // frame state
     FrameState* st = nullptr;
     FrameState* st_host = nullptr;
@@ -199,6 +209,29 @@ int ensure_nodes(fgs_ctx* c, size_t n_pad)
     if ((r = grow(c, (void**)&c->sel_cnt, (n_pad / 32 / kCompactWords + 2) * 4))) return r;
     if ((r = grow(c, (void**)&c->foot, n_pad * sizeof(uint4)))) return r;
     c->node_cap = n_pad;
+    return FGS_OK;
+}
+
+// The two device images of pipelined host outputs (rgb planes + T, `pixels`
+// each), the copy stream and its events, created on first use.  Growing the
+// images first waits for the copies that read them.
+int ensure_ring(fgs_ctx* c, size_t pixels)
+{
+    int r;
+    if (!c->copy_stream) {
+        FGS_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            FGS_CUDA(c, cudaEventCreateWithFlags(&c->ev_blend[i], cudaEventDisableTiming));
+            FGS_CUDA(c, cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming));
+        }
+    }
+    if (pixels > c->ring_cap) {
+        FGS_CUDA(c, cudaStreamSynchronize(c->copy_stream));
+        for (int i = 0; i < 2; ++i)
+            if ((r = grow(c, (void**)&c->ring[i], pixels * 4 * 4))) return r;
+        c->ring_busy[0] = c->ring_busy[1] = false;
+        c->ring_cap = pixels;
+    }
     return FGS_OK;
 }
 
@@ -418,6 +451,12 @@ int fgs_destroy(fgs_ctx* c)
                     c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->ranges, c->tile_cnt, c->large,
                     c->G, c->img, c->keep, c->st, c->gsplat};
     for (void* p : bufs) free_ptr(p);
+    for (float* p : c->ring) free_ptr(p);
+    for (int i = 0; i < 2; ++i) {
+        if (c->ev_blend[i]) cudaEventDestroy(c->ev_blend[i]);
+        if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     {
         auto& b = c->batch;
         void* bb[] = {b.d_cams, b.d_tile_base, b.d_img_off, b.pbits, b.selbits, b.sel, b.splat,
@@ -796,12 +835,23 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
         ++c->ev_count;
     }
     const bool count = (flags & FGS_RENDER_COUNT) != 0;
-    int launches = enqueue_front(c, dc, s, ev, count);
+    const bool pipelined = !out_is_device && (flags & FGS_RENDER_ASYNC);
     const size_t hw = (size_t)dc.width * dc.height;
-    float* rgb_dst = out_is_device ? rgb_out : c->img;
-    float* T_dst = out_is_device ? T_out : (T_out ? c->img + 3 * hw : nullptr);
+    int slot = 0;
+    if (pipelined) {
+        if (flags & (FGS_RENDER_STATS | FGS_RENDER_COUNT))
+            return fail(c, FGS_ERR_ARG, "FGS_RENDER_ASYNC does not combine with STATS or COUNT");
+        if ((r = ensure_ring(c, hw))) return r;
+        slot = c->ring_next;
+    }
+    int launches = enqueue_front(c, dc, s, ev, count);
+    float* const img = pipelined ? c->ring[slot] : c->img;
+    float* rgb_dst = out_is_device ? rgb_out : img;
+    float* T_dst = out_is_device ? T_out : (T_out ? img + 3 * hw : nullptr);
     const bool keep = (flags & FGS_RENDER_KEEP) && !count;
     if (count) flags |= FGS_RENDER_STATS;
+    // the image two frames back must have reached the host before it is overwritten
+    if (pipelined && c->ring_busy[slot]) FGS_CUDA(c, cudaStreamWaitEvent(s, c->ev_copied[slot], 0));
     launch_blend(dc, c->ranges, c->vals1, c->splat, rgb_dst, T_dst, keep ? c->keep : nullptr, c->st, count, s);
     ++launches;
     if (ev) cudaEventRecord(ev[kStages], s);
@@ -809,6 +859,22 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
     c->have_frame = true;
     c->frame_rendered = true;
     c->frame_kept = keep;
+    if (pipelined) {
+        // the copy runs on copy_stream while the caller's stream renders the next frame
+        FGS_CUDA(c, cudaEventRecord(c->ev_blend[slot], s));
+        FGS_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_blend[slot], 0));
+        FGS_CUDA(c, cudaMemcpyAsync(rgb_out, img, 3 * hw * 4, cudaMemcpyDeviceToHost, c->copy_stream));
+        if (T_out)
+            FGS_CUDA(c, cudaMemcpyAsync(T_out, img + 3 * hw, hw * 4, cudaMemcpyDeviceToHost, c->copy_stream));
+        FGS_CUDA(c, cudaEventRecord(c->ev_copied[slot], c->copy_stream));
+        c->ring_busy[slot] = true;
+        c->ring_next = slot ^ 1;
+        if (st) {
+            std::memset(st, 0, sizeof *st);
+            st->n_launches = (uint32_t)launches;
+        }
+        return FGS_OK;
+    }
     if (!out_is_device) {
         FGS_CUDA(c, cudaMemcpyAsync(rgb_out, c->img, 3 * hw * 4, cudaMemcpyDeviceToHost, s));
         if (T_out) FGS_CUDA(c, cudaMemcpyAsync(T_out, c->img + 3 * hw, hw * 4, cudaMemcpyDeviceToHost, s));
@@ -1322,6 +1388,7 @@ int fgs_sync(fgs_ctx* c, void* stream)
     r = latched_status(c);
     if (r) clear_status(c, s);
     FGS_CUDA(c, cudaStreamSynchronize(s));
+    if (c->copy_stream) FGS_CUDA(c, cudaStreamSynchronize(c->copy_stream));   // pipelined host copies
     return r;
 }
 

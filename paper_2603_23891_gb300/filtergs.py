@@ -32,6 +32,7 @@ FGS_RENDER_COUNT = 8
 FGS_N_STAGES = 7
 FGS_BATCH_GRAPH = 4
 FGS_RENDER_KEEP = 16
+FGS_RENDER_ASYNC = 32
 STAGE_NAMES = ["filter_rl", "ancestor_compact", "project", "tile_ranges", "keys", "sort", "blend"]
 SPLAT_FIELDS = ["u", "v", "A", "B", "C", "lthr", "a0", "depth", "r", "g", "b", "radius"]
 
@@ -493,9 +494,12 @@ class Renderer:
         fgs_render(self.ctx, self.stream, rgb, T, 1, flags, st)
         return rgb, T, st
 
-    def render_host(self, rgb_host: np.ndarray, T_host=None, stats=False):
+    def render_host(self, rgb_host: np.ndarray, T_host=None, stats=False, pipelined=False):
+        """Render into host buffers.  pipelined: FGS_RENDER_ASYNC (returns once
+        enqueued; the buffers hold the frame after sync())."""
         st = fgs_stats()
-        fgs_render(self.ctx, self.stream, rgb_host, T_host, 0, FGS_RENDER_STATS if stats else 0, st)
+        flags = (FGS_RENDER_STATS if stats else 0) | (FGS_RENDER_ASYNC if pipelined else 0)
+        fgs_render(self.ctx, self.stream, rgb_host, T_host, 0, flags, st)
         return st
 
     def n_pairs(self) -> int:

@@ -6,7 +6,7 @@
 With --cycle frame k renders pose (pose + k) mod poses.  With --batch the 32-view batch of the city workload is rendered --frames times
 (shrink as given by --tau).  With --tau the frames use that shrink threshold and no calibration kernels run,
 so the launch sequence is exactly the per-frame path (9 kernels per frame:
-frame_begin, filter_pred, filter_anc, compact, project, tile_scan, scatter,
+frame_begin, filter_pred, filter_anc, compact_counted, project, tile_scan, scatter,
 segsort, blend).
 Without it the frames use the 3-sigma footprint.  With --backward the tree's
 attributes are first recomputed from its parameters (one prep_params launch)

@@ -482,3 +482,37 @@ def test_bucket_sizes_at_sort_boundaries(renderer, ties):
     depth_tie = (o.keys[1:] == o.keys[:-1])
     assert depth_tie.any() == (ties != "none")
     assert_frame_parity(g, o)
+
+
+def test_pipelined_host_outputs(renderer, tiny):
+    """FGS_RENDER_ASYNC: six frames of mixed cameras (and one resolution change)
+    rendered into pinned host buffers without waiting, two frames in flight; after
+    fgs_sync every buffer holds exactly what a synchronising host render of the same
+    camera returns (bits of colour and transmittance)."""
+    import torch
+    tree, cam0 = tiny
+    renderer.load_tree(tree)
+    renderer.set_params(tau_R=1.0)
+    renderer.shrink(None)
+    cams = orbit_cameras(tree, 4, (256, 256), 5) + orbit_cameras(tree, 2, (320, 200), 6)
+    ref = []
+    for c in cams:
+        renderer.set_camera(c)
+        rgb = np.zeros((3, c.height, c.width), np.float32)
+        T = np.zeros((c.height, c.width), np.float32)
+        renderer.render_host(rgb, T)
+        ref.append((rgb, T))
+    bufs = [(torch.zeros((3, c.height, c.width), dtype=torch.float32).pin_memory(),
+             torch.zeros((c.height, c.width), dtype=torch.float32).pin_memory()) for c in cams]
+    for c, (rgb, T) in zip(cams, bufs):
+        renderer.set_camera(c)
+        renderer.render_host(rgb.numpy(), T.numpy(), pipelined=True)
+    renderer.sync()
+    for (rgb, T), (rr, tr) in zip(bufs, ref):
+        assert np.array_equal(rgb.numpy().view(np.uint32), rr.view(np.uint32))
+        assert np.array_equal(T.numpy().view(np.uint32), tr.view(np.uint32))
+    # stats need a synchronisation, so they do not combine with the pipelined mode
+    from paper_2603_23891_gb300 import filtergs
+    with pytest.raises(RuntimeError):
+        filtergs.fgs_render(renderer.ctx, renderer.stream, bufs[0][0].numpy(), None, 0,
+                            filtergs.FGS_RENDER_ASYNC | filtergs.FGS_RENDER_STATS, filtergs.fgs_stats())
