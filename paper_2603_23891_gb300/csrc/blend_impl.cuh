@@ -411,6 +411,10 @@ __device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t t
         mbar_init(&H.bar, 1);
         H.timed_out = 0;
     }
+    // every group entry's alpha0 and colour finite from the start
+    static_assert(sizeof(H.grp) == 2 * 256 * sizeof(float4), "two float4 a thread");
+    reinterpret_cast<float4*>(&H.grp[0][0][0])[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    reinterpret_cast<float4*>(&H.grp[0][0][0])[tid + 256] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
 
     float T = 1.0f;
@@ -482,7 +486,9 @@ __device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t t
             const uint32_t n_rounds = __reduce_max_sync(0xffffffffu, (uint32_t)__popc(hits));
             for (uint32_t round = 0; round < n_rounds; ++round) {
                 // branch-free: a lane without a hit left (or whose application
-                // stops) computes on entry 0 and adds nothing
+                // stops) computes on entry 0 and adds nothing: w = 0 times a finite
+                // colour (every group entry holds a real Gaussian's colour or the
+                // zeros it was initialised with)
                 const bool valid = hits != 0u;
                 const uint32_t e = valid ? (uint32_t)(__ffs(hits) - 1) : 0u;
                 hits &= hits - 1u;
@@ -493,9 +499,9 @@ __device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t t
                 const bool stop = valid && Tn < 0.0001f;       // stop before adding this Gaussian
                 const bool apply = valid && !(Tn < 0.0001f);
                 const float w = apply ? alpha * T : 0.0f;
-                Cacc.x = fmaf(apply ? qv.y : 0.0f, w, Cacc.x);
-                Cacc.y = fmaf(apply ? qv.z : 0.0f, w, Cacc.y);
-                Cacc.z = fmaf(apply ? qv.w : 0.0f, w, Cacc.z);
+                Cacc.x = fmaf(qv.y, w, Cacc.x);
+                Cacc.y = fmaf(qv.z, w, Cacc.y);
+                Cacc.z = fmaf(qv.w, w, Cacc.z);
                 if (kCount && valid) {
                     ++c_hits;
                     proc |= 1u << e;
