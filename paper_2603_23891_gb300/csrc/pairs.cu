@@ -14,9 +14,11 @@
 //    taken from the tile's cursor, as one 64-bit item (depth bits << 32 |
 //    rank); the order inside a bucket is arbitrary;
 //  * segsort_kernel: each bucket is sorted by item.  (depth, rank) is unique
-//    within a tile, so the result does not depend on the scatter order.  Three
-//    forms by bucket size: a warp sorts up to kSegSmall items in registers
-//    (bitonic network, lanes exchange through shuffles); a block sorts up to
+//    within a tile, so the result does not depend on the scatter order.  Four
+//    forms by bucket size: a warp sorts up to 32 items in registers (bitonic
+//    network, lanes exchange through shuffles) and up to kSegSmall by depth
+//    radix passes through its slice of shared memory (with the fix of
+//    equal-depth runs below; a longer run: the network); a block sorts up to
 //    kSegSmem items by depth with a stable LSD radix sort in shared memory
 //    (and, if two depths are equal, with the bitonic network by (depth, rank)
 //    instead); a block sorts a larger bucket with an LSD radix sort over every
@@ -509,6 +511,106 @@ __device__ void block_radix_global(unsigned long long* a, unsigned long long* b,
     __syncthreads();
 }
 
+// A warp sorts n <= 32 I items of one tile by (depth, rank), items in registers
+// (item it of lane L is element 32 it + L): stable LSD radix passes over the
+// depth bytes in which the items differ, each ranking the digits with one ballot
+// per digit bit and the warp's 256 counters (hist), the items exchanged through
+// the warp's buffer buf (32 I slots); then each run of equal depths in rank
+// order where it lies, and the pairs written.  Returns false, writing nothing,
+// if a run is longer than kTieRun (the caller sorts the bucket by the bitonic
+// network instead).
+template <int I>
+__device__ bool warp_radix_small(const unsigned long long* items, uint32_t n, uint32_t tile,
+                                 unsigned long long* keys_out, uint32_t* vals_out, unsigned long long* buf,
+                                 uint32_t* hist)
+{
+    const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    unsigned long long x[I];
+    uint32_t vor = 0u, vand = ~0u;
+#pragma unroll
+    for (int it = 0; it < I; ++it) {
+        const uint32_t i = ((uint32_t)it << 5) + lane;
+        x[it] = i < n ? items[i] : ~0ull;
+        if (i < n) {
+            vor |= (uint32_t)(x[it] >> 32);
+            vand &= (uint32_t)(x[it] >> 32);
+        }
+    }
+    const uint32_t diff = __reduce_or_sync(0xffffffffu, vor) & ~__reduce_and_sync(0xffffffffu, vand);
+    for (uint32_t shift = 32; shift < 64; shift += 8) {
+        if (((diff >> (shift - 32)) & 0xFFu) == 0u) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) hist[lane * 8 + j] = 0u;
+        __syncwarp();
+        uint32_t rank[I], dg[I];
+#pragma unroll
+        for (int it = 0; it < I; ++it) {
+            const bool valid = ((uint32_t)it << 5) + lane < n;
+            dg[it] = (uint32_t)(x[it] >> shift) & 0xFFu;
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int bit = 0; bit < 8; ++bit) {
+                const bool on = (dg[it] >> bit) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, on);
+                peers &= on ? bb : ~bb;
+            }
+            const uint32_t base = valid ? hist[dg[it]] : 0u;
+            __syncwarp();
+            if (valid && lane == (uint32_t)(__ffs(peers) - 1)) hist[dg[it]] = base + __popc(peers);
+            __syncwarp();
+            rank[it] = base + __popc(peers & lt);
+        }
+        // exclusive scan of the 256 counters, 8 consecutive ones a lane
+        uint32_t c[8], sum = 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            c[j] = hist[lane * 8 + j];
+            sum += c[j];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += u;
+        }
+        uint32_t run = incl - sum;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            hist[lane * 8 + j] = run;
+            run += c[j];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < I; ++it)
+            if (((uint32_t)it << 5) + lane < n) buf[hist[dg[it]] + rank[it]] = x[it];
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < I; ++it) {
+            const uint32_t i = ((uint32_t)it << 5) + lane;
+            if (i < n) x[it] = buf[i];
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int it = 0; it < I; ++it) {
+        const uint32_t i = ((uint32_t)it << 5) + lane;
+        if (i < n) buf[i] = x[it];
+    }
+    __syncwarp();
+    bool long_run = false;
+    for (uint32_t i = lane; i + 1 < n; i += 32) {
+        const uint32_t d = (uint32_t)(buf[i] >> 32);
+        if ((uint32_t)(buf[i + 1] >> 32) == d && (i == 0 || (uint32_t)(buf[i - 1] >> 32) != d))
+            long_run |= !sort_tie_run64(buf, i, n);
+    }
+    if (__any_sync(0xffffffffu, long_run)) return false;
+    __syncwarp();
+    for (uint32_t i = lane; i < n; i += 32) put_pair(buf[i], tile, keys_out, vals_out, i);
+    __syncwarp();
+    return true;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -737,18 +839,31 @@ __global__ void __launch_bounds__(kSegThreads) segsort_kernel(const uint2* __res
             block_radix_global(it, keys_out + r.x, n, t, keys_out + r.x, vals_out + r.x, s_radix);
         }
     }
-    // small buckets: one warp each, tiles dealt out by warp index
+    // small buckets: one warp each, tiles dealt out by warp index; up to 32 items
+    // by the bitonic network in registers, more by depth radix passes with the
+    // warp's slice of the block sorts' shared memory (free once they are done:
+    // the loop above ends on a barrier), the network if a tie run is too long
     const uint32_t gw = (blockIdx.x * kSegThreads + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * kSegThreads) >> 5;
+    static_assert(kSegSmem >= kSegThreads / 32 * kSegSmall, "a warp's slice holds a small bucket");
+    const uint32_t wl = threadIdx.x >> 5;
+    unsigned long long* const wbuf = s_items + wl * kSegSmall;
+    uint32_t* const whist = s_radix.whist[wl];
     for (uint32_t t = gw; t < n_tiles; t += nw) {
         const uint2 r = ranges[t];
         const uint32_t n = r.y - r.x;
         if (n == 0u || n > (uint32_t)kSegSmall) continue;
         const unsigned long long* it = items + r.x;
+        bool done = true;
         if (n <= 32u) warp_sort_bucket<1>(it, n, t, keys_out + r.x, vals_out + r.x);
-        else if (n <= 64u) warp_sort_bucket<2>(it, n, t, keys_out + r.x, vals_out + r.x);
-        else if (n <= 128u) warp_sort_bucket<4>(it, n, t, keys_out + r.x, vals_out + r.x);
-        else warp_sort_bucket<8>(it, n, t, keys_out + r.x, vals_out + r.x);
+        else if (n <= 64u) done = warp_radix_small<2>(it, n, t, keys_out + r.x, vals_out + r.x, wbuf, whist);
+        else if (n <= 128u) done = warp_radix_small<4>(it, n, t, keys_out + r.x, vals_out + r.x, wbuf, whist);
+        else done = warp_radix_small<8>(it, n, t, keys_out + r.x, vals_out + r.x, wbuf, whist);
+        if (!done) {
+            if (n <= 64u) warp_sort_bucket<2>(it, n, t, keys_out + r.x, vals_out + r.x);
+            else if (n <= 128u) warp_sort_bucket<4>(it, n, t, keys_out + r.x, vals_out + r.x);
+            else warp_sort_bucket<8>(it, n, t, keys_out + r.x, vals_out + r.x);
+        }
     }
 }
 
