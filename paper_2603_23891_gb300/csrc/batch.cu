@@ -158,8 +158,7 @@ __global__ void __launch_bounds__(kProjThreads) bproject_kernel(
     for (int i = threadIdx.x; i < V * (int)(sizeof(DevCamera) / 4); i += blockDim.x)
         reinterpret_cast<uint32_t*>(s_cam)[i] = reinterpret_cast<const uint32_t*>(cams)[i];
     for (int i = threadIdx.x; i < V; i += blockDim.x) s_base[i] = tile_base[i];
-    __shared__ BigPairs s_big;
-    big_pairs_init(s_big);
+    __syncthreads();
     const uint32_t M = st->M;
     const uint32_t n_groups = (M + kProjThreads - 1) / kProjThreads;
     for (uint32_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
@@ -173,9 +172,7 @@ __global__ void __launch_bounds__(kProjThreads) bproject_kernel(
             tiles_x = (uint32_t)s_cam[v].tiles_x;
             tbase = s_base[v];
         }
-        const uint32_t cnt = big_pairs_defer(s_big, f.z, m, tiles_x, tbase);
-        warp_count_pairs(cnt, f.x, f.y, tiles_x, tbase, tile_cnt);
-        big_pairs_count(s_big, foot, tile_cnt);
+        warp_count_pairs(f.z, f.x, f.y, tiles_x, tbase, tile_cnt);
     }
 }
 

@@ -63,6 +63,10 @@ struct WarpPairs {
     }
 };
 
+// Pair counts above which the projection's warp counts a Gaussian's pairs with
+// all its lanes instead of in its rounds.
+constexpr uint32_t kWarpWidePairs = 128;
+
 // The lanes of a round that share a tile form one group; its lowest lane is
 // the leader.  Returns the group mask.
 __device__ __forceinline__ uint32_t tile_group(bool valid, uint32_t tile)
@@ -72,13 +76,26 @@ __device__ __forceinline__ uint32_t tile_group(bool valid, uint32_t tile)
 }
 
 // Count every pair of a warp's Gaussians into tile_cnt: one reduction per tile
-// and round (the lanes of a round that share a tile add together).
+// and round (the lanes of a round that share a tile add together).  A Gaussian
+// with more than kBigPairs pairs is counted first by all 32 lanes, one tile of
+// its rectangle a lane and step (all distinct tiles, so plain reductions).
 __device__ __forceinline__ void warp_count_pairs(uint32_t cnt, uint32_t rect_x, uint32_t rect_y,
                                                  uint32_t tiles_x, uint32_t tile_base,
                                                  uint32_t* __restrict__ tile_cnt)
 {
-    if (__ballot_sync(0xffffffffu, cnt != 0) == 0u) return;
     const uint32_t lane = threadIdx.x & 31;
+    uint32_t wide = __ballot_sync(0xffffffffu, cnt > kWarpWidePairs);
+    while (wide) {
+        const uint32_t b = (uint32_t)__ffs(wide) - 1u;
+        wide &= wide - 1u;
+        const uint32_t n = __shfl_sync(0xffffffffu, cnt, b);
+        const uint32_t rx = __shfl_sync(0xffffffffu, rect_x, b), ry = __shfl_sync(0xffffffffu, rect_y, b);
+        const uint32_t tx = __shfl_sync(0xffffffffu, tiles_x, b), tb = __shfl_sync(0xffffffffu, tile_base, b);
+        const uint32_t x0 = rx & 0xFFFFu, rw = (rx >> 16) - x0, y0 = ry & 0xFFFFu;
+        for (uint32_t k = lane; k < n; k += 32) atomicAdd(tile_cnt + tb + (y0 + k / rw) * tx + (x0 + k % rw), 1u);
+    }
+    if (cnt > kWarpWidePairs) cnt = 0;
+    if (__ballot_sync(0xffffffffu, cnt != 0) == 0u) return;
     const WarpPairs wp(cnt, rect_x, rect_y, tiles_x, tile_base, 0u, 0u);
     for (uint32_t q0 = 0; q0 < wp.wtot; q0 += 32) {
         uint32_t tile, a, b;
@@ -88,11 +105,12 @@ __device__ __forceinline__ void warp_count_pairs(uint32_t cnt, uint32_t rect_x, 
     }
 }
 
-// A Gaussian with more than kBigPairs pairs (a near, wide footprint) would keep
-// its warp walking hundreds of rounds alone while the rest of the grid has
-// finished, so it is set aside in a block-local list and its pairs are
-// enumerated by the whole block after the group of kProjThreads Gaussians it
-// belongs to (a group sets aside at most kProjThreads, so the list never fills).
+// In the scatter, a Gaussian with more than kBigPairs pairs (a near, wide
+// footprint) would keep its warp waiting on hundreds of rounds of cursor
+// increments alone while the rest of the grid has finished, so it is set aside
+// in a block-local list and its pairs are enumerated by the whole block after
+// the group of kProjThreads Gaussians it belongs to (a group sets aside at most
+// kProjThreads, so the list never fills).
 constexpr uint32_t kBigPairs = 128;
 constexpr uint32_t kBigList = kProjThreads;
 
@@ -145,20 +163,6 @@ __device__ __forceinline__ uint32_t rect_tile(const uint4& f, uint32_t k, uint32
     const uint32_t x0 = f.x & 0xFFFFu, rw = (f.x >> 16) - x0;
     const uint32_t y0 = f.y & 0xFFFFu;
     return tile_base + (y0 + k / rw) * tiles_x + (x0 + k % rw);
-}
-
-// The projection's end of a group: count the pairs of its set-aside Gaussians
-// into tile_cnt (foot holds their footprint records).  All threads call it.
-__device__ __forceinline__ void big_pairs_count(BigPairs& L, const uint4* foot, uint32_t* tile_cnt)
-{
-    const uint32_t nb = big_pairs_take(L);
-    if (nb == 0u) return;
-    for (uint32_t b = 0; b < nb; ++b) {
-        const uint4 f = foot[L.m[b]];
-        for (uint32_t k = threadIdx.x; k < f.z; k += blockDim.x)
-            atomicAdd(tile_cnt + rect_tile(f, k, L.tiles_x[b], L.tile_base[b]), 1u);
-    }
-    big_pairs_done(L);
 }
 
 }  // namespace fgs

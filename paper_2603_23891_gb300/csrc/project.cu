@@ -5,8 +5,8 @@
 // radius) and its footprint record (tile rectangle, pair count, depth bits);
 // then each warp enumerates its Gaussians' Gaussian-tile pairs and counts them
 // into their tiles, from which the tile ranges of the sorted pair list follow
-// (pairs.cu); the pairs of a Gaussian with more than kBigPairs of them are
-// counted by the whole block after its group.
+// (pairs.cu); the pairs of a Gaussian with more than kWarpWidePairs of them
+// are counted by all the warp's lanes at once.
 #include "pairs_impl.cuh"
 #include "project_impl.cuh"
 
@@ -16,10 +16,8 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(
     DevTree t, DevCamera cam, const uint32_t* __restrict__ sel, float* __restrict__ splat,
     uint4* __restrict__ foot, uint32_t* __restrict__ tile_cnt, FrameState* st)
 {
-    __shared__ BigPairs s_big;
     grid_dep_wait();
     grid_dep_trigger();
-    big_pairs_init(s_big);
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t M = st->M;
     const uint32_t n_groups = (M + kProjThreads - 1) / kProjThreads;
@@ -29,9 +27,7 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(
         if (m < M) f = proj::project_one(t, cam, __ldg(sel + m), m, splat, foot);
         const uint32_t emitting = __popc(__ballot_sync(0xffffffffu, f.z > 0));
         if (lane == 0 && emitting) atomicAdd(&st->n_emitting, emitting);
-        const uint32_t cnt = big_pairs_defer(s_big, f.z, m, (uint32_t)cam.tiles_x, 0u);
-        warp_count_pairs(cnt, f.x, f.y, (uint32_t)cam.tiles_x, 0u, tile_cnt);
-        big_pairs_count(s_big, foot, tile_cnt);
+        warp_count_pairs(f.z, f.x, f.y, (uint32_t)cam.tiles_x, 0u, tile_cnt);
     }
 }
 
