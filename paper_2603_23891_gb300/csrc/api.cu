@@ -45,7 +45,7 @@ struct fgs_ctx {
     std::string err;
     fgs_params params{};
     // occupancy (resident blocks per SM)
-    int occ_pred = 1, occ_anc = 1, occ_compact = 1, occ_proj = 1, occ_scatter = 1, occ_segsort = 1;
+    int occ_pred = 1, occ_anc = 1, occ_compact = 1, occ_proj = 1, occ_scatter = 1, occ_segsort = 1, occ_scan = 1;
     // tree
     bool has_tree = false;
     DevTree tree{};
@@ -84,6 +84,7 @@ struct fgs_ctx {
     uint2* ranges = nullptr;
     uint32_t* tile_cnt = nullptr;   // pairs per tile, then the tile's scatter cursor
     uint32_t* large = nullptr;      // tiles whose pairs one block sorts
+    unsigned long long* lb_scan = nullptr;   // the tile scan's look-back entries
     float* G = nullptr;
     // image staging for host outputs: rgb planes + T
     size_t img_cap = 0;
@@ -129,7 +130,7 @@ struct fgs_ctx {
         uint32_t *pbits = nullptr, *selbits = nullptr, *sel = nullptr;
         float* splat = nullptr;
         uint4* foot = nullptr;
-        unsigned long long *items = nullptr, *keys = nullptr, *lb_compact = nullptr;
+        unsigned long long *items = nullptr, *keys = nullptr, *lb_compact = nullptr, *lb_scan = nullptr;
         uint32_t* vals = nullptr;
         uint2* ranges = nullptr;
         uint32_t *tile_cnt = nullptr, *large = nullptr;
@@ -242,6 +243,7 @@ int ensure_tiles(fgs_ctx* c, size_t tiles, size_t pixels)
         if ((r = grow(c, (void**)&c->ranges, tiles * sizeof(uint2)))) return r;
         if ((r = grow(c, (void**)&c->tile_cnt, tiles * 4))) return r;
         if ((r = grow(c, (void**)&c->large, tiles * 4))) return r;
+        if ((r = grow(c, (void**)&c->lb_scan, tile_scan_lookback_entries(tiles) * 8))) return r;
         if ((r = grow(c, (void**)&c->G, tiles * 4))) return r;
         c->tile_cap = tiles;
     }
@@ -355,7 +357,8 @@ int enqueue_front(fgs_ctx* c, const DevCamera& dc, cudaStream_t s, cudaEvent_t* 
     if (ev) cudaEventRecord(ev[2], s);
     launch_project(c->tree, dc, c->sel, c->splat, c->foot, c->tile_cnt, c->st, c->sms * c->occ_proj, s);
     if (ev) cudaEventRecord(ev[3], s);
-    launch_tile_scan(c->tile_cnt, c->ranges, tiles, c->large, c->pair_cap, c->st, s);
+    launch_tile_scan(c->tile_cnt, c->ranges, tiles, c->large, c->pair_cap, c->lb_scan, c->st, c->sms * c->occ_scan,
+                     s);
     if (ev) cudaEventRecord(ev[4], s);
     launch_scatter(dc, c->foot, c->tile_cnt, c->keys0, c->pair_cap, c->st, c->sms * c->occ_scatter, s);
     if (ev) cudaEventRecord(ev[5], s);
@@ -420,6 +423,7 @@ int fgs_create(fgs_ctx** out, int device)
     c->occ_proj = occ_project();
     c->occ_scatter = occ_scatter();
     c->occ_segsort = occ_segsort();
+    c->occ_scan = occ_tile_scan();
     c->params.tau_R = 3.0f;
     c->params.tile_w = 16;
     c->params.tile_h = 16;
@@ -448,7 +452,7 @@ int fgs_destroy(fgs_ctx* c)
     cudaDeviceSynchronize();
     void* bufs[] = {c->child_start, c->children, c->frontier0, c->frontier1, c->d_counter,
                     c->tree_mem, c->pbits, c->selbits, c->sel, c->splat, c->lb_compact, c->sel_cnt, c->foot,
-                    c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->ranges, c->tile_cnt, c->large,
+                    c->keys0, c->keys1, c->vals0, c->vals1, c->kpc, c->ranges, c->tile_cnt, c->large, c->lb_scan,
                     c->G, c->img, c->keep, c->st, c->gsplat};
     for (void* p : bufs) free_ptr(p);
     for (float* p : c->ring) free_ptr(p);
@@ -460,7 +464,8 @@ int fgs_destroy(fgs_ctx* c)
     {
         auto& b = c->batch;
         void* bb[] = {b.d_cams, b.d_tile_base, b.d_img_off, b.pbits, b.selbits, b.sel, b.splat,
-                      b.foot, b.items, b.keys, b.vals, b.lb_compact, b.ranges, b.tile_cnt, b.large, b.st};
+                      b.foot, b.items, b.keys, b.vals, b.lb_compact, b.lb_scan, b.ranges, b.tile_cnt, b.large,
+                      b.st};
         for (void* p : bb) free_ptr(p);
         if (b.h_cams) cudaFreeHost(b.h_cams);
         if (b.graph) cudaGraphExecDestroy(b.graph);
@@ -1209,6 +1214,7 @@ int fgs_batch_setup(fgs_ctx* c, const fgs_camera* views, int n_views, const int3
     if ((r = grow(c, (void**)&b.pbits, 4 * n_words * n_views))) return r;
     if ((r = grow(c, (void**)&b.selbits, 4 * n_words * n_views))) return r;
     if ((r = grow(c, (void**)&b.lb_compact, 8 * (n_words * n_views / kCompactWords + 2)))) return r;
+    if ((r = grow(c, (void**)&b.lb_scan, 8 * tile_scan_lookback_entries(b.total_tiles)))) return r;
     if (sel_cap != b.sel_cap) {
         if ((r = grow(c, (void**)&b.sel, 4 * sel_cap))) return r;
         if ((r = grow(c, (void**)&b.splat, 4 * kSplatStride * sel_cap))) return r;
@@ -1264,7 +1270,7 @@ void enqueue_batch(fgs_ctx* c, float* rgb, float* T, cudaStream_t s)
     auto& b = c->batch;
     launch_batch_front(c->tree, b.d_cams, b.V, b.total_tiles, b.d_tile_base, b.pbits, b.selbits, b.sel,
                        (uint32_t)b.sel_cap, b.splat, b.foot, b.tile_cnt, b.large, b.items, b.keys, b.vals,
-                       b.pair_cap, b.lb_compact, b.ranges, b.st, c->sms, s);
+                       b.pair_cap, b.lb_compact, b.lb_scan, b.ranges, b.st, c->sms, s);
     launch_batch_blend(b.d_cams, b.V, b.total_tiles, b.d_tile_base, b.d_img_off, b.ranges, b.vals, b.splat,
                        rgb, T, b.st, s);
 }

@@ -211,8 +211,8 @@ void launch_batch_front(const DevTree& t, const DevCamera* cams, int V, uint32_t
                         const uint32_t* tile_base, uint32_t* pbits, uint32_t* selbits, uint32_t* sel,
                         uint32_t sel_cap, float* splat, uint4* foot, uint32_t* tile_cnt, uint32_t* large,
                         unsigned long long* items, unsigned long long* keys, uint32_t* vals,
-                        unsigned long long cap, unsigned long long* lb_compact, uint2* ranges,
-                        FrameState* st, int sms, cudaStream_t s)
+                        unsigned long long cap, unsigned long long* lb_compact, unsigned long long* lb_scan,
+                        uint2* ranges, FrameState* st, int sms, cudaStream_t s)
 {
     const uint32_t n_words = t.n_pad >> 5;
     int b0 = (int)((total_tiles + 255) / 256);
@@ -227,7 +227,7 @@ void launch_batch_front(const DevTree& t, const DevCamera* cams, int V, uint32_t
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bproject_kernel, kProjThreads, 0);
     bproject_kernel<<<sms * (occ > 0 ? occ : 1), kProjThreads, 0, s>>>(t, cams, V, tile_base, sel, splat,
                                                                        foot, tile_cnt, st);
-    launch_tile_scan(tile_cnt, ranges, total_tiles, large, cap, st, s);
+    launch_tile_scan(tile_cnt, ranges, total_tiles, large, cap, lb_scan, st, sms * occ_tile_scan(), s);
     launch_scatter_batch(cams, tile_base, t.n_pad, sel, foot, tile_cnt, items, cap, st, sms * occ_scatter(), s);
     launch_segsort(ranges, total_tiles, large, items, keys, vals, st, sms * occ_segsort(), s);
 }

@@ -75,7 +75,7 @@ struct FrameState {
     uint32_t tickets[16];      // dynamic tile counters (one per kernel use)
     int32_t status;            // latched error (0 = ok)
     uint32_t status_info;
-    uint32_t n_large;                     // tiles whose pairs one block sorts (> kSegSmall)
+    uint32_t reserved0;
     unsigned long long blend_entries;     // lockstep warp steps of the list walk (counting frames only)
     unsigned long long blend_evals;       // pixel-Gaussian evaluations (lanes not yet stopped)
     unsigned long long blend_hits;        // evaluations that reached the alpha / T update
@@ -87,7 +87,7 @@ struct FrameState {
 };
 
 // Ticket slots
-enum : int { kTicketCompact = 0, kTicketSegSort = 2 };
+enum : int { kTicketCompact = 0, kTicketSegSort = 2, kTicketScan = 4, kTicketLarge = 5 };
 
 // ---------------------------------------------------------------------
 // decision-exact binary32 helpers
@@ -358,9 +358,16 @@ void launch_compact_counted(const uint32_t* selbits, uint32_t n_words, uint32_t*
 void launch_project(const DevTree& t, const DevCamera& cam, const uint32_t* sel, float* splat,
                     uint4* foot, uint32_t* tile_cnt, FrameState* st, int blocks, cudaStream_t s);
 // Tile ranges (clamped to cap), scatter cursors (in tile_cnt), N_P and the list
-// of tiles with more than kSegSmall pairs (large[], FrameState::n_large).
+// of tiles with more than kSegSmall pairs (large[], their number in
+// FrameState::tickets[kTicketLarge]); lookback holds
+// tile_scan_lookback_entries(n_tiles) entries; blocks at most the resident
+// capacity (sms * occ_tile_scan()).
 void launch_tile_scan(uint32_t* tile_cnt, uint2* ranges, uint32_t n_tiles, uint32_t* large,
-                      unsigned long long cap, FrameState* st, cudaStream_t s);
+                      unsigned long long cap, unsigned long long* lookback, FrameState* st, int blocks,
+                      cudaStream_t s);
+int occ_tile_scan();
+// Look-back entries the tile scan needs for n_tiles tiles.
+inline size_t tile_scan_lookback_entries(size_t n_tiles) { return n_tiles / 2048 + 2; }
 // Every pair into its tile's bucket of items[] (depth bits << 32 | rank).
 void launch_scatter(const DevCamera& cam, const uint4* foot, uint32_t* cursor, unsigned long long* items,
                     unsigned long long cap, FrameState* st, int blocks, cudaStream_t s);
@@ -385,7 +392,7 @@ void launch_batch_front(const DevTree& t, const DevCamera* cams, int V, uint32_t
                         const uint32_t* tile_base, uint32_t* pbits, uint32_t* selbits, uint32_t* sel,
                         uint32_t sel_cap, float* splat, uint4* foot, uint32_t* tile_cnt, uint32_t* large,
                         unsigned long long* items, unsigned long long* keys, uint32_t* vals,
-                        unsigned long long cap, unsigned long long* lb_compact, uint2* ranges,
+                        unsigned long long cap, unsigned long long* lb_compact, unsigned long long* lb_scan, uint2* ranges,
                         FrameState* st, int sms, cudaStream_t s);
 void launch_batch_blend(const DevCamera* cams, int V, uint32_t total_tiles, const uint32_t* tile_base,
                         const unsigned long long* img_off, const uint2* ranges, const uint32_t* vals,

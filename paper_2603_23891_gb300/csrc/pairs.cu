@@ -7,9 +7,9 @@
 // key, the pairs are bucketed by tile and each tile's bucket is sorted on its
 // own:
 //  * the projection counts every pair into its tile (pairs_impl.cuh);
-//  * tile_scan_kernel: one block turns the counts into tile ranges [first,
-//    last) and scatter cursors (exclusive prefix), N_P, and the list of tiles
-//    with more than kSegSmall pairs;
+//  * tile_scan_kernel: turns the counts into tile ranges [first, last) and
+//    scatter cursors (exclusive prefix, decoupled look-back across scan tiles
+//    of 2048 tiles), N_P, and the list of tiles with more than kSegSmall pairs;
 //  * scatter_kernel: every pair is written into its tile's bucket at a slot
 //    taken from the tile's cursor, as one 64-bit item (depth bits << 32 |
 //    rank); the order inside a bucket is arbitrary;
@@ -31,8 +31,8 @@ namespace fgs {
 
 namespace {
 
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 8;                 // tiles per thread per round (8192 per round)
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;                 // consecutive tiles per thread (2048 per scan tile)
 constexpr int kSegThreads = 256;
 constexpr int kScatterRounds = 4;             // enumeration rounds whose cursor increments overlap
 constexpr unsigned long long kItemPad = ~0ull;   // sorts after every real item
@@ -616,83 +616,163 @@ __device__ bool warp_radix_small(const unsigned long long* items, uint32_t n, ui
 // ---------------------------------------------------------------------------
 // tile ranges
 // ---------------------------------------------------------------------------
+// Scan tiles of kScanTile consecutive image tiles, kScanItems a thread; a scan
+// tile's first pair slot comes from a decoupled look-back over the totals of
+// the scan tiles before it (64-bit look-back entries: epoch tag, flag, 32-bit
+// count).  Counts saturate at 2^32 - 1, far above any pair capacity (< 2^31),
+// so a saturated prefix still clamps to the capacity and latches the error.
+constexpr uint32_t kScanTile = (uint32_t)kScanThreads * kScanItems;
+constexpr uint32_t kScanTag = 10u;          // the tile scan's look-back tag, epoch * 16 + 10
+
+__device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b)
+{
+    const uint32_t r = a + b;
+    return r < a ? 0xFFFFFFFFu : r;
+}
+
+// The exclusive prefix of scan tile `tile` over the entries of lb (one full
+// warp; lane l reads predecessor base - l, nearest first up to the first
+// inclusive entry), with saturating sums; bounded like warp_lookback.
+__device__ uint32_t scan_lookback(const unsigned long long* lb, uint32_t tile, uint32_t tag, FrameState* st)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t tg = tag & 0x3FFFFFFFu;
+    unsigned long long prefix = 0;
+    int base = (int)tile - 1;
+    uint64_t spins = 0;
+    while (base >= 0) {
+        const int j = base - (int)lane;
+        bool ready = true, incl = true;
+        uint32_t val = 0;
+        if (j >= 0) {
+            const unsigned long long e = ld_lb_u64(lb + j);
+            const unsigned long long flag = (e >> 32) & 3ull;
+            ready = ((uint32_t)(e >> 34) == tg) && flag != 0;
+            incl = flag == kFlagIncl;
+            val = (uint32_t)e;
+        }
+        const uint32_t nr = __ballot_sync(0xffffffffu, !ready);
+        const uint32_t first_nr = nr ? (uint32_t)(__ffs(nr) - 1) : 32u;
+        const uint32_t usable = first_nr == 32u ? 0xffffffffu : ((1u << first_nr) - 1u);
+        const uint32_t inc = __ballot_sync(0xffffffffu, ready && incl) & usable;
+        const uint32_t take = inc ? (uint32_t)__ffs(inc) : first_nr;
+        unsigned long long v = lane < take ? val : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        prefix += v;
+        if (prefix > 0xFFFFFFFFull) prefix = 0xFFFFFFFFull;
+        if (inc) break;
+        if (take == 0) {
+            if (++spins > kSpinLimit) {
+                set_status(st, kErrTimeout, 0x310u);
+                break;
+            }
+            __nanosleep(20);
+        }
+        base -= (int)take;
+    }
+    return (uint32_t)prefix;
+}
+
 __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(uint32_t* __restrict__ tile_cnt,
                                                                  uint2* __restrict__ ranges,
                                                                  uint32_t n_tiles,
                                                                  uint32_t* __restrict__ large,
-                                                                 unsigned long long cap, FrameState* st)
+                                                                 unsigned long long cap,
+                                                                 unsigned long long* lb, FrameState* st)
 {
     constexpr int kWarps = kScanThreads / 32;
-    __shared__ unsigned long long s_warp[kScanItems][kWarps];   // per round: warp totals, then prefixes
-    __shared__ unsigned long long s_round[kScanItems];          // per round: total
-    __shared__ uint32_t s_nlarge;
+    __shared__ uint32_t s_warp[kWarps];
+    __shared__ uint32_t s_tile, s_prefix;
     grid_dep_wait();
     grid_dep_trigger();
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_nlarge = 0;
-    unsigned long long carry = 0;
-    // kScanItems rounds of kScanThreads consecutive tiles each (coalesced): all
-    // rounds' warp scans, one barrier, round and warp prefixes, one barrier
-    for (uint32_t base = 0; base < n_tiles; base += kScanThreads * kScanItems) {
+    const uint32_t n_st = (n_tiles + kScanTile - 1) / kScanTile;
+    const uint32_t tag = st->epoch * 16u + kScanTag;
+    const uint32_t cap32 = (uint32_t)cap;
+    // block b takes scan tile b first, later ones come from a ticket counter in
+    // order (the grid is at most the resident capacity: every look-back wait ends)
+    bool first = true;
+    for (;;) {
+        if (tid == 0) s_tile = first ? blockIdx.x : gridDim.x + atomicAdd(&st->tickets[kTicketScan], 1u);
+        first = false;
+        __syncthreads();
+        const uint32_t sti = s_tile;
+        if (sti >= n_st) break;
+        const uint32_t t0 = sti * kScanTile + tid * kScanItems;
         uint32_t c[kScanItems];
-        unsigned long long incl[kScanItems];
+        if (t0 + kScanItems <= n_tiles) {
+            const uint4 a = *reinterpret_cast<const uint4*>(tile_cnt + t0);
+            const uint4 b = *reinterpret_cast<const uint4*>(tile_cnt + t0 + 4);
+            c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+            c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+        } else {
 #pragma unroll
-        for (int i = 0; i < kScanItems; ++i) {
-            const uint32_t t = base + i * kScanThreads + tid;
-            c[i] = t < n_tiles ? tile_cnt[t] : 0u;
+            for (int i = 0; i < kScanItems; ++i) c[i] = t0 + i < n_tiles ? tile_cnt[t0 + i] : 0u;
         }
+        uint32_t sum = 0;
 #pragma unroll
-        for (int i = 0; i < kScanItems; ++i) {
-            incl[i] = c[i];
+        for (int i = 0; i < kScanItems; ++i) sum = sat_add(sum, c[i]);
+        // warp and block scans of the threads' sums (saturating)
+        uint32_t incl = sum;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long up = __shfl_up_sync(0xffffffffu, incl[i], o);
-                if (lane >= (uint32_t)o) incl[i] += up;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl = sat_add(incl, u);
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        uint32_t woff = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t tw = s_warp[w];
+            if (w < (int)warp) woff = sat_add(woff, tw);
+            total = sat_add(total, tw);
+        }
+        if (warp == 0) {
+            uint32_t prefix = 0;
+            if (sti == 0) {
+                if (lane == 0) st_lb_u64(lb, lb_pack(tag, kFlagIncl, total));
+            } else {
+                if (lane == 0) st_lb_u64(lb + sti, lb_pack(tag, kFlagAgg, total));
+                prefix = scan_lookback(lb, sti, tag, st);
+                if (lane == 0) st_lb_u64(lb + sti, lb_pack(tag, kFlagIncl, sat_add(prefix, total)));
             }
-            if (lane == 31) s_warp[i][warp] = incl[i];
+            if (lane == 0) {
+                s_prefix = prefix;
+                if (sti == n_st - 1) {
+                    const uint32_t np = sat_add(prefix, total);
+                    st->n_pairs = np;
+                    if ((unsigned long long)np > cap) set_status(st, kErrCapacity, 0x300u);
+                }
+            }
         }
         __syncthreads();
-        if (warp < kScanItems) {
-            const unsigned long long v = s_warp[warp][lane];
-            unsigned long long w = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long up = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= (uint32_t)o) w += up;
-            }
-            s_warp[warp][lane] = w - v;                  // exclusive over the round's warps
-            if (lane == 31) s_round[warp] = w;
-        }
-        __syncthreads();
-        unsigned long long round_base = carry;
+        uint32_t off = sat_add(s_prefix, sat_add(woff, incl - (incl == 0xFFFFFFFFu ? 0u : sum)));
+        if (incl == 0xFFFFFFFFu) off = 0xFFFFFFFFu;          // saturated: clamps to the capacity below
+        // each tile's range [first, last) clamped to the capacity, its scatter cursor,
+        // and the list of tiles for the block sort (one reservation per warp and item)
 #pragma unroll
         for (int i = 0; i < kScanItems; ++i) {
-            const uint32_t t = base + i * kScanThreads + tid;
-            const unsigned long long off = round_base + s_warp[i][warp] + incl[i] - c[i];
-            const unsigned long long a = off < cap ? off : cap;
-            const unsigned long long e = off + c[i] < cap ? off + c[i] : cap;
+            const uint32_t t = t0 + i;
+            const uint32_t a = off < cap32 ? off : cap32;
+            const uint32_t end = sat_add(off, c[i]);
+            const uint32_t e = end < cap32 ? end : cap32;
             if (t < n_tiles) {
-                ranges[t] = make_uint2((uint32_t)a, (uint32_t)e);
-                tile_cnt[t] = (uint32_t)a;            // the tile's scatter cursor
+                ranges[t] = make_uint2(a, e);
+                tile_cnt[t] = a;
             }
-            // tiles for the block sort: one list reservation per warp and round
-            const bool big = t < n_tiles && e - a > (unsigned long long)kSegSmall;
+            const bool big = t < n_tiles && e - a > (uint32_t)kSegSmall;
             const uint32_t bm = __ballot_sync(0xffffffffu, big);
             if (bm) {
                 uint32_t slot = 0;
-                if (lane == 0) slot = atomicAdd(&s_nlarge, (uint32_t)__popc(bm));
+                if (lane == 0) slot = atomicAdd(&st->tickets[kTicketLarge], (uint32_t)__popc(bm));
                 slot = __shfl_sync(0xffffffffu, slot, 0);
                 if (big) large[slot + __popc(bm & ((1u << lane) - 1u))] = t;
             }
-            round_base += s_round[i];
+            off = end;
         }
-        carry = round_base;
         __syncthreads();
-    }
-    if (tid == 0) {
-        st->n_pairs = carry;
-        st->n_large = s_nlarge;
-        if (carry > cap) set_status(st, kErrCapacity, 0x300u);
     }
 }
 
@@ -703,8 +783,8 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(uint32_t* __res
 // indexes entries view * n_pad + node, and a pair's tile is its view's first
 // tile plus the tile in the view) goes to its tile's bucket as
 // depth bits << 32 | m.  Slots at or beyond cap are not written (the scan has
-// latched FGS_ERR_CAPACITY).  A Gaussian with more than kBigPairs pairs is
-// scattered by the whole block after its group.
+// latched FGS_ERR_CAPACITY).  A Gaussian with more than kWarpWidePairs pairs
+// is scattered by all lanes of its warp first (scatter_wide).
 // One warp's Gaussians (lane L: pair count cnt, footprint f, its view's grid
 // width and first tile, rank m) into their tiles' buckets, kScatterRounds rounds
 // at a time so that their cursor increments are in flight together; one
@@ -739,23 +819,38 @@ __device__ __forceinline__ void scatter_warp(uint32_t cnt, const uint4& f, uint3
     }
 }
 
-// The pairs of one set-aside Gaussian (rank m, footprint f) by the whole block,
-// kScatterRounds slots a thread in flight.
-__device__ __forceinline__ void scatter_block(const uint4& f, uint32_t m, uint32_t tiles_x, uint32_t tbase,
-                                              uint32_t* __restrict__ cursor,
-                                              unsigned long long* __restrict__ items, unsigned long long cap)
+// The warp's Gaussians with more than kWarpWidePairs pairs (a near, wide
+// footprint: up to thousands of tiles), one at a time, by all 32 lanes: one tile
+// of the rectangle a lane and step (all distinct tiles, so one cursor increment
+// a pair), kWideSlots increments a lane in flight before the items are stored.
+constexpr int kWideSlots = 16;
+__device__ __forceinline__ void scatter_wide(uint32_t wide, const uint4& f, uint32_t tiles_x, uint32_t tbase,
+                                             uint32_t m, uint32_t* __restrict__ cursor,
+                                             unsigned long long* __restrict__ items, unsigned long long cap)
 {
-    const unsigned long long item = ((unsigned long long)f.w << 32) | m;
-    for (uint32_t k0 = 0; k0 < f.z; k0 += kScatterRounds * kProjThreads) {
-        uint32_t pos[kScatterRounds];
+    const uint32_t lane = threadIdx.x & 31;
+    while (wide) {
+        const uint32_t b = (uint32_t)__ffs(wide) - 1u;
+        wide &= wide - 1u;
+        uint4 fb;
+        fb.x = __shfl_sync(0xffffffffu, f.x, b);
+        fb.y = __shfl_sync(0xffffffffu, f.y, b);
+        fb.z = __shfl_sync(0xffffffffu, f.z, b);
+        fb.w = __shfl_sync(0xffffffffu, f.w, b);
+        const uint32_t mb = __shfl_sync(0xffffffffu, m, b);
+        const uint32_t tx = __shfl_sync(0xffffffffu, tiles_x, b), tb = __shfl_sync(0xffffffffu, tbase, b);
+        const unsigned long long item = ((unsigned long long)fb.w << 32) | mb;
+        for (uint32_t k0 = 0; k0 < fb.z; k0 += 32u * kWideSlots) {
+            uint32_t pos[kWideSlots];
 #pragma unroll
-        for (int r = 0; r < kScatterRounds; ++r) {
-            const uint32_t k = k0 + r * kProjThreads + threadIdx.x;
-            pos[r] = k < f.z ? atomicAdd(cursor + rect_tile(f, k, tiles_x, tbase), 1u) : 0xFFFFFFFFu;
+            for (int r = 0; r < kWideSlots; ++r) {
+                const uint32_t k = k0 + (uint32_t)r * 32u + lane;
+                pos[r] = k < fb.z ? atomicAdd(cursor + rect_tile(fb, k, tx, tb), 1u) : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int r = 0; r < kWideSlots; ++r)
+                if (pos[r] != 0xFFFFFFFFu && pos[r] < cap) items[pos[r]] = item;
         }
-#pragma unroll
-        for (int r = 0; r < kScatterRounds; ++r)
-            if (pos[r] != 0xFFFFFFFFu && pos[r] < cap) items[pos[r]] = item;
     }
 }
 
@@ -766,10 +861,8 @@ __global__ void __launch_bounds__(kProjThreads) scatter_kernel(
     uint32_t* __restrict__ cursor, unsigned long long* __restrict__ items, unsigned long long cap,
     FrameState* st)
 {
-    __shared__ BigPairs s_big;
     grid_dep_wait();
     grid_dep_trigger();
-    big_pairs_init(s_big);
     const uint32_t M = st->M;
     const uint32_t n_groups = (M + kProjThreads - 1) / kProjThreads;
     for (uint32_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
@@ -786,14 +879,10 @@ __global__ void __launch_bounds__(kProjThreads) scatter_kernel(
                 tiles_x = (uint32_t)cam.tiles_x;
             }
         }
-        const uint32_t cnt = big_pairs_defer(s_big, f.z, m, tiles_x, tbase);
+        const uint32_t wide = __ballot_sync(0xffffffffu, f.z > kWarpWidePairs);
+        if (wide) scatter_wide(wide, f, tiles_x, tbase, m, cursor, items, cap);
+        const uint32_t cnt = f.z > kWarpWidePairs ? 0u : f.z;
         if (__ballot_sync(0xffffffffu, cnt != 0) != 0u) scatter_warp(cnt, f, tiles_x, tbase, m, cursor, items, cap);
-        const uint32_t nb = big_pairs_take(s_big);
-        if (nb == 0u) continue;
-        for (uint32_t b = 0; b < nb; ++b)
-            scatter_block(__ldg(foot + s_big.m[b]), s_big.m[b], s_big.tiles_x[b], s_big.tile_base[b], cursor,
-                          items, cap);
-        big_pairs_done(s_big);
     }
 }
 
@@ -814,7 +903,7 @@ __global__ void __launch_bounds__(kSegThreads) segsort_kernel(const uint2* __res
     grid_dep_trigger();
     // large buckets first: one block each; a block's first bucket is its index,
     // later ones come from a ticket counter
-    const uint32_t n_large = st->n_large;
+    const uint32_t n_large = st->tickets[kTicketLarge];
     bool first = true;
     for (;;) {
         if (threadIdx.x == 0)
@@ -871,9 +960,21 @@ __global__ void __launch_bounds__(kSegThreads) segsort_kernel(const uint2* __res
 // launchers
 // ---------------------------------------------------------------------------
 void launch_tile_scan(uint32_t* tile_cnt, uint2* ranges, uint32_t n_tiles, uint32_t* large,
-                      unsigned long long cap, FrameState* st, cudaStream_t s)
+                      unsigned long long cap, unsigned long long* lookback, FrameState* st, int blocks,
+                      cudaStream_t s)
 {
-    launch_pdl(tile_scan_kernel, 1, kScanThreads, 0, s, tile_cnt, ranges, n_tiles, large, cap, st);
+    const uint32_t n_st = (n_tiles + kScanTile - 1) / kScanTile;
+    if (blocks > (int)n_st) blocks = (int)n_st;
+    if (blocks < 1) blocks = 1;
+    launch_pdl(tile_scan_kernel, blocks, kScanThreads, 0, s, tile_cnt, ranges, n_tiles, large, cap, lookback,
+               st);
+}
+
+int occ_tile_scan()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tile_scan_kernel, kScanThreads, 0);
+    return b > 0 ? b : 1;
 }
 
 void launch_scatter(const DevCamera& cam, const uint4* foot, uint32_t* cursor, unsigned long long* items,

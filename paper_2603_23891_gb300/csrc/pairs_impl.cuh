@@ -63,8 +63,10 @@ struct WarpPairs {
     }
 };
 
-// Pair counts above which the projection's warp counts a Gaussian's pairs with
-// all its lanes instead of in its rounds.
+// Pair counts above which the projection's (and the scatter's) warp enumerates
+// a Gaussian's pairs with all its lanes instead of in its rounds: a footprint
+// of thousands of tiles would otherwise keep one warp walking hundreds of rounds
+// alone while the rest of the grid has finished.
 constexpr uint32_t kWarpWidePairs = 128;
 
 // The lanes of a round that share a tile form one group; its lowest lane is
@@ -77,7 +79,7 @@ __device__ __forceinline__ uint32_t tile_group(bool valid, uint32_t tile)
 
 // Count every pair of a warp's Gaussians into tile_cnt: one reduction per tile
 // and round (the lanes of a round that share a tile add together).  A Gaussian
-// with more than kBigPairs pairs is counted first by all 32 lanes, one tile of
+// with more than kWarpWidePairs pairs is counted first by all 32 lanes, one tile of
 // its rectangle a lane and step (all distinct tiles, so plain reductions).
 __device__ __forceinline__ void warp_count_pairs(uint32_t cnt, uint32_t rect_x, uint32_t rect_y,
                                                  uint32_t tiles_x, uint32_t tile_base,
@@ -103,58 +105,6 @@ __device__ __forceinline__ void warp_count_pairs(uint32_t cnt, uint32_t rect_x, 
         const uint32_t grp = tile_group(valid, tile);
         if (grp && lane == (uint32_t)(__ffs(grp) - 1)) atomicAdd(tile_cnt + tile, (uint32_t)__popc(grp));
     }
-}
-
-// In the scatter, a Gaussian with more than kBigPairs pairs (a near, wide
-// footprint) would keep its warp waiting on hundreds of rounds of cursor
-// increments alone while the rest of the grid has finished, so it is set aside
-// in a block-local list and its pairs are enumerated by the whole block after
-// the group of kProjThreads Gaussians it belongs to (a group sets aside at most
-// kProjThreads, so the list never fills).
-constexpr uint32_t kBigPairs = 128;
-constexpr uint32_t kBigList = kProjThreads;
-
-struct BigPairs {
-    uint32_t n;                     // Gaussians set aside
-    uint32_t m[kBigList];           // their ranks
-    uint32_t tiles_x[kBigList];     // their view's tile-grid width
-    uint32_t tile_base[kBigList];   // their view's first tile id
-};
-
-__device__ __forceinline__ void big_pairs_init(BigPairs& L)
-{
-    if (threadIdx.x == 0) L.n = 0;
-    __syncthreads();
-}
-
-// The pair count this lane's warp enumerates: 0 for a Gaussian set aside.
-__device__ __forceinline__ uint32_t big_pairs_defer(BigPairs& L, uint32_t cnt, uint32_t m, uint32_t tiles_x,
-                                                    uint32_t tile_base)
-{
-    if (cnt <= kBigPairs) return cnt;
-    const uint32_t slot = atomicAdd(&L.n, 1u);
-    L.m[slot] = m;
-    L.tiles_x[slot] = tiles_x;
-    L.tile_base[slot] = tile_base;
-    return 0u;
-}
-
-// After a group (all threads call it): how many Gaussians the group set aside.
-// Every thread has read the count before any thread sets one aside again.
-__device__ __forceinline__ uint32_t big_pairs_take(const BigPairs& L)
-{
-    __syncthreads();
-    const uint32_t nb = L.n;
-    __syncthreads();
-    return nb;
-}
-
-// After the set-aside Gaussians of a group are enumerated (all threads call
-// it, only when big_pairs_take returned a nonzero count): empty the list.
-__device__ __forceinline__ void big_pairs_done(BigPairs& L)
-{
-    if (threadIdx.x == 0) L.n = 0;
-    __syncthreads();
 }
 
 // Tile of pair k of footprint f (row-major in its rectangle).
