@@ -70,7 +70,7 @@ struct fgs_ctx {
     uint32_t* sel = nullptr;
     float* splat = nullptr;
     unsigned long long* lb_compact = nullptr;
-    uint32_t* sel_cnt = nullptr;    // selected nodes per compaction tile (the Ancestor filter's counts)
+    uint32_t* sel_cnt = nullptr;    // selected nodes per 256-word tile (the Ancestor filter's counts)
     uint4* foot = nullptr;          // per selected Gaussian: rect, pair count, depth bits
     // pair-sized buffers
     uint64_t pair_cap = 0;
@@ -207,7 +207,7 @@ int ensure_nodes(fgs_ctx* c, size_t n_pad)
     if ((r = grow(c, (void**)&c->sel, n_pad * 4))) return r;
     if ((r = grow(c, (void**)&c->splat, n_pad * kSplatStride * 4))) return r;
     if ((r = grow(c, (void**)&c->lb_compact, (n_pad / 32 / kCompactWords + 2) * 8))) return r;
-    if ((r = grow(c, (void**)&c->sel_cnt, (n_pad / 32 / kCompactWords + 2) * 4))) return r;
+    if ((r = grow(c, (void**)&c->sel_cnt, (n_pad / 32 / kSelTileWords + 2) * 4))) return r;
     if ((r = grow(c, (void**)&c->foot, n_pad * sizeof(uint4)))) return r;
     c->node_cap = n_pad;
     return FGS_OK;
@@ -330,8 +330,8 @@ bool valid_camera(const fgs_camera* cam)
            cam->width >= 1 && cam->height >= 1 && cam->width <= 16384 && cam->height <= 16384;
 }
 
-// Compaction tiles of the loaded tree's selection bits.
-size_t n_sel_tiles(const fgs_ctx* c) { return (c->tree.n_pad / 32 + kCompactWords - 1) / kCompactWords; }
+// Counted tiles (kSelTileWords words each) of the loaded tree's selection bits.
+size_t n_sel_tiles(const fgs_ctx* c) { return (c->tree.n_pad / 32 + kSelTileWords - 1) / kSelTileWords; }
 
 int check_ready(fgs_ctx* c)
 {

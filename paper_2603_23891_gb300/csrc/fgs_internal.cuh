@@ -22,6 +22,7 @@ constexpr int kSegSmall = 256;            // pairs of a tile sorted by one warp 
 constexpr int kSegSmem = 2048;            // pairs of a tile sorted by one block in shared memory
 constexpr int kFilterTile = 4096;         // node arrays are padded to a multiple of this
 constexpr int kCompactWords = 1024;       // 32-bit selection words per compaction tile (32K nodes)
+constexpr int kSelTileWords = 256;        // words per counted tile (the Ancestor filter's sel_cnt)
 constexpr int kAncCacheWords = 4096;      // P-bit words of the lowest node ids kept in shared memory
 constexpr int kProjThreads = 256;         // selected Gaussians per projection tile
 constexpr uint64_t kSpinLimit = 1ull << 24;   // bounded spin-waits
@@ -338,7 +339,7 @@ void launch_frame_begin(FrameState* st, uint32_t* tile_cnt, int n_tiles, uint32_
                         cudaStream_t s);
 void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits, FrameState* count_st, int blocks,
                         cudaStream_t s);
-// Also adds each word's selected nodes to sel_cnt[word / kCompactWords].
+// Also adds each word's selected nodes to sel_cnt[word / kSelTileWords].
 void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, uint32_t* sel_cnt,
                        int blocks, cudaStream_t s);
 // Writes at most cap ids; more survivors latch FGS_ERR_CAPACITY and M = cap.

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256) filter_anc_kernel(DevTree t, const uint32
             if (keep) keep = !ancestor_blocked16(t, pbits, s_pb, cw, n);
             const uint32_t b = __ballot_sync(0xffffffffu, keep);
             if (lane == i) res = b;
-            if (lane == 0 && b) atomicAdd(sel_cnt + w / kCompactWords, (uint32_t)__popc(b));
+            if (lane == 0 && b) atomicAdd(sel_cnt + w / kSelTileWords, (uint32_t)__popc(b));
         }
         if (wl < n_words) selbits[wl] = res;
     }
@@ -313,46 +313,41 @@ __global__ void __launch_bounds__(256) compact_kernel(const uint32_t* __restrict
 }
 
 // Compaction of the frame's selection bits when the Ancestor filter has also
-// counted the selected nodes of every compaction tile (sel_cnt): one block per
-// tile takes its first slot as the sum of the counts of the tiles before it, so
-// no block waits on another (no look-back chain); then the popcounts, block scan
-// and warp-cooperative bit expansion of compact_kernel.
-__global__ void __launch_bounds__(256) compact_counted_kernel(const uint32_t* __restrict__ selbits,
-                                                              uint32_t n_words, uint32_t* __restrict__ sel,
-                                                              uint32_t cap, const uint32_t* __restrict__ sel_cnt,
-                                                              FrameState* st)
+// counted the selected nodes of every kSelTileWords-word tile (sel_cnt): one
+// block per tile, one word per thread, takes the tile's first slot as the sum
+// of the counts of the tiles before it, so no block waits on another (no
+// look-back chain); then popcounts, a block scan and a warp-cooperative bit
+// expansion of each warp's 32 words (coalesced stores of ascending ids).
+__global__ void __launch_bounds__(kSelTileWords) compact_counted_kernel(const uint32_t* __restrict__ selbits,
+                                                                        uint32_t n_words,
+                                                                        uint32_t* __restrict__ sel, uint32_t cap,
+                                                                        const uint32_t* __restrict__ sel_cnt,
+                                                                        FrameState* st)
 {
-    __shared__ uint32_t s_warp_tot[8];
+    constexpr int kWarps = kSelTileWords / 32;
+    __shared__ uint32_t s_warp_tot[kWarps];
     __shared__ uint32_t s_prefix;
     grid_dep_wait();
     grid_dep_trigger();
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t tile = blockIdx.x;
-    const uint32_t n_tiles = (n_words + kCompactWords - 1) / kCompactWords;
+    const uint32_t n_tiles = (n_words + kSelTileWords - 1) / kSelTileWords;
+    const uint32_t w = tile * kSelTileWords + tid;
+    const uint32_t wv = w < n_words ? selbits[w] : 0u;       // issued before the prefix loads
     uint32_t part = 0;
-    for (uint32_t j = tid; j < tile; j += 256) part += sel_cnt[j];
+    for (uint32_t j = tid; j < tile; j += kSelTileWords) part += sel_cnt[j];
     part = warp_sum_u32(part);
     if (lane == 0) s_warp_tot[warp] = part;
     __syncthreads();
     if (tid == 0) {
         uint32_t p = 0;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) p += s_warp_tot[w];
+        for (int k = 0; k < kWarps; ++k) p += s_warp_tot[k];
         s_prefix = p;
     }
     __syncthreads();
     const uint32_t prefix = s_prefix;
-    const uint32_t wbase = tile * kCompactWords + tid * 4;
-    uint4 wv = make_uint4(0, 0, 0, 0);
-    if (wbase + 3 < n_words) {
-        wv = *reinterpret_cast<const uint4*>(selbits + wbase);
-    } else {
-        if (wbase < n_words) wv.x = selbits[wbase];
-        if (wbase + 1 < n_words) wv.y = selbits[wbase + 1];
-        if (wbase + 2 < n_words) wv.z = selbits[wbase + 2];
-    }
-    const uint32_t c0 = __popc(wv.x), c1 = __popc(wv.y), c2 = __popc(wv.z), c3 = __popc(wv.w);
-    const uint32_t cnt = c0 + c1 + c2 + c3;
+    const uint32_t cnt = __popc(wv);
     uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -364,9 +359,9 @@ __global__ void __launch_bounds__(256) compact_counted_kernel(const uint32_t* __
     __syncthreads();
     uint32_t off = 0, total = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        const uint32_t tw = s_warp_tot[w];
-        off += (w < (int)warp) ? tw : 0u;
+    for (int k = 0; k < kWarps; ++k) {
+        const uint32_t tw = s_warp_tot[k];
+        off += (k < (int)warp) ? tw : 0u;
         total += tw;
     }
     if (tid == 0 && tile == n_tiles - 1) {
@@ -375,17 +370,16 @@ __global__ void __launch_bounds__(256) compact_counted_kernel(const uint32_t* __
         if (m_all > cap) set_status(st, kErrCapacity, 0x120u);
         st->M = m_all < cap ? m_all : cap;
     }
-    // warp-cooperative expansion: the warp's 128 words in order, one bit per lane
-    const uint32_t p0 = prefix + off + incl - cnt;        // first slot of this lane's words
+    // warp-cooperative expansion: the warp's 32 words in order, one bit per lane
+    const uint32_t p0 = prefix + off + incl - cnt;        // first slot of this lane's word
     const uint32_t lt = (1u << lane) - 1u;
-    const uint32_t wbase_warp = tile * kCompactWords + warp * 128;
-    for (uint32_t q = 0; q < 128; ++q) {
-        const uint32_t owner = q >> 2, sub = q & 3;
-        const uint32_t mine = sub == 0 ? wv.x : sub == 1 ? wv.y : sub == 2 ? wv.z : wv.w;
-        const uint32_t before = sub == 0 ? 0u : sub == 1 ? c0 : sub == 2 ? c0 + c1 : c0 + c1 + c2;
-        const uint32_t wq = __shfl_sync(0xffffffffu, mine, owner);
-        if (wq == 0u) continue;
-        const uint32_t bq = __shfl_sync(0xffffffffu, p0 + before, owner);
+    const uint32_t wbase_warp = tile * kSelTileWords + warp * 32;
+    uint32_t any = __ballot_sync(0xffffffffu, wv != 0u);
+    while (any) {
+        const uint32_t q = (uint32_t)__ffs(any) - 1u;
+        any &= any - 1u;
+        const uint32_t wq = __shfl_sync(0xffffffffu, wv, q);
+        const uint32_t bq = __shfl_sync(0xffffffffu, p0, q);
         const uint32_t pos = bq + __popc(wq & lt);
         if (((wq >> lane) & 1u) && pos < cap) sel[pos] = ((wbase_warp + q) << 5) + lane;
     }
@@ -394,14 +388,14 @@ __global__ void __launch_bounds__(256) compact_counted_kernel(const uint32_t* __
 void launch_compact_counted(const uint32_t* selbits, uint32_t n_words, uint32_t* sel, uint32_t cap,
                             const uint32_t* sel_cnt, FrameState* st, cudaStream_t s)
 {
-    const int n_tiles = (int)((n_words + kCompactWords - 1) / kCompactWords);
-    launch_pdl(compact_counted_kernel, n_tiles < 1 ? 1 : n_tiles, 256, 0, s, selbits, n_words, sel, cap, sel_cnt,
-               st);
+    const int n_tiles = (int)((n_words + kSelTileWords - 1) / kSelTileWords);
+    launch_pdl(compact_counted_kernel, n_tiles < 1 ? 1 : n_tiles, kSelTileWords, 0, s, selbits, n_words, sel,
+               cap, sel_cnt, st);
 }
 
 // One warp looks back from tile 1 at tile 0 with a tag whose low four bits
-// (15) no frame uses (frames tag epoch * 16 + 0, 2..9), so entry 0 never reads as
-// ready and the wait ends by its bound.
+// (15) no frame uses (frames tag epoch * 16 + 0, 2..10), so entry 0 never reads
+// as ready and the wait ends by its bound.
 __global__ void wait_probe_kernel(const unsigned long long* lb, FrameState* st)
 {
     (void)warp_lookback<kProbeSpins>(lb, 1u, 0x3FFFFFFFu, st, kProbeSite);
