@@ -130,15 +130,19 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- roofline
 
-def algorithmic_bytes(tree, M, NP, width, height, sh_floats, E, n_cov, tiles):
+def algorithmic_bytes(tree, M, NP, width, height, sh_floats, E, n_cov, tiles, chunks=None):
     """Bytes the method must move per frame, per stage.  E: selected Gaussians that
     emit pairs, the only ones whose SH colour is evaluated; n_cov: in-frustum
-    internal nodes, the only ones whose covariance R&L needs (both counted on the
-    device); tiles: screen tiles."""
+    internal nodes, the only ones whose covariance R&L needs; chunks: 128-node
+    chunks whose centres R&L reads (the others lie wholly outside the frustum; all
+    three counted on the device; None: every chunk); tiles: screen tiles."""
     N = tree.n
     D = tree.depth
+    n_box = (N + 127) // 128
+    read = n_box if chunks is None else chunks
     return {
-        "filter_rl": 12.0 * N + 24.0 * n_cov + N / 8.0 + N / 8.0,
+        # chunk boxes, the centres and leaf bits of the chunks read, covariances, P bits out
+        "filter_rl": 32.0 * n_box + (12.0 * 128 + 16.0) * read + 24.0 * n_cov + N / 8.0,
         "ancestor_compact": N / 8.0 + 4.0 * D * M + 4.0 * M,
         # id, centre, covariance, opacity + ln opacity in; splat and footprint out;
         # SH rows of the emitting Gaussians; the per-tile pair counts
@@ -437,6 +441,7 @@ def run_ours(args):
         _, _, st = r.render(rgb, Tt, count=True)
         work[k] = {"M": st.n_selected, "NP": st.n_pairs, "E": st.n_emitting,
                    "cov_nodes": st.filter_cov_nodes, "in_frustum": st.filter_in_frustum,
+                   "chunks": st.filter_chunks_read,
                    "evals": st.blend_evals, "hits": st.blend_hits, "entries": st.blend_entries,
                    "active": st.blend_active}
         launches = st.n_launches
@@ -586,9 +591,11 @@ def run_ours(args):
             return float(np.mean([work[k][key] for k in timed]))
         M_mean, NP_mean, E_mean = timed_mean("M"), timed_mean("NP"), timed_mean("E")
         cov_mean = timed_mean("cov_nodes")
+        chunks_mean = timed_mean("chunks")
         sh_floats = (tree.sh_degree + 1) ** 2 * 3
         n_screen_tiles = ((W + 15) // 16) * ((H + 15) // 16)
-        ab = algorithmic_bytes(tree, M_mean, NP_mean, W, H, sh_floats, E_mean, cov_mean, n_screen_tiles)
+        ab = algorithmic_bytes(tree, M_mean, NP_mean, W, H, sh_floats, E_mean, cov_mean, n_screen_tiles,
+                               chunks_mean)
         st_mean = stage_ms.mean(axis=0)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -638,6 +645,8 @@ def run_ours(args):
                        "tau_R": tau_R, "lambda_G": args.lambda_g, "tau": tau,
                        "M_mean": round(M_mean, 1), "emitting_mean": round(E_mean, 1),
                        "N_P_mean": round(NP_mean, 1), "rl_cov_nodes_mean": round(cov_mean, 1),
+                       "rl_chunks_read_mean": round(chunks_mean, 1),
+                       "rl_chunks_total": int((tree.n + 127) // 128),
                        "in_frustum_mean": round(timed_mean("in_frustum"), 1),
                        "work_sample": f"per-frame work averaged over the {K} timed steps' poses "
                                       f"(counted on the device, one counting frame per pose)",

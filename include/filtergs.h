@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define FGS_VERSION 2
+#define FGS_VERSION 3
 
 #define FGS_OK 0
 #define FGS_ERR_ARG (-1)       /* invalid argument (NULL, size, NaN camera ...) */
@@ -146,6 +146,8 @@ typedef struct fgs_stats {
     uint64_t filter_cov_nodes;   /* FGS_RENDER_COUNT: in-frustum internal nodes, the only ones whose
                                     covariance the R&L filter must read (a leaf passes on the
                                     frustum test alone) */
+    uint64_t filter_chunks_read; /* FGS_RENDER_COUNT: 128-node chunks whose centres the R&L filter
+                                    read (the others lie wholly outside the frustum) */
 } fgs_stats;
 
 /* Library version (FGS_VERSION). */

@@ -605,6 +605,7 @@ int fgs_load_tree(fgs_ctx* c, const fgs_tree* t)
     const size_t o_leaf = off; off = align_up(off + sz_leaf, 256);
     const size_t o_ap = off; off = align_up(off + sz_ap, 256);
     const size_t o_attr = off; off = align_up(off + n_pad * 48, 256);
+    const size_t o_box = off; off = align_up(off + n_pad / 128 * 32, 256);
     const size_t total = off;
 
     free_ptr(c->tree_mem);
@@ -666,6 +667,12 @@ int fgs_load_tree(fgs_ctx* c, const fgs_tree* t)
     dt.leaf_bits = (const uint32_t*)(base + o_leaf);
     dt.ap = (const uint32_t*)(base + o_ap);
     dt.attr = (const float4*)(base + o_attr);
+    dt.cbox = (const float4*)(base + o_box);
+    // the box of the centres of every 128 consecutive nodes (the R&L filter's
+    // per-warp chunk)
+    launch_chunk_boxes(dt, c->sms, 0);
+    FGS_CUDA(c, cudaGetLastError());
+    FGS_CUDA(c, cudaStreamSynchronize(0));
     int r = ensure_nodes(c, n_pad);
     if (r) return r;
     // children lists (CSR, ascending ids) for the level-wise baseline
@@ -901,6 +908,7 @@ int fgs_render(fgs_ctx* c, void* stream, float* rgb_out, float* T_out, int out_i
             st->n_emitting = c->st_host->n_emitting;
             st->filter_in_frustum = c->st_host->filter_in_frustum;
             st->filter_cov_nodes = c->st_host->filter_cov_nodes;
+            st->filter_chunks_read = c->st_host->filter_chunks;
         }
         if ((r = latched_status(c))) {
             clear_status(c, s);
@@ -1125,6 +1133,7 @@ int fgs_update_params(fgs_ctx* c, void* stream, const fgs_gauss_params* p)
     const int blocks = (int)std::min<uint64_t>((c->tree.n + 255) / 256, (uint64_t)c->sms * 8);
     launch_prep_params(c->tree, p->mu, p->log_scale, p->quat, p->logit, p->sh, std::max(blocks, 1),
                        (cudaStream_t)stream);
+    launch_chunk_boxes(c->tree, c->sms, (cudaStream_t)stream);     // the centres changed
     FGS_CUDA(c, cudaGetLastError());
     return FGS_OK;
 }

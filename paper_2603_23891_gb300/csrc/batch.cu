@@ -37,20 +37,41 @@ __global__ void bframe_begin_kernel(FrameState* st, uint32_t* tile_cnt, uint32_t
     for (uint32_t i = tid; i < n_tiles; i += gridDim.x * blockDim.x) tile_cnt[i] = 0;
 }
 
-// R&L for V views: 4 consecutive nodes per thread, cameras in shared memory.
+// R&L for V views: 4 consecutive nodes per thread, a warp a 128-node chunk,
+// cameras and their frustum planes in shared memory.  Lane v tests the chunk's
+// box against view v's frustum: the chunk's centres are read only if some view
+// may hold one of them, and evaluated only for those views (a chunk outside a
+// view's frustum has no node with P there: its P bits are written as 0); lane l
+// tests views l and l + 32.
 __global__ void __launch_bounds__(256) bpred_kernel(DevTree t, const DevCamera* __restrict__ cams,
                                                     int V, uint32_t* __restrict__ pbits)
 {
     __shared__ DevCamera s_cam[kMaxBatchViews];
+    __shared__ FrustumPlanes s_planes[kMaxBatchViews];
     for (int i = threadIdx.x; i < V * (int)(sizeof(DevCamera) / 4); i += blockDim.x)
         reinterpret_cast<uint32_t*>(s_cam)[i] = reinterpret_cast<const uint32_t*>(cams)[i];
+    __syncthreads();
+    if ((int)threadIdx.x < V) frustum_planes(s_cam[threadIdx.x], s_planes[threadIdx.x]);
     __syncthreads();
     const uint32_t n_chunks = t.n_pad >> 2;
     const uint32_t n_words = t.n_pad >> 5;
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t stride = gridDim.x * blockDim.x;       // a multiple of 32: warps keep 128-node chunks
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_chunks; i += stride) {
         const uint32_t n0 = i << 2;
+        const uint32_t c = i >> 5;
+        const float4 lo = __ldg(t.cbox + 2 * c), hi = __ldg(t.cbox + 2 * c + 1);
+        static_assert(kMaxBatchViews <= 64, "two ballots of views");
+        const unsigned long long vmask =
+            (unsigned long long)__ballot_sync(0xffffffffu, (int)lane < V && !chunk_outside(s_planes[lane], lo, hi)) |
+            ((unsigned long long)__ballot_sync(0xffffffffu, (int)lane + 32 < V &&
+                                                                !chunk_outside(s_planes[lane + 32 < kMaxBatchViews ? lane + 32 : 0], lo, hi))
+             << 32);
+        if (vmask == 0ull) {
+            for (int v = 0; v < V; ++v)
+                if ((lane & 7) == 0) pbits[(size_t)v * n_words + (i >> 3)] = 0u;
+            continue;
+        }
         const float4 mx = __ldg(reinterpret_cast<const float4*>(t.mu) + i);
         const float4 my = __ldg(reinterpret_cast<const float4*>(t.mu + t.n_pad) + i);
         const float4 mz = __ldg(reinterpret_cast<const float4*>(t.mu + 2 * (size_t)t.n_pad) + i);
@@ -61,6 +82,10 @@ __global__ void __launch_bounds__(256) bpred_kernel(DevTree t, const DevCamera* 
         float4 cv[6];
         bool have_cov = false;
         for (int v = 0; v < V; ++v) {
+            if (!((vmask >> v) & 1ull)) {
+                if ((lane & 7) == 0) pbits[(size_t)v * n_words + (i >> 3)] = 0u;
+                continue;
+            }
             const DevCamera& cam = s_cam[v];
             float vz[4], txtz[4], tytz[4];
             uint32_t inf = 0;

@@ -66,6 +66,10 @@ struct DevTree {
     // the projection's gather copy, node-major: {mu.x, mu.y, mu.z, alpha0},
     // {xx, xy, xz, yy}, {yz, zz, ln alpha0, 0}
     const float4* attr;        // [n_pad][3]
+    // per 128 consecutive nodes (one warp's chunk in the R&L filter): the box of
+    // their centres, {lo.x, lo.y, lo.z, 0}, {hi.x, hi.y, hi.z, 0}; lo.x > hi.x for a
+    // chunk of padding only
+    const float4* cbox;        // [n_pad / 128][2]
 };
 
 // Per-frame device state (one per context).
@@ -84,6 +88,7 @@ struct FrameState {
     uint32_t n_emitting;                  // selected Gaussians with at least one pair
     unsigned long long filter_in_frustum; // counting frames: nodes in the frustum
     unsigned long long filter_cov_nodes;  // counting frames: in-frustum internal nodes
+    unsigned long long filter_chunks;     // counting frames: 128-node chunks whose centres R&L read
 
 };
 
@@ -167,6 +172,52 @@ __device__ __forceinline__ bool frustum_test(const DevCamera& cam, float vx, flo
     txtz = fd(vx, vz);
     tytz = fd(vy, vz);
     return txtz >= -limx && txtz <= limx && tytz >= -limy && tytz <= limy;
+}
+
+// Whether every centre in the box [lo, hi] fails the frustum test (§3.2's
+// in-frustum condition: depth above 0.2, |x / z| and |y / z| within 1.3 times
+// the half-FOV tangents), so that the R&L filter can skip reading the chunk: the
+// box lies beyond one of the five planes x = L z, x = -L z, y = L z, y = -L z,
+// z = 0.2 (a point beyond a side plane either has x / z beyond L or a depth
+// below the near plane).  Exact for the per-node binary32 test: a plane counts
+// only if the box clears it by a margin of 1e-3 times the magnitudes involved,
+// a thousand times the rounding of the camera transform and the divisions.
+struct FrustumPlanes {
+    float4 p[5];      // n.x, n.y, n.z, d: outside where n . p + d > 0
+    float scale;      // 1 + the larger guard-banded tangent
+    float tt;         // |t|_1 of the camera translation
+};
+
+__device__ __forceinline__ void frustum_planes(const DevCamera& cam, FrustumPlanes& F)
+{
+    const float Lx = fm(1.3f, cam.tan_half_x), Ly = fm(1.3f, cam.tan_half_y);
+    const float* R = cam.R;
+    const float* t = cam.t;
+    // right, left, bottom, top, near
+    F.p[0] = make_float4(R[0] - Lx * R[6], R[1] - Lx * R[7], R[2] - Lx * R[8], t[0] - Lx * t[2]);
+    F.p[1] = make_float4(-R[0] - Lx * R[6], -R[1] - Lx * R[7], -R[2] - Lx * R[8], -t[0] - Lx * t[2]);
+    F.p[2] = make_float4(R[3] - Ly * R[6], R[4] - Ly * R[7], R[5] - Ly * R[8], t[1] - Ly * t[2]);
+    F.p[3] = make_float4(-R[3] - Ly * R[6], -R[4] - Ly * R[7], -R[5] - Ly * R[8], -t[1] - Ly * t[2]);
+    F.p[4] = make_float4(-R[6], -R[7], -R[8], 0.2f - t[2]);
+    F.scale = 1.0f + fmaxf(Lx, Ly);
+    F.tt = fabsf(t[0]) + fabsf(t[1]) + fabsf(t[2]);
+}
+
+__device__ __forceinline__ bool chunk_outside(const FrustumPlanes& F, float4 lo, float4 hi)
+{
+    if (lo.x > hi.x) return true;                          // padding only
+    const float ax = fmaxf(fabsf(lo.x), fabsf(hi.x)), ay = fmaxf(fabsf(lo.y), fabsf(hi.y));
+    const float az = fmaxf(fabsf(lo.z), fabsf(hi.z));
+    const float margin = 1e-3f * ((ax + ay + az + F.tt) * F.scale + 1.0f);
+    bool out = false;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float4 q = F.p[k];
+        const float m = q.w + fminf(q.x * lo.x, q.x * hi.x) + fminf(q.y * lo.y, q.y * hi.y) +
+                        fminf(q.z * lo.z, q.z * hi.z);
+        out |= m > margin;
+    }
+    return out;
 }
 
 // Sigma_2D and lambda_max for an in-frustum node.  s = {xx, xy, xz, yy, yz, zz}.
@@ -339,6 +390,8 @@ void launch_frame_begin(FrameState* st, uint32_t* tile_cnt, int n_tiles, uint32_
                         cudaStream_t s);
 void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits, FrameState* count_st, int blocks,
                         cudaStream_t s);
+// The per-128-node boxes of the centres (t.cbox) from t.mu.
+void launch_chunk_boxes(const DevTree& t, int sms, cudaStream_t s);
 // Also adds each word's selected nodes to sel_cnt[word / kSelTileWords].
 void launch_filter_anc(const DevTree& t, const uint32_t* pbits, uint32_t* selbits, uint32_t* sel_cnt,
                        int blocks, cudaStream_t s);

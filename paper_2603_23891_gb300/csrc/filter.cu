@@ -2,9 +2,11 @@
 //
 //  filter_pred        R&L filter: every node independently, P(n) = in-frustum and
 //                     (leaf or R_2D = 3 sqrt(lambda_max) <= tau_R).  Streams the
-//                     SoA centres with 16-byte loads; the covariance is read only
-//                     for in-frustum internal nodes (a leaf passes on the frustum
-//                     test alone).  Output: one bit per node.
+//                     SoA centres with 16-byte loads, skipping each 128-node chunk
+//                     whose centres' box lies outside the frustum (none of its
+//                     nodes can pass); the covariance is read only for in-frustum
+//                     internal nodes (a leaf passes on the frustum test alone).
+//                     Output: one bit per node.
 //  filter_anc         Ancestor filter: a node with P walks its ancestor path AP
 //                     (parent first, stopping at the first ancestor with P); one bit
 //                     per node for the survivors, and the survivors of every
@@ -36,6 +38,7 @@ __global__ void frame_begin_kernel(FrameState* st, uint32_t* tile_cnt, int n_til
         st->n_emitting = 0;
         st->filter_in_frustum = 0;
         st->filter_cov_nodes = 0;
+        st->filter_chunks = 0;
     }
     if (tid < 16) st->tickets[tid] = 0;
     for (int i = tid; i < n_tiles; i += gridDim.x * blockDim.x) tile_cnt[i] = 0;
@@ -52,81 +55,149 @@ void launch_frame_begin(FrameState* st, uint32_t* tile_cnt, int n_tiles, uint32_
 
 // ---------------------------------------------------------------------------
 // R&L predicate: 4 consecutive nodes per thread, bits assembled per warp.
-// count_st (counting frames only, else null): in-frustum nodes and in-frustum
-// internal nodes are added to its filter counters, one atomic per warp.
+// count_st (counting frames only, else null): in-frustum nodes, in-frustum
+// internal nodes and the chunks read are added to its filter counters, one
+// atomic per warp.
 // ---------------------------------------------------------------------------
+
 __global__ void __launch_bounds__(256) filter_pred_kernel(DevTree t, DevCamera cam, uint32_t* pbits,
                                                           FrameState* count_st)
 {
+    __shared__ FrustumPlanes s_planes;
+    if (threadIdx.x == 0) frustum_planes(cam, s_planes);
+    __syncthreads();
     grid_dep_wait();
     grid_dep_trigger();
-    const uint32_t n_chunks = t.n_pad >> 2;               // multiple of 32
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    uint32_t n_in = 0, n_cov = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_chunks; i += stride) {
-        const uint32_t n0 = i << 2;
-        if (i + stride < n_chunks) {
-            // next chunk's centres (and covariances) into L2 while this one computes
-            const float* nx = t.mu + ((size_t)(i + stride) << 2);
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(nx));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + t.n_pad));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 2 * (size_t)t.n_pad));
+    const uint32_t n_box = t.n_pad >> 7;                  // 128-node chunks
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t n_in = 0, n_cov = 0, n_read = 0;
+    // warp g takes chunks g, g + W, g + 2W, ... (W warps), 32 at a time: lane l tests
+    // the box of the l-th; a chunk whose box lies outside the frustum has no node with
+    // P, so its centres are not read and its P bits are written as 0; the others are
+    // read by the whole warp, 4 nodes a lane, the next one prefetched into L2
+    for (uint32_t cb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; cb < n_box; cb += 32u * n_warps) {
+        const uint32_t cl = cb + lane * n_warps;
+        bool out = true;
+        if (cl < n_box) {
+            out = chunk_outside(s_planes, __ldg(t.cbox + 2 * cl), __ldg(t.cbox + 2 * cl + 1));
+            if (out) reinterpret_cast<uint4*>(pbits)[cl] = make_uint4(0u, 0u, 0u, 0u);
         }
-        const float4 mx = __ldg(reinterpret_cast<const float4*>(t.mu) + i);
-        const float4 my = __ldg(reinterpret_cast<const float4*>(t.mu + t.n_pad) + i);
-        const float4 mz = __ldg(reinterpret_cast<const float4*>(t.mu + 2 * (size_t)t.n_pad) + i);
-        const uint32_t leaf = (__ldg(t.leaf_bits + (i >> 3)) >> ((i & 7) << 2)) & 0xFu;
-        const float xs[4] = {mx.x, mx.y, mx.z, mx.w};
-        const float ys[4] = {my.x, my.y, my.z, my.w};
-        const float zs[4] = {mz.x, mz.y, mz.z, mz.w};
-        float vz[4], txtz[4], tytz[4];
-        uint32_t inf = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float vx, vy;
-            camera_space(cam, xs[k], ys[k], zs[k], vx, vy, vz[k]);
-            txtz[k] = tytz[k] = 0.0f;
-            const bool in = (n0 + k < t.n) && frustum_test(cam, vx, vy, vz[k], txtz[k], tytz[k]);
-            inf |= (uint32_t)in << k;
-        }
-        uint32_t pnib = inf & leaf;                       // in-frustum leaves pass
-        const uint32_t need = inf & ~leaf;                // in-frustum internal nodes
-        n_in += __popc(inf);
-        n_cov += __popc(need);
-        if (need) {
-            const float* c = t.cov;
-            const size_t np = t.n_pad;
-            float4 cv[6];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) cv[q] = __ldg(reinterpret_cast<const float4*>(c + q * np) + i);
+        uint32_t todo = __ballot_sync(0xffffffffu, !out);
+        while (todo) {
+            const uint32_t j = (uint32_t)__ffs(todo) - 1u;
+            todo &= todo - 1u;
+            if (todo) {
+                const uint32_t cn = cb + ((uint32_t)__ffs(todo) - 1u) * n_warps;
+                const float* nx = t.mu + ((size_t)cn << 7) + (lane << 2);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nx));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + t.n_pad));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + 2 * (size_t)t.n_pad));
+            }
+            const uint32_t i = ((cb + j * n_warps) << 5) + lane;   // this lane's 4 nodes
+            const uint32_t n0 = i << 2;
+            ++n_read;
+            const float4 mx = __ldg(reinterpret_cast<const float4*>(t.mu) + i);
+            const float4 my = __ldg(reinterpret_cast<const float4*>(t.mu + t.n_pad) + i);
+            const float4 mz = __ldg(reinterpret_cast<const float4*>(t.mu + 2 * (size_t)t.n_pad) + i);
+            const uint32_t leaf = (__ldg(t.leaf_bits + (i >> 3)) >> ((i & 7) << 2)) & 0xFu;
+            const float xs[4] = {mx.x, mx.y, mx.z, mx.w};
+            const float ys[4] = {my.x, my.y, my.z, my.w};
+            const float zs[4] = {mz.x, mz.y, mz.z, mz.w};
+            float vz[4], txtz[4], tytz[4];
+            uint32_t inf = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (!((need >> k) & 1u)) continue;
-                float s6[6];
-#pragma unroll
-                for (int q = 0; q < 6; ++q)
-                    s6[q] = k == 0 ? cv[q].x : k == 1 ? cv[q].y : k == 2 ? cv[q].z : cv[q].w;
-                float a, b, cc, lam;
-                ewa_cov2d(cam, vz[k], txtz[k], tytz[k], s6, a, b, cc, lam);
-                const float R2d = fm(3.0f, fsq(lam));
-                if (R2d <= cam.tau_R) pnib |= 1u << k;
+                float vx, vy;
+                camera_space(cam, xs[k], ys[k], zs[k], vx, vy, vz[k]);
+                txtz[k] = tytz[k] = 0.0f;
+                const bool in = (n0 + k < t.n) && frustum_test(cam, vx, vy, vz[k], txtz[k], tytz[k]);
+                inf |= (uint32_t)in << k;
             }
+            uint32_t pnib = inf & leaf;                       // in-frustum leaves pass
+            const uint32_t need = inf & ~leaf;                // in-frustum internal nodes
+            n_in += __popc(inf);
+            n_cov += __popc(need);
+            if (need) {
+                const float* c = t.cov;
+                const size_t np = t.n_pad;
+                float4 cv[6];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) cv[q] = __ldg(reinterpret_cast<const float4*>(c + q * np) + i);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!((need >> k) & 1u)) continue;
+                    float s6[6];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q)
+                        s6[q] = k == 0 ? cv[q].x : k == 1 ? cv[q].y : k == 2 ? cv[q].z : cv[q].w;
+                    float a, b, cc, lam;
+                    ewa_cov2d(cam, vz[k], txtz[k], tytz[k], s6, a, b, cc, lam);
+                    const float R2d = fm(3.0f, fsq(lam));
+                    if (R2d <= cam.tau_R) pnib |= 1u << k;
+                }
+            }
+            // assemble 32-bit words: lanes 8j..8j+7 hold the nibbles of word j
+            uint32_t w = pnib << ((lane & 7) << 2);
+            w |= __shfl_xor_sync(0xffffffffu, w, 1);
+            w |= __shfl_xor_sync(0xffffffffu, w, 2);
+            w |= __shfl_xor_sync(0xffffffffu, w, 4);
+            if ((lane & 7) == 0) pbits[i >> 3] = w;
         }
-        // assemble 32-bit words: lanes 8j..8j+7 hold the nibbles of word j
-        uint32_t w = pnib << ((lane & 7) << 2);
-        w |= __shfl_xor_sync(0xffffffffu, w, 1);
-        w |= __shfl_xor_sync(0xffffffffu, w, 2);
-        w |= __shfl_xor_sync(0xffffffffu, w, 4);
-        if ((lane & 7) == 0) pbits[i >> 3] = w;
     }
     if (count_st) {
         const uint32_t a = warp_sum_u32(n_in), b = warp_sum_u32(n_cov);
         if (lane == 0) {
             atomicAdd(&count_st->filter_in_frustum, (unsigned long long)a);
             atomicAdd(&count_st->filter_cov_nodes, (unsigned long long)b);
+            atomicAdd(&count_st->filter_chunks, (unsigned long long)n_read);
         }
     }
+}
+
+// The box of the centres of each 128 consecutive nodes (one warp a chunk, four
+// nodes a lane); a chunk of padding only gets lo.x > hi.x.  Run after every change
+// of the centres (tree upload, parameter map).
+__global__ void __launch_bounds__(256) chunk_boxes_kernel(DevTree t)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t n_box = t.n_pad >> 7;
+    float4* box = const_cast<float4*>(t.cbox);
+    for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < n_box;
+         b += (gridDim.x * blockDim.x) >> 5) {
+        float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t n = (b << 7) + (lane << 2) + k;
+            if (n < t.n)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float v = t.mu[(size_t)q * t.n_pad + n];
+                    lo[q] = fminf(lo[q], v);
+                    hi[q] = fmaxf(hi[q], v);
+                }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                lo[q] = fminf(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+                hi[q] = fmaxf(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+            }
+        if (lane == 0) {
+            box[2 * b] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+            box[2 * b + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+        }
+    }
+}
+
+void launch_chunk_boxes(const DevTree& t, int sms, cudaStream_t s)
+{
+    const uint32_t n_box = t.n_pad >> 7;
+    int blocks = (int)((n_box + 7) / 8);
+    if (blocks > sms * 8) blocks = sms * 8;
+    if (blocks < 1) blocks = 1;
+    chunk_boxes_kernel<<<blocks, 256, 0, s>>>(t);
 }
 
 void launch_filter_pred(const DevTree& t, const DevCamera& cam, uint32_t* pbits, FrameState* count_st,

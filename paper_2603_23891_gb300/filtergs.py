@@ -87,7 +87,7 @@ class fgs_stats(C.Structure):
                 ("n_launches", C.c_uint32), ("device_status", C.c_int32),
                 ("blend_entries", C.c_uint64), ("blend_evals", C.c_uint64), ("blend_hits", C.c_uint64),
                 ("blend_active", C.c_uint64), ("filter_in_frustum", C.c_uint64),
-                ("filter_cov_nodes", C.c_uint64)]
+                ("filter_cov_nodes", C.c_uint64), ("filter_chunks_read", C.c_uint64)]
 
 
 _lib = None

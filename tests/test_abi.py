@@ -40,7 +40,7 @@ def test_exports_every_declared_symbol(lib):
     for name in declared:
         assert hasattr(L, name), name
     assert set(lib.EXPORTED) == declared
-    assert L.fgs_version() == 2
+    assert L.fgs_version() == 3
 
 
 def test_create_without_gpu_fails_cleanly(lib):

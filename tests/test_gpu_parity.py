@@ -516,3 +516,34 @@ def test_pipelined_host_outputs(renderer, tiny):
     with pytest.raises(RuntimeError):
         filtergs.fgs_render(renderer.ctx, renderer.stream, bufs[0][0].numpy(), None, 0,
                             filtergs.FGS_RENDER_ASYNC | filtergs.FGS_RENDER_STATS, filtergs.fgs_stats())
+
+
+def test_frustum_boundary_chunks(renderer):
+    """Leaves on and beside the guard-banded frustum's planes (|x / z| and |y / z| at
+    1.3 times the half-FOV tangents, depth 0.2) at relative offsets down to 1e-7:
+    the R&L filter skips a 128-node chunk only when its centres' box lies beyond a
+    plane by a margin, so the selection must equal the oracle's node for node."""
+    import math as _m
+    W, H = 320, 240
+    cam = synth.look_at_camera([0.0, 0.0, 0.0], [0.0, 1.0, 0.0], W, H, 60.0)
+    R = np.asarray(cam.R, np.float64).reshape(3, 3)
+    t = np.asarray(cam.t, np.float64)
+    Lx, Ly = 1.3 * cam.tan_half_x, 1.3 * cam.tan_half_y
+    rng = np.random.default_rng(31)
+    n = 8192
+    z = rng.uniform(0.05, 60.0, n)
+    rel = rng.choice([-1e-3, -1e-5, -1e-7, 0.0, 1e-7, 1e-5, 1e-3], n)
+    side = rng.integers(0, 5, n)
+    x = rng.uniform(-Lx, Lx, n) * z
+    y = rng.uniform(-Ly, Ly, n) * z
+    x = np.where(side == 0, (Lx + rel) * z, np.where(side == 1, -(Lx + rel) * z, x))
+    y = np.where(side == 2, (Ly + rel) * z, np.where(side == 3, -(Ly + rel) * z, y))
+    z = np.where(side == 4, 0.2 * (1.0 + rel), z)
+    mu = (np.stack([x, y, z], 1) - t) @ R
+    tree = synth.tree_from_gaussians(mu, np.full((n, 3), -4.0), np.tile([1.0, 0, 0, 0], (n, 1)),
+                                     rng.normal(0, 1, n), rng.normal(0, 1, (n, 1, 3)), 0)
+    renderer.load_tree(tree)
+    g = gpu_frame(renderer, tree, cam, -1.0)
+    o, _ = oracle_frame(tree, cam, -1.0, blend=False)
+    assert 0 < len(o.sel) < n
+    assert np.array_equal(g["sel"], o.sel), (len(g["sel"]), len(o.sel))
