@@ -305,16 +305,42 @@ __device__ __forceinline__ void blend_tile_kpc(const DevCamera& cam, uint32_t ti
 constexpr int kHalfBlocks = 16;
 
 struct HalfSmem {
-    uint32_t vals[kValsSlots];
+    uint32_t vals[2][kValsSlots];               // two chunks of values: the walked one, the next
     float4 g0[kChunk];                          // u, v, A', B'
     float4 g1[kChunk];                          // C', lthr, alpha0, depth
     uint16_t hmask[kChunk];                     // bit b: half-block b may hold a pixel reaching lthr
     alignas(16) uint8_t hl[kHalfBlocks][kChunk];   // per half-block ordered list of chunk slots
     float pw[8][kGroup][32];                    // each lane's power per group entry
     float4 grp[8][2][kGroup];                   // alpha0, r, g, b per half and group entry
-    uint64_t bar;
+    uint64_t bar[2];                            // completion of each values buffer's copy
     int timed_out;
 };
+
+// Thread 0: start the TMA bulk copy of chunk [s0, e0) of the sorted values into
+// dst (the 16-byte aligned superset [s0 & ~3, (e0 + 3) & ~3)), completing on bar.
+__device__ __forceinline__ void stage_issue(uint32_t* dst, uint64_t* bar, const uint32_t* vals, uint32_t s0,
+                                            uint32_t e0)
+{
+    const uint32_t a0 = s0 & ~3u;
+    const uint32_t a1 = (e0 + 3u) & ~3u;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, (a1 - a0) * 4u);
+    tma_bulk_g2s(dst, vals + a0, (a1 - a0) * 4u, bar);
+}
+
+// Thread 0: wait for the copy on bar to complete phase `phase` (bounded: on
+// giving up FGS_ERR_TIMEOUT is latched and *timed_out set, as in stage_vals).
+__device__ __forceinline__ void stage_wait(uint64_t* bar, uint32_t phase, int* timed_out, FrameState* st)
+{
+    uint64_t spins = 0;
+    while (!mbar_try_wait(bar, phase)) {
+        if (++spins > kSpinLimit) {
+            *timed_out = 1;
+            set_status(st, kErrTimeout, 0x500u);
+            break;
+        }
+    }
+}
 
 // Half-blocks of the tile (grid of tile_w / 4 x tile_h / 4, row-major bits) that
 // the Gaussian's threshold box meets; the box and its margins are warp_mask's.
@@ -408,8 +434,10 @@ __device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t t
     const uint32_t lt = (1u << lane) - 1u;
 
     if (tid == 0) {
-        mbar_init(&H.bar, 1);
+        mbar_init(&H.bar[0], 1);
+        mbar_init(&H.bar[1], 1);
         H.timed_out = 0;
+        if (s < e) stage_issue(H.vals[0], &H.bar[0], vals, s, min(e, s + kChunk));
     }
     // every group entry's alpha0 and colour finite from the start
     static_assert(sizeof(H.grp) == 2 * 256 * sizeof(float4), "two float4 a thread");
@@ -420,14 +448,22 @@ __device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t t
     float T = 1.0f;
     float3 Cacc = make_float3(0.0f, 0.0f, 0.0f);
     bool done = !inside;
-    uint32_t phase = 0;
-    for (uint32_t s0 = s; s0 < e; s0 += kChunk) {
+    // chunk k's values in buffer k & 1; the next chunk's copy is started once this
+    // chunk's records are gathered, so it lands while the chunk is walked
+    uint32_t phases = 0u;                       // bit i: the parity buffer i's copy completes next
+    uint32_t k = 0;
+    for (uint32_t s0 = s; s0 < e; s0 += kChunk, ++k) {
         const uint32_t e0 = min(e, s0 + kChunk);
         const uint32_t cnt = e0 - s0;
-        const uint32_t off = stage_vals(H.vals, &H.bar, &H.timed_out, vals, s0, e0, phase, st);
+        const uint32_t bi = k & 1u;
+        if (tid == 0) stage_wait(&H.bar[bi], (phases >> bi) & 1u, &H.timed_out, st);
+        phases ^= 1u << bi;
+        __syncthreads();
         if (H.timed_out) break;
+        const uint32_t* cv = H.vals[bi];
+        const uint32_t off = s0 - (s0 & ~3u);
         if (tid < cnt) {
-            uint32_t m = H.vals[off + tid];
+            uint32_t m = cv[off + tid];
             if (m >= M) m = 0;      // only after a failed sort (status already latched)
             const float4* g = reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride);
             const float4 a = __ldg(g), b = __ldg(g + 1);
@@ -435,6 +471,9 @@ __device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t t
             H.hmask[tid] = (uint16_t)half_mask(cam, tx0, ty0, a.x, a.y, a.z, a.w, b.x, b.y);
         }
         __syncthreads();
+        // the other buffer's last reader (chunk k - 1's walk) has finished
+        const bool more = s0 + kChunk < e;
+        if (tid == 0 && more) stage_issue(H.vals[bi ^ 1u], &H.bar[bi ^ 1u], vals, s0 + kChunk, min(e, s0 + 2 * kChunk));
         // the ordered lists of this warp's two half-blocks
         uint32_t n0 = 0, n1 = 0;
         for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
@@ -463,13 +502,13 @@ __device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t t
             float4 ca = make_float4(0.f, 0.f, 0.f, 0.f), cb = ca;
             if (lane < g0n) {
                 ja = H.hl[hb0][i0 + lane];
-                uint32_t m = H.vals[off + ja];
+                uint32_t m = cv[off + ja];
                 if (m >= M) m = 0;
                 ca = __ldg(reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride) + 2);
             }
             if (lane < g1n) {
                 jb = H.hl[hb1][i0 + lane];
-                uint32_t m = H.vals[off + jb];
+                uint32_t m = cv[off + jb];
                 if (m >= M) m = 0;
                 cb = __ldg(reinterpret_cast<const float4*>(splat + (size_t)m * kSplatStride) + 2);
             }
@@ -532,7 +571,14 @@ __device__ __forceinline__ void blend_tile_half(const DevCamera& cam, uint32_t t
             }
         }
         const int n_done = __syncthreads_count(done);
-        if (n_done == (int)blockDim.x) break;
+        if (n_done == (int)blockDim.x) {
+            // a started copy must land before the block leaves
+            if (more) {
+                if (tid == 0) stage_wait(&H.bar[bi ^ 1u], (phases >> (bi ^ 1u)) & 1u, &H.timed_out, st);
+                __syncthreads();
+            }
+            break;
+        }
     }
     if (inside) {
         const size_t hw = (size_t)cam.width * cam.height;
