@@ -5,9 +5,10 @@
 // warp covers an 8 x 4 (or 4 x 8) pixel block.  The tile's slice of the sorted
 // value list is brought into shared memory in chunks of 256 by a TMA bulk copy
 // (cp.async.bulk, completion on an mbarrier; the copy starts at the 16-byte
-// boundary at or below the slice and the index is offset accordingly).  Each
-// thread then gathers one splat record into shared memory and computes which
-// pixel blocks the Gaussian can reach.  The forward culls per 4 x 4 half-block
+// boundary at or below the slice and the index is offset accordingly); in the
+// forward two buffers alternate, the next chunk's copy landing while the
+// current chunk is walked.  Each thread then gathers one splat record into
+// shared memory and computes which pixel blocks the Gaussian can reach.  The forward culls per 4 x 4 half-block
 // (each warp's two halves walk their own ordered lists in lockstep, testing in
 // groups of 32 entries and then applying each lane's hits); the KPC pass culls
 // per warp and walks one entry at a time, reducing alpha * T across the warp.
