@@ -96,3 +96,45 @@ def test_validate_tree(lib):
     sh = tree.sh.copy()
     sh[3, 1, 2] = np.inf
     assert lib.fgs_validate_tree(_mutated(tree, sh=sh))[0] == lib.FGS_ERR_TREE
+
+
+_STRUCTS = ["fgs_tree", "fgs_camera", "fgs_params", "fgs_stats", "fgs_gauss_params", "fgs_gauss_grads"]
+
+
+def test_binding_layouts_match_the_header(tmp_path):
+    """Every struct the ctypes binding passes has the header's size and field offsets (a C
+    program compiled against include/filtergs.h prints them), and every FGS_* integer
+    constant the binding defines has the header's value."""
+    import ctypes
+    import subprocess
+    from paper_2603_23891_gb300 import filtergs
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "filtergs.h"', "int main(void) {"]
+    for s in _STRUCTS:
+        lines.append(f'printf("{s} size %zu\\n", sizeof({s}));')
+        for name, _ in getattr(filtergs, s)._fields_:
+            lines.append(f'printf("{s} {name} %zu\\n", offsetof({s}, {name}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for s in _STRUCTS:
+        cls = getattr(filtergs, s)
+        assert got[(s, "size")] == ctypes.sizeof(cls), s
+        for name, _ in cls._fields_:
+            assert got[(s, name)] == getattr(cls, name).offset, (s, name)
+    header = open(os.path.join(ROOT, "include", "filtergs.h")).read()
+    consts = {m.group(1): int(m.group(2).rstrip("u"), 0)
+              for m in re.finditer(r"^#define (FGS_\w+) \(?(-?\w+)\)?", header, flags=re.M)
+              if re.fullmatch(r"-?(0x[0-9a-fA-F]+|\d+)u?", m.group(2))}
+    checked = 0
+    for name, v in consts.items():
+        if hasattr(filtergs, name):
+            assert getattr(filtergs, name) == v, name
+            checked += 1
+    assert checked >= 10
