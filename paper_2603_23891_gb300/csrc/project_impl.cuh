@@ -92,7 +92,6 @@ __device__ __forceinline__ uint4 project_one(const DevTree& t, const DevCamera& 
                                                 uint32_t m, float* __restrict__ splat,
                                                 uint4* __restrict__ foot)
 {
-    const float fw = (float)cam.tile_w, fh = (float)cam.tile_h;
     const float ftx = (float)cam.tiles_x, fty = (float)cam.tiles_y;
     uint32_t cnt = 0;
     // ---- decision-exact binary32: frustum, EWA covariance, footprint
@@ -108,8 +107,9 @@ __device__ __forceinline__ uint4 project_one(const DevTree& t, const DevCamera& 
     const bool inf = frustum_test(cam, vx, vy, vz, txtz, tytz);
     float a = 0.0f, b = 0.0f, c = 0.0f, lam = 0.0f;
     if (inf) ewa_cov2d(cam, vz, txtz, tytz, s6, a, b, c, lam);
-    const float u = fa(fm(cam.fx, fd(vx, vz)), cam.cx);
-    const float v = fa(fm(cam.fy, fd(vy, vz)), cam.cy);
+    // x / z and y / z: the frustum test's quotients when it formed them (depth above 0.2)
+    const float u = fa(fm(cam.fx, vz > 0.2f ? txtz : fd(vx, vz)), cam.cx);
+    const float v = fa(fm(cam.fy, vz > 0.2f ? tytz : fd(vy, vz)), cam.cy);
     const float det = fs(fm(a, c), fm(b, b));
     const float lthr = fs(-5.5412635451584258f, ln_a0);   // -ln 255 - ln alpha0
     float A = 0.0f, B = 0.0f, C = 0.0f, radius = 0.0f;
@@ -129,10 +129,14 @@ __device__ __forceinline__ uint4 project_one(const DevTree& t, const DevCamera& 
         }
         if (!drop) {
             radius = r;
-            const float fx0 = clampf(floorf(fd(fs(u, r), fw)), 0.0f, ftx);
-            const float fx1 = clampf(fa(floorf(fd(fa(u, r), fw)), 1.0f), 0.0f, ftx);
-            const float fy0 = clampf(floorf(fd(fs(v, r), fh)), 0.0f, fty);
-            const float fy1 = clampf(fa(floorf(fd(fa(v, r), fh)), 1.0f), 0.0f, fty);
+            // tiles are powers of two wide and high, so x / w is x * (1 / w) bit for bit
+            // (both the correctly rounded x * 2^-k)
+            const float iw = __uint_as_float((uint32_t)(127 - cam.tile_shift_x) << 23);
+            const float ih = __uint_as_float((uint32_t)(127 - cam.tile_shift_y) << 23);
+            const float fx0 = clampf(floorf(fm(fs(u, r), iw)), 0.0f, ftx);
+            const float fx1 = clampf(fa(floorf(fm(fa(u, r), iw)), 1.0f), 0.0f, ftx);
+            const float fy0 = clampf(floorf(fm(fs(v, r), ih)), 0.0f, fty);
+            const float fy1 = clampf(fa(floorf(fm(fa(v, r), ih)), 1.0f), 0.0f, fty);
             x0 = (int32_t)fx0; x1 = (int32_t)fx1; y0 = (int32_t)fy0; y1 = (int32_t)fy1;
             if (x1 > x0 && y1 > y0) cnt = (uint32_t)((x1 - x0) * (y1 - y0));
         }
