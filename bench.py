@@ -709,27 +709,49 @@ def oracle_sample(tree, cams, tau_R, tau, ln_tau, pose, pix_frac, seed=0):
     return t_front + t_blend, {"front_s": t_front, "blend_s_scaled": t_blend, "pixels": k}
 
 
+CPU_SAMPLE_S = 10.0     # single-thread seconds of whole oracle frames the CPU-baseline leg times
+CPU_SAMPLE_MAX = 16     # at most this many poses
+
+
+def cpu_sample_poses(n_poses, first):
+    """Pose order of the CPU-baseline sample: the poses in ``first``, then every
+    eighth pose of the flythrough, then the poses between them."""
+    order = list(first)
+    for step_off in range(8):
+        for k in range(step_off, n_poses, 8):
+            if k not in order:
+                order.append(k)
+    return order
+
+
 def cpu_baseline(tree, cams, tau_R, tau, ln_tau, shrunk_images):
-    """The CPU-baseline leg: the oracle on two whole frames (the poses of
-    ``shrunk_images``), on one thread and on every host core (OpenMP; the results
-    are bit-identical).  Untimed, the same leg renders those poses with the
-    oracle's unshrunk (3-sigma) footprint and reports the GPU's shrunk image
-    against it (§3.3: shrinking changes the image; reported, not gated)."""
+    """The CPU-baseline leg: the oracle on whole frames, on one thread and on
+    every host core (OpenMP; the results are bit-identical).  The single-thread
+    run renders poses (those of ``shrunk_images`` first, then spread over the
+    flythrough) until CPU_SAMPLE_S seconds are spent or CPU_SAMPLE_MAX poses are
+    done; the all-core run renders the same poses.  Untimed, the same leg renders
+    the poses of ``shrunk_images`` with the oracle's unshrunk (3-sigma) footprint
+    and reports the GPU's shrunk image against it (§3.3: shrinking changes the
+    image; reported, not gated)."""
     import oracle
-    poses = sorted(shrunk_images)
+    order = cpu_sample_poses(len(cams), sorted(shrunk_images))
     n_all = oracle.set_threads(0)
     out = {}
-    for label, nt in (("single", 1), ("all", n_all)):
-        oracle.set_threads(nt)
-        ts = []
-        for k in poses:
-            t, _ = oracle_sample(tree, cams, tau_R, tau, ln_tau, k, 1.0)
-            ts.append(t)
-        out[label] = (len(ts) / sum(ts), sum(ts), nt)
+    oracle.set_threads(1)
+    poses, ts = [], []
+    for k in order:
+        if len(poses) >= CPU_SAMPLE_MAX or (len(poses) >= len(shrunk_images) and sum(ts) >= CPU_SAMPLE_S):
+            break
+        t, _ = oracle_sample(tree, cams, tau_R, tau, ln_tau, k, 1.0)
+        poses.append(k)
+        ts.append(t)
+    out["single"] = (len(ts) / sum(ts), sum(ts), 1)
     oracle.set_threads(n_all)
+    ts = [oracle_sample(tree, cams, tau_R, tau, ln_tau, k, 1.0)[0] for k in poses]
+    out["all"] = (len(ts) / sum(ts), sum(ts), n_all)
     # shrunk GPU image against the unshrunk oracle image, whole frames
     errs = []
-    for k in poses:
+    for k in sorted(shrunk_images):
         cam = cams[k]
         p = oracle.Params(tau_R=tau_R)
         fr = oracle.frame(tree, cam, p, blend=True)
@@ -741,10 +763,11 @@ def cpu_baseline(tree, cams, tau_R, tau, ln_tau, shrunk_images):
     v_all, s_all, n = out["all"]
     v_one, s_one, _ = out["single"]
     return {"value": round(v_all, 5), "unit": "frames/s", "cores": n, "kind": "oracle",
-            "sample": (f"poses {poses}: whole frames (LoD cut, projection, pairs, per-pixel "
-                       f"blending) on {n} threads, {s_all:.1f}s total"),
+            "sample": (f"poses {poses}: {len(poses)} whole frames (LoD cut, projection, pairs, "
+                       f"per-pixel blending) on {n} threads, {s_all:.1f}s total"),
             "single_core": {"value": round(v_one, 5), "unit": "frames/s", "cores": 1,
-                            "sample": f"the same two frames on 1 thread, {s_one:.1f}s total"},
+                            "sample": (f"the same {len(poses)} frames on 1 thread, {s_one:.1f}s total "
+                                       f"(poses added until {CPU_SAMPLE_S:.0f}s)")},
             "shrink_vs_unshrunk_oracle": {
                 "tau": tau, "poses": errs,
                 "how": "GPU image at the calibrated tau against the oracle's 3-sigma image of the "

@@ -62,3 +62,14 @@ def test_cpu_baseline_leg_on_the_tiny_workload():
     assert out["cores"] >= 1 and out["single_core"]["cores"] == 1
     e = out["shrink_vs_unshrunk_oracle"]["poses"][0]
     assert e["pose"] == 0 and e["max_abs"] > 0 and 10 < e["psnr_db"] < 200
+    assert "1 whole frames" in out["sample"]
+
+
+def test_cpu_sample_pose_order():
+    """The CPU-baseline sample takes the compared poses first, then spreads over the
+    flythrough; every pose appears once."""
+    order = bench.cpu_sample_poses(64, [0, 32])
+    assert order[:8] == [0, 32, 8, 16, 24, 40, 48, 56]
+    assert sorted(order) == list(range(64))
+    assert bench.cpu_sample_poses(1, [0]) == [0]
+    assert sorted(bench.cpu_sample_poses(8, [0, 4])) == list(range(8))
