@@ -240,6 +240,7 @@ def run_batched(r, torch, filtergs, args):
         r.render_batch(rgb, T, graph=True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hold_stream(torch, reps)              # both loops: the host enqueues them behind a spin
     e0.record()
     for _ in range(reps):
         r.render_batch(rgb, T, graph=True)
@@ -257,6 +258,7 @@ def run_batched(r, torch, filtergs, args):
         r.set_camera(c)
         r.render(*outs[(c.width, c.height)])
     torch.cuda.synchronize()
+    hold_stream(torch, reps * len(cams))
     e0.record()
     for _ in range(reps):
         for c in cams:
@@ -271,7 +273,10 @@ def run_batched(r, torch, filtergs, args):
             "sequential_ms": round(seq_ms, 3), "speedup": round(seq_ms / batch_ms, 2),
             "selected_entries": int(st.n_selected), "pairs": int(st.n_pairs),
             "autotune": {f"{w}x{h}": list(v) for (w, h), v in choice.items()},
-            "autotune_s": round(tune_s, 2), "graph": True}
+            "autotune_s": round(tune_s, 2), "graph": True,
+            "how": ("CUDA events around reps batch replays and around reps x 32 single-view "
+                    "calls, each loop enqueued behind a fixed-length spin (device time, no "
+                    "waits for the host)")}
 
 
 # ----------------------------------------------------------------------------- ours
@@ -301,6 +306,7 @@ def _time_backward(r, torch, cams, poses, P, G, dL_of, keep, accumulate, flush):
     torch.cuda.synchronize()
     fwd, bwd = [], []
     for k in poses:
+        hold_stream(torch, 1, min_s=0.01)                 # the host enqueues the pose behind it
         flush.zero_()
         r.set_camera(cams[k])
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -374,7 +380,8 @@ def run_backward(r, torch, filtergs, args):
             "recompute": out["recompute"], "kept_state": out["kept_state"],
             "prep_params_ms": round(prep_ms, 4), "loss_pose0": loss[0] if loss else None,
             "how": "CUDA events around fgs_render and around fgs_backward per pose (L2 flushed "
-                   "before each pose), accumulate mode; the loss gradient is outside both"}
+                   "before each pose, each pose enqueued behind a 10 ms fixed-length spin), accumulate "
+                   "mode; the loss gradient is outside both"}
 
 
 def run_backward_city(r, torch, tree, cams, poses, args):
@@ -469,6 +476,10 @@ def run_ours(args):
     clocks.start()
     time.sleep(0.3)
     wall0 = time.perf_counter()
+    # hold the stream with torch's fixed-length spin kernel while the host enqueues
+    # the K steps, so that a step's events never include the GPU waiting for the host
+    # to launch its first kernel (the spin runs before the first step's start event)
+    hold_s = hold_stream(torch, K)
     for k in range(K):
         flush.zero_()                                     # evict L2 between steps
         r.set_camera(cams[my_poses[k % len(my_poses)]])
@@ -652,6 +663,7 @@ def run_ours(args):
                                       f"(counted on the device, one counting frame per pose)",
                        "N_P_mean_shrink_off": round(float(np.mean(NP_off)), 1),
                        "l2": "flushed between steps (256 MiB write, outside the step events)",
+                       "stream_hold_s": hold_s,
                        "parallelism": f"replicas x{world} (views round-robin)"},
             "stages_ms": {nm: stages[nm]["ms"] for nm in STAGES},
             "stages": stages,
@@ -711,6 +723,24 @@ def oracle_sample(tree, cams, tau_R, tau, ln_tau, pose, pix_frac, seed=0):
 
 CPU_SAMPLE_S = 10.0     # single-thread seconds of whole oracle frames the CPU-baseline leg times
 CPU_SAMPLE_MAX = 16     # at most this many poses
+
+
+HOLD_S_MIN = 0.5        # seconds the stream is held while the host enqueues the timed steps
+HOLD_S_PER_STEP = 0.01
+HOLD_S_MAX = 5.0
+
+
+def hold_stream(torch, steps, min_s=HOLD_S_MIN, clock_hz=2.07e9):
+    """Enqueue torch's fixed-length spin kernel (a clock-count loop, no flag) on the
+    current stream, long enough for the host to enqueue ``steps`` steps behind it
+    (at least ``min_s`` seconds).  Returns its nominal length in seconds (0 when
+    torch lacks the helper)."""
+    spin = getattr(torch.cuda, "_sleep", None)
+    if spin is None:
+        return 0.0
+    s = min(HOLD_S_MAX, max(min_s, HOLD_S_PER_STEP * steps))
+    spin(int(s * clock_hz))
+    return round(s, 3)
 
 
 def cpu_sample_poses(n_poses, first):

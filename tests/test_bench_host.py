@@ -73,3 +73,29 @@ def test_cpu_sample_pose_order():
     assert sorted(order) == list(range(64))
     assert bench.cpu_sample_poses(1, [0]) == [0]
     assert sorted(bench.cpu_sample_poses(8, [0, 4])) == list(range(8))
+
+
+def test_hold_stream_lengths():
+    """The timed loops' stream hold: at least the minimum, 10 ms a step, at most 5 s,
+    passed to torch's spin helper as clock cycles; nothing without the helper."""
+    calls = []
+
+    class Cuda:
+        @staticmethod
+        def _sleep(c):
+            calls.append(c)
+
+    class Torch:
+        cuda = Cuda
+
+    assert bench.hold_stream(Torch, 20) == 0.5
+    assert bench.hold_stream(Torch, 64) == 0.64
+    assert bench.hold_stream(Torch, 10_000) == 5.0
+    assert bench.hold_stream(Torch, 1, min_s=0.01) == 0.01
+    assert calls == [int(s * 2.07e9) for s in (0.5, 0.64, 5.0, 0.01)]
+
+    class NoSpin:
+        class cuda:
+            pass
+
+    assert bench.hold_stream(NoSpin, 20) == 0.0
