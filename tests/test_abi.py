@@ -138,3 +138,36 @@ def test_binding_layouts_match_the_header(tmp_path):
             assert getattr(filtergs, name) == v, name
             checked += 1
     assert checked >= 10
+
+
+def test_null_arguments_rejected_before_any_cuda_call(lib):
+    """Every entry point checks its context and output pointers before it touches the
+    GPU: with a null context (or null buffers) each returns FGS_ERR_ARG, here on a
+    machine without a GPU; fgs_destroy(NULL) is a no-op, fgs_last_error(NULL) a fixed
+    string, and the context-free entry points reject bad sizes before any launch."""
+    import ctypes
+    L = lib.lib()
+    special = {"fgs_version", "fgs_destroy", "fgs_last_error", "fgs_validate_tree", "fgs_eval_exp",
+               "fgs_compact_selection_noalloc"}
+    checked = 0
+    for name in lib.EXPORTED:
+        if name in special:
+            continue
+        f = getattr(L, name)
+        args = [0.0 if t is ctypes.c_float else 0 if t in (ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64,
+                                                          ctypes.c_size_t) else None
+                for t in f.argtypes]
+        assert f(*args) == lib.FGS_ERR_ARG, name
+        checked += 1
+    assert checked == len(lib.EXPORTED) - len(special)
+    assert L.fgs_destroy(None) == lib.FGS_OK
+    assert L.fgs_last_error(None) == b"null context"
+    msg = ctypes.create_string_buffer(128)
+    assert L.fgs_validate_tree(None, msg, 128) == lib.FGS_ERR_ARG and msg.value == b"null tree"
+    assert L.fgs_eval_exp(None, None, 0, None) == lib.FGS_OK          # nothing to do
+    assert L.fgs_eval_exp(None, None, 5, None) == lib.FGS_ERR_ARG
+    nz = ctypes.c_void_p(0x1000)                                         # never dereferenced
+    noalloc = L.fgs_compact_selection_noalloc
+    assert noalloc(None, 4, nz, nz, None) == lib.FGS_ERR_ARG
+    assert noalloc(nz, 0, nz, nz, None) == lib.FGS_ERR_ARG
+    assert noalloc(nz, (1 << 26) + 1, nz, nz, None) == lib.FGS_ERR_ARG   # above the scratch's limit
